@@ -1,0 +1,362 @@
+"""Benchmark of the PIMI sweep path on GB300 (one JSON line on stdout, rank 0).
+
+Workload (default): SK-1 spin glasses, N = 200, J_ij = +-1 symmetric, zero diagonal,
+h = 0, 100 seeded instances x 1024 replicas x 2000 synchronous sweeps, linear beta
+0.1 -> 3, eta = sqrt(beta/5), xi = 0.5, c = 1/sqrt(N), Philox seed 0.  A step is one
+pass of the whole hot path over that batch: initial spins, 2000 fused sweeps (fields,
+decisions, spin write-back, energy and best-state tracking) and the final energy, in one
+batched launch.  Inputs are synthetic (generated, seeded).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the same per-GPU workload on its own instance ids (weak
+scaling, no collective on the data path); times are max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SPINS = 200
+N_INST = 100
+REPLICAS = 1024
+SWEEPS = 2000
+XI = 0.5
+WORKLOAD = "sk200_100inst_1024rep_2000sweeps"
+METRIC = "spin-updates/s"
+
+# Algorithmic operation count per spin update of the sweep (integer / FP32 ALU):
+#   noise: one Philox4x32-10 block per 8 spins; a round = 2 mul.lo + 2 mul.hi + 4 xor +
+#          2 key adds = 10 ops -> 100 ops per block -> 12.5 per spin
+#   key extraction 2, field-to-index 1, threshold lookup 1, spin select 1, compare 1,
+#   new-spin insert 1, energy accumulate 2, spin-to-operand write-back 1
+ALU_OPS_PER_SPIN_UPDATE = 12.5 + 2 + 1 + 1 + 1 + 1 + 1 + 2 + 1
+SM_COUNT = 152
+LANES_PER_SM = 128
+
+
+def _schedule():
+    from workloads import eta_power, linear_beta
+    beta = linear_beta(SWEEPS)
+    return beta, eta_power(beta)
+
+
+def _instances(rank: int):
+    from workloads import sk_batch
+    return sk_batch(N_SPINS, N_INST, first_seed=rank * N_INST)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- oracle (CPU)
+def _oracle_sample(budget_s: float, max_instances: int, replicas: int):
+    """Time the oracle as it stands on a bounded sample of the workload: whole 2000-sweep
+    runs of the first instances with `replicas` replicas each, until the time budget is
+    spent.  Returns (spin updates, seconds, description)."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from workloads import sk_pm1
+    beta, eta = _schedule()
+    done, t0 = 0, time.perf_counter()
+    k = 0
+    while k < max_instances:
+        inst = sk_pm1(N_SPINS, k)
+        oracle.anneal(inst.J, inst.h, inst.c, beta, eta, XI, replicas=replicas, seed=0, q=k)
+        done += N_SPINS * replicas * SWEEPS
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, (f"{k} instance(s) x {replicas} replicas x {SWEEPS} sweeps of the "
+                      f"{WORKLOAD} workload, single thread")
+
+
+def _cpu_worker(argv):
+    budget, max_inst, reps = float(argv[0]), int(argv[1]), int(argv[2])
+    n, dt, desc = _oracle_sample(budget, max_inst, reps)
+    print(json.dumps({"updates": n, "seconds": dt, "sample": desc}))
+
+
+def cpu_baseline(budget_s=15.0, max_instances=8, replicas=16):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                          str(budget_s), str(max_instances), str(replicas)],
+                         capture_output=True, text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": d["updates"] / d["seconds"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": d["sample"]}
+
+
+# ------------------------------------------------------------------------- distributed
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    base = cpu_baseline(budget_s=5.0, max_instances=2, replicas=8)
+    vals = []
+    sample = None
+    for k in range(args.warmup + args.steps):
+        n, dt, sample = _oracle_sample(0.0, 1, 8)
+        if k >= args.warmup:
+            vals.append(n / dt)
+    value = statistics.mean(vals)
+    per_step_updates = N_SPINS * 8 * SWEEPS
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step_updates / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SPINS, "instances": N_INST,
+                   "replicas": REPLICAS, "sweeps": SWEEPS,
+                   "sample_per_step": "1 instance x 8 replicas x 2000 sweeps"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_calibration": base,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------- our arm
+def run_ours(args):
+    world, rank, local = _dist()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2604_17109_gb300 import build as pkg_build
+    from paper_2604_17109_gb300 import pim
+
+    pkg_build.build()
+    beta, eta = _schedule()
+    insts = _instances(rank)
+    ids = np.arange(rank * N_INST, (rank + 1) * N_INST, dtype=np.uint32)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # ---- device-resident inputs: staged once, reused by every timed step -------------
+    handles = [pim.pim_create(i.J, None, i.c) for i in insts]
+    for hd in handles:
+        pim.pim_set_schedule(hd, beta, eta, XI)
+    updates_per_step = N_SPINS * REPLICAS * SWEEPS * N_INST
+
+    def step():
+        pim.pim_anneal_batch(handles, REPLICAS, SWEEPS, seed=0, instance_ids=ids, stream=stream)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    with ClockSampler(local) as clocks:
+        _barrier(world)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush between timed steps (outside the event pair)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+            kernel_ms.append(None)
+            ends[k].synchronize()
+            kernel_ms[-1] = pim.pim_kernel_ms(handles[0])
+        torch.cuda.synchronize()
+        _barrier(world)
+        wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = _max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / args.steps
+    value = updates_per_step * world / (ms_per_step * 1e-3)
+    k_ms = statistics.mean(kernel_ms)
+
+    # ---- end to end through the public API from host buffers ---------------------------
+    e2e_steps = max(1, min(3, args.steps))
+    h2d = sum(i.J.nbytes for i in insts)
+    R = REPLICAS
+    d2h = N_INST * (R * (8 + 4 + 4 + 8) + R * 8 * 4)
+    out_E = [None] * N_INST
+    torch.cuda.synchronize()
+    _barrier(world)
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hs = [pim.pim_create(i.J, None, i.c) for i in insts]
+        for hd in hs:
+            pim.pim_set_schedule(hd, beta, eta, XI)
+        pim.pim_anneal_batch(hs, REPLICAS, SWEEPS, seed=0, instance_ids=ids, stream=stream)
+        for q, hd in enumerate(hs):
+            out_E[q] = pim.pim_energies(hd)["best_E"]
+            pim.pim_best_state(hd, N_SPINS)
+        for hd in hs:
+            pim.pim_destroy(hd)
+    e2e_s = _max_over_ranks(time.perf_counter() - e0, world) / e2e_steps
+    e2e_value = updates_per_step * world / e2e_s
+
+    for hd in handles:
+        pim.pim_destroy(hd)
+
+    if rank != 0:
+        return 0
+    peaks, peak_kind = _peaks()
+    clk = clocks.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
+    alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * SWEEPS * N_INST
+    fp8_peak = float(peaks["bf16_tflops"]) * 2.0
+    tensor_achieved = flops / (k_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8e4m3/i32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_SPINS, "instances_per_gpu": N_INST,
+                   "replicas": REPLICAS, "sweeps": SWEEPS, "couplings": "SK +-1, h=0",
+                   "schedule": "linear beta 0.1->3, eta=sqrt(beta/5), xi=0.5",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                     "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": None,
+                     "kernel": "sweep_tc_kernel<256>", "kernel_ms": k_ms,
+                     "ops_per_spin_update": ALU_OPS_PER_SPIN_UPDATE,
+                     "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"},
+        "tensor_pipe": {"achieved_tflops": tensor_achieved, "peak_tflops": fp8_peak,
+                        "frac": tensor_achieved / fp8_peak,
+                        "peak_basis": f"bf16 {peak_kind} x 2 (fp8 nominal ratio)"},
+        "cpu_baseline": cpu_baseline(),
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "min_best_energy_instance0": float(np.min(out_E[0])),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-worker":
+        _cpu_worker(sys.argv[2:])
+        return 0
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

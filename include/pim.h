@@ -1,0 +1,234 @@
+/*
+ * pim.h -- C ABI of the GB300 PIMI sweep library.
+ *
+ * The library runs the probabilistic Ising machine with inertia (PIMI) of
+ * arXiv 2604.17109: fully parallel, synchronous spin updates
+ *
+ *     I_i(t)   = sum_j J_ij s_j(t) + h_i                                  (Eq. 2)
+ *     s_i(t+1) = sign[ tanh(beta(t) I_i(t)) + xi s_i(t) + eta(t) N(0,1) ]  (Eq. 4)
+ *
+ * over many replicas ("trials", Box 1) and many instances at once, tracking for every
+ * replica the Ising energy H(s) = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i (Eq. 1) of
+ * every visited state, the best state, and the first step whose energy reaches a target
+ * (success criterion of the supplementary CCTS section).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a status (pim_status); nothing throws across the ABI.  On error
+ *    pim_last_error() returns a thread-local message describing the last failure.
+ *  - Host buffers passed in are only read during the call; the library deep-copies what
+ *    it keeps.  The caller owns every buffer it passes and every output buffer.
+ *  - Device state (staged couplings, schedules, spins, results) is owned by the
+ *    pim_instance and freed by pim_destroy.
+ *  - Spin arrays on the host are int8 values -1/+1, row-major (replica, spin).
+ *  - Annealing calls are asynchronous on the CUDA stream passed as `cuda_stream`
+ *    (a cudaStream_t; NULL = the legacy default stream).  Result getters synchronise on
+ *    the instance's last launch before copying.
+ *  - One GPU: all device memory lives on the device that is current when pim_create
+ *    runs; later calls must run with that device current.
+ */
+#ifndef PIM_H
+#define PIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum pim_status {
+  PIM_OK = 0,
+  PIM_PENDING = 1,          /* pim_poll: the submitted work has not finished yet */
+  PIM_ERR_INVALID = -1,     /* bad argument: sizes, asymmetric J, non-zero diagonal, ... */
+  PIM_ERR_NOMEM = -2,       /* device or host allocation refused */
+  PIM_ERR_CUDA = -3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  PIM_ERR_STATE = -4,       /* call out of order (no schedule, no previous state, ...) */
+  PIM_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  PIM_ERR_UNSUPPORTED = -6  /* valid request that this build does not implement */
+} pim_status;
+
+/* Element type of the host coupling matrix passed to pim_create. */
+typedef enum pim_j_type {
+  PIM_J_INT8 = 0,  /* int8, integer couplings |J_ij| <= 16 (held exactly as FP8 E4M3) */
+  PIM_J_FP32 = 1,  /* float32 real couplings (not yet accepted: PIM_ERR_UNSUPPORTED) */
+  PIM_J_FP64 = 2   /* float64 real couplings (not yet accepted: PIM_ERR_UNSUPPORTED) */
+} pim_j_type;
+
+/* Noise term of the update rule. */
+typedef enum pim_noise {
+  PIM_NOISE_GAUSS = 0,   /* eta(t) N(0,1), Eq. 4 */
+  PIM_NOISE_UNIFORM = 1  /* eta(t) U(-1,1), Eq. 3 */
+} pim_noise;
+
+/* Activation applied to beta(t) I_i(t). */
+typedef enum pim_act {
+  PIM_ACT_TANH = 0,  /* tanh, Eq. 4 */
+  PIM_ACT_LUT = 1    /* L-level staircase of Algorithm "LUT-based tanh approximation" */
+} pim_act;
+
+/* Flags of pim_anneal / pim_anneal_batch. */
+typedef enum pim_flags {
+  PIM_CONTINUE = 1,     /* start from the instance's current state and keep its best /
+                           first-hit records (resume); replicas must equal the last run's */
+  PIM_PATH_FP32REF = 2  /* run the plain FP32 two-kernels-per-sweep comparator path instead
+                           of the fused tensor-core sweep kernel (same decisions) */
+} pim_flags;
+
+typedef struct pim_instance pim_instance;
+
+/*
+ * pim_create -- stage one Ising instance (J, h) on the device.
+ * Defines the problem of Eq. 1 / Eq. 2 (Ising Hamiltonian and local field).
+ *   out      receives the new handle (set to NULL on failure).
+ *   n        number of spins, 1 <= n <= 256 for the fused kernel path.
+ *   j_type   element type of J (pim_j_type).
+ *   J        host, row-major n x n; must be symmetric with a zero diagonal.
+ *   h        host bias, n entries: int32 when j_type == PIM_J_INT8, else the float type
+ *            of J; NULL means h = 0.
+ *   scale_c  coupling scale c > 0 applied after the multiply-accumulate (the paper's
+ *            2/sqrt(N) for Max-Cut, 1/sqrt(N) for SK-1): the activation sees beta_t*c*I.
+ *            Energies are reported in unscaled units of J and h.
+ * Errors: PIM_ERR_INVALID (n out of range, J asymmetric, diagonal non-zero, |J| > 16,
+ *         scale_c <= 0 or not finite), PIM_ERR_UNSUPPORTED (real-valued J),
+ *         PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_create(pim_instance** out, int n, int j_type, const void* J, const void* h,
+               double scale_c);
+
+/*
+ * pim_set_schedule -- annealing schedule of Eq. 4 (beta(t), eta(t), xi).
+ * Schedule section of the supplementary PIMI implementation (inverse-temperature,
+ * noise and self-alignment paragraphs); the schedule values are inputs here.
+ *   steps      number of schedule entries T >= 1; anneals use steps [t_begin, t_end).
+ *   beta, eta  host float arrays of `steps` entries; beta >= 0, eta >= 0, finite.
+ *   xi         inertia (self-alignment) strength, finite, >= 0.
+ *   noise_kind pim_noise;  act_kind pim_act;  lut_levels L >= 2 (used by PIM_ACT_LUT).
+ * Builds, for every step t, the exact decision thresholds of the float32 rule
+ *   delta = (tau_t(I) + xi s) + eta_t z(m),  s' = +1 iff delta >= 0,
+ * with tau_t(I) = fl32(tanh(fl32(beta_t c) * I)) and z(m) one of 4096 noise levels
+ * selected by a 12-bit key m from the Philox stream.  Threshold tables are shared
+ * between instances with the same (schedule, c, field range).
+ * Errors: PIM_ERR_INVALID, PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_set_schedule(pim_instance* inst, int steps, const float* beta, const float* eta,
+                     float xi, int noise_kind, int act_kind, int lut_levels);
+
+/*
+ * pim_anneal -- run sweeps t_begin .. t_begin+sweeps-1 of Eq. 4 on `replicas` replicas.
+ * Box 1 (PIMI loop) and the supplementary algorithm "Fully unrolled PIMI update".
+ *   replicas      R >= 1 independent trials.
+ *   t_begin       first schedule step (0 for a fresh run); t_begin + sweeps <= steps.
+ *   sweeps        number of synchronous sweeps (>= 0).
+ *   seed          64-bit Philox key; draws use counter (i>>3, r, t, instance_id).
+ *   instance_id   counter word that separates instances sharing a seed.
+ *   init_spins    host int8 R x n of -1/+1, or NULL: Philox initial spins (bit 15 of the
+ *                 draw at step field 0xFFFFFFFF).  Ignored with PIM_CONTINUE.
+ *   target_energy first-hit threshold: records the first t with H(s(t)) <= target;
+ *                 NaN disables it.
+ *   flags         pim_flags.
+ *   cuda_stream   cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Records for every replica the minimum of H over s(t_begin) .. s(t_begin+sweeps)
+ * (earliest wins ties), its step and state, the first-hit step and the final state.
+ * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (no schedule; CONTINUE without a previous run
+ *         of the same R), PIM_ERR_UNSUPPORTED, PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_anneal(pim_instance* inst, int replicas, int t_begin, int sweeps, uint64_t seed,
+               uint32_t instance_id, const int8_t* init_spins, double target_energy,
+               int flags, void* cuda_stream);
+
+/*
+ * pim_anneal_batch -- one launch over many instances (the kernels of the paper process
+ * instances back to back; here all of them share one grid).
+ *   insts         `count` handles, each with a schedule set.
+ *   replicas      count entries, R_q >= 1.
+ *   t_begin, sweeps, seed, flags, cuda_stream  as pim_anneal, common to all instances.
+ *   instance_ids  count counter words, or NULL for 0 .. count-1.
+ *   targets       count first-hit targets, or NULL for none.
+ * Initial spins come from Philox (or the previous state with PIM_CONTINUE).
+ * Errors: as pim_anneal.
+ */
+int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas, int t_begin,
+                     int sweeps, uint64_t seed, const uint32_t* instance_ids,
+                     const double* targets, int flags, void* cuda_stream);
+
+/* pim_sync -- block until the instance's last anneal has finished.
+ * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up). */
+int pim_sync(pim_instance* inst);
+
+/*
+ * pim_energies -- per-replica results of the last anneal (host outputs, R entries each;
+ * any pointer may be NULL).  Synchronises first.
+ *   best_E       minimum energy H over the visited states (Eq. 1, unscaled units).
+ *   best_t       step t of the state that reached best_E.
+ *   first_hit_t  first step with H <= target, or -1.
+ *   final_E      H of the final state s(t_begin + sweeps).
+ * Errors: PIM_ERR_STATE (no anneal yet), PIM_ERR_CUDA, PIM_ERR_TIMEOUT.
+ */
+int pim_energies(pim_instance* inst, double* best_E, int32_t* best_t, int32_t* first_hit_t,
+                 double* final_E);
+
+/* pim_best_state / pim_final_state -- host int8 R x n of -1/+1.  Synchronises first.
+ * Errors: PIM_ERR_STATE, PIM_ERR_CUDA, PIM_ERR_TIMEOUT. */
+int pim_best_state(pim_instance* inst, int8_t* out);
+int pim_final_state(pim_instance* inst, int8_t* out);
+
+/* pim_replicas -- R of the last anneal (0 before the first). */
+int pim_replicas(const pim_instance* inst);
+
+/*
+ * pim_kernel_ms -- device time, in milliseconds, of the sweep kernel launch(es) of the
+ * instance's last anneal (all sweeps plus the final energy evaluation; staging and initial
+ * spins excluded), measured with CUDA events recorded on the launching stream around the
+ * launch.  Synchronises first.  With PIM_PATH_FP32REF it covers all the per-sweep kernels.
+ * Errors: PIM_ERR_STATE (no anneal yet), PIM_ERR_CUDA.
+ */
+int pim_kernel_ms(pim_instance* inst, float* ms);
+
+/*
+ * pim_submit / pim_poll -- asynchronous anneal on the library's own stream.
+ * pim_submit enqueues pim_anneal(inst, replicas, 0, sweeps, seed, 0, NULL, NaN, 0) and
+ * returns a ticket; pim_poll returns PIM_PENDING while it runs, PIM_OK when done, or an
+ * error.  A ticket is valid until the instance is destroyed or re-submitted.
+ * Errors: as pim_anneal; pim_poll: PIM_ERR_INVALID for an unknown ticket.
+ */
+int pim_submit(pim_instance* inst, int replicas, int sweeps, uint64_t seed, uint64_t* ticket);
+int pim_poll(uint64_t ticket);
+
+/* pim_destroy -- free the instance and its device memory (NULL is a no-op).  Waits for
+ * its pending work first. */
+void pim_destroy(pim_instance* inst);
+
+/* pim_last_error -- thread-local description of the last failure ("" if none). */
+const char* pim_last_error(void);
+
+/*
+ * Inspection entry points (host only; no GPU needed).
+ * pim_noise_levels -- the 4096 float32 noise levels z(m) the decision tables use:
+ *   Gaussian: z(m) = fl32(Phi^-1((m+0.5)/4096)) for m < 2048 and z(4095-m) = -z(m);
+ *   uniform:  z(m) = (2m - 4095)/4096.
+ * pim_activation_levels -- tau_t(I) for I = -imax .. imax (2*imax+1 floats) for one b_t:
+ *   tanh: fl32(tanh(b_t * I)) evaluated in float64; LUT: Algorithm "LUT-based tanh
+ *   approximation" with L = lut_levels.
+ * Errors: PIM_ERR_INVALID.
+ */
+int pim_noise_levels(int noise_kind, float* out4096);
+int pim_activation_levels(float b_t, int imax, int act_kind, int lut_levels, float* out);
+
+/*
+ * pim_thresholds -- copy the device decision table of the instance's schedule to the
+ * host: for every step t and field I = -imax..imax a uint32 word whose low half is the
+ * least key m with a +1 decision when s_i(t) = -1 and whose high half is the same for
+ * s_i(t) = +1 (4096 = never).  Layout [steps][stride_words]; entry I is at index
+ * I + imax.  `*steps`, `*imax` and `*stride_words` are returned when non-NULL; `out` may
+ * be NULL to query the sizes only.
+ * Errors: PIM_ERR_STATE (no schedule), PIM_ERR_INVALID (cap too small), PIM_ERR_CUDA.
+ */
+int pim_thresholds(pim_instance* inst, uint32_t* out, size_t cap_words, int* steps, int* imax,
+                   int* stride_words);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIM_H */

@@ -1,0 +1,70 @@
+// Host-side constant tables of the decision rule: the 4096 noise levels z(m) and the
+// activation values tau_t(I).  These are the only transcendental evaluations of the
+// library; everything per sweep runs on the device from integer tables built from them.
+#include "host_tables.h"
+
+#include <cmath>
+#include <cstdint>
+
+namespace pim {
+
+// Standard normal CDF through the complementary error function of the C library:
+// Phi(x) = erfc(-x / sqrt 2) / 2, accurate in the lower tail where it is used.
+static double normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+// Phi^-1(p) for 0 < p < 1/2 by bisection on Phi over [-40, 0] until the bracket stops
+// shrinking, then the bracket end whose CDF is closer to p.  Phi is strictly increasing,
+// so the bracket always holds the root; the result is within a few units in the last
+// place of double, far below the float32 rounding applied afterwards.
+static double normal_quantile_lower(double p) {
+  double lo = -40.0, hi = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (normal_cdf(mid) < p)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return (std::fabs(normal_cdf(lo) - p) <= std::fabs(normal_cdf(hi) - p)) ? lo : hi;
+}
+
+void noise_levels(int kind, float* out) {
+  if (kind == 0) {  // Gaussian quantiles, exactly antisymmetric
+    for (int m = 0; m < kNoiseLevels / 2; ++m) {
+      const double p = (m + 0.5) / kNoiseLevels;
+      const float v = static_cast<float>(normal_quantile_lower(p));
+      out[m] = v;
+      out[kNoiseLevels - 1 - m] = -v;
+    }
+  } else {  // uniform grid (2m - 4095) / 4096
+    for (int m = 0; m < kNoiseLevels; ++m)
+      out[m] = static_cast<float>((2.0 * m - (kNoiseLevels - 1)) / kNoiseLevels);
+  }
+}
+
+// L-level staircase on [-1, 1]: output levels -1 + 2k/(L-1), input breakpoints
+// -1 + 2k/L; saturates outside [-1, 1].
+static double staircase(double x, int levels) {
+  if (x < -1.0) return -1.0;
+  if (x > 1.0) return 1.0;
+  int k = 0;
+  for (int kk = 1; kk < levels; ++kk)
+    if (x >= -1.0 + 2.0 * kk / levels) k = kk;
+  return -1.0 + 2.0 * k / (levels - 1);
+}
+
+void activation_levels(float b_t, int imax, int act, int lut_levels, float* out) {
+  const double b = static_cast<double>(b_t);
+  for (int I = -imax; I <= imax; ++I) {
+    const double x = b * static_cast<double>(I);  // exact: 24-bit b times |I| < 2^20
+    const double tau = (act == 0) ? std::tanh(x) : staircase(x, lut_levels);
+    out[I + imax] = static_cast<float>(tau);
+  }
+}
+
+float scaled_beta(float beta, double c) {
+  return static_cast<float>(static_cast<double>(beta) * c);
+}
+
+}  // namespace pim

@@ -1,0 +1,144 @@
+// Staging kernels: coupling images, decision thresholds and initial spins.
+#include <cuda_fp8.h>
+
+#include "kernels.h"
+#include "philox.cuh"
+
+namespace pim {
+
+// ---------------------------------------------------------------------------------------
+// J (int8, row-major n x n) -> FP8 E4M3 operand image of the fused kernel.  The image is
+// the K-major layout in which the MMA reads the B operand: row i (output spin), K = j,
+// value J_ij; zero outside n x n.  One thread per image byte.
+// ---------------------------------------------------------------------------------------
+__global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int npad,
+                                       uint8_t* __restrict__ img) {
+  const uint32_t off = blockIdx.x * blockDim.x + threadIdx.x;
+  if (off >= static_cast<uint32_t>(npad) * npad) return;
+  const uint32_t block_bytes = static_cast<uint32_t>(npad) * 128u;
+  const int kb = off / block_bytes;
+  const uint32_t rem = off % block_bytes;
+  const int i = (rem >> 10) * 8 + ((rem & 1023) >> 7);
+  const int within = rem & 127;
+  const int chunk = (within >> 4) ^ (i & 7);
+  const int j = kb * 128 + chunk * 16 + (within & 15);
+  uint8_t v = 0;
+  if (i < n && j < n) {
+    const __nv_fp8_storage_t e =
+        __nv_cvt_float_to_fp8(static_cast<float>(J[static_cast<size_t>(i) * n + j]),
+                              __NV_SATFINITE, __NV_E4M3);
+    v = static_cast<uint8_t>(e);
+  }
+  img[off] = v;
+}
+
+cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+                                   cudaStream_t st) {
+  const uint32_t total = static_cast<uint32_t>(npad) * npad;
+  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, d_img);
+  return cudaGetLastError();
+}
+
+__global__ void stage_f32_kernel(const int8_t* __restrict__ J, int n, float* __restrict__ jf) {
+  const size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < static_cast<size_t>(n) * n) jf[k] = static_cast<float>(J[k]);
+}
+
+cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st) {
+  const size_t total = static_cast<size_t>(n) * n;
+  stage_f32_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(d_J, n, d_jf);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Decision thresholds.  For step t, field I and current spin s the float32 rule
+//   a = tau_t(I) + (s>0 ? xi : -xi);   delta(m) = a + eta_t * z(m);   s' = +1 iff delta >= 0
+// is non-decreasing in the key m (z is increasing, both roundings are monotone), so it is
+// exactly "m >= M" with M the least key giving delta >= 0 (4096 = never).  Each thread
+// finds M for one (t, I) and both s by bisection, with explicitly rounded float32
+// operations (no contraction into FMA).  Word = M(s=-1) | M(s=+1) << 16.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t least_up_key(float a, float eta, const float* z) {
+  int lo = 0, hi = 4096;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float delta = __fadd_rn(a, __fmul_rn(eta, z[mid]));
+    if (delta >= 0.0f)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return static_cast<uint32_t>(lo);
+}
+
+__global__ void thresholds_kernel(const float* __restrict__ tau, const float* __restrict__ eta,
+                                  const float* __restrict__ z, float xi, int imax,
+                                  int stride_words, uint32_t* __restrict__ thr) {
+  __shared__ float zs[4096];
+  for (int k = threadIdx.x; k < 4096; k += blockDim.x) zs[k] = z[k];
+  __syncthreads();
+  const int t = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int width = 2 * imax + 1;
+  if (idx >= stride_words) return;
+  uint32_t word = 0;
+  if (idx < width) {
+    const float tv = tau[static_cast<size_t>(t) * width + idx];
+    const float e = eta[t];
+    const uint32_t m_down = least_up_key(__fadd_rn(tv, -xi), e, zs);
+    const uint32_t m_up = least_up_key(__fadd_rn(tv, xi), e, zs);
+    word = m_down | (m_up << 16);
+  }
+  thr[static_cast<size_t>(t) * stride_words + idx] = word;
+}
+
+cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const float* d_z,
+                              float xi, int steps, int imax, int stride_words,
+                              uint32_t* d_thr, cudaStream_t st) {
+  dim3 grid((stride_words + 127) / 128, steps);
+  thresholds_kernel<<<grid, 128, 0, st>>>(d_tau, d_eta, d_z, xi, imax, stride_words, d_thr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Initial spin bits.  Philox mode: spin i of replica r is +1 iff bit 15 of its draw at
+// step field 0xFFFFFFFF is set.  Host mode: pack int8 +-1 (d_init[R][n], instance 0 only).
+// Grid: x = word, y = replica, z = problem.
+// ---------------------------------------------------------------------------------------
+__global__ void init_bits_kernel(const Problem* __restrict__ probs, const int8_t* __restrict__ init,
+                                 uint32_t key_lo, uint32_t key_hi) {
+  const Problem& P = probs[blockIdx.z];
+  const int r = blockIdx.y * blockDim.y + threadIdx.y;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.R || w >= P.words) return;
+  uint32_t bits = 0;
+  if (init != nullptr) {
+    for (int b = 0; b < 32; ++b) {
+      const int i = w * 32 + b;
+      if (i < P.n && init[static_cast<size_t>(r) * P.n + i] > 0) bits |= 1u << b;
+    }
+  } else {
+    for (int g = 0; g < 4; ++g) {
+      const int i0 = w * 32 + g * 8;
+      if (i0 >= P.n) break;
+      const PhiloxOut o = philox4x32_10(static_cast<uint32_t>(i0 >> 3), static_cast<uint32_t>(r),
+                                        0xFFFFFFFFu, P.q, key_lo, key_hi);
+      for (int k = 0; k < 8; ++k) {
+        const int i = i0 + k;
+        if (i < P.n && ((philox_half(o, k) >> 15) & 1u)) bits |= 1u << (g * 8 + k);
+      }
+    }
+  }
+  P.cur_bits[static_cast<size_t>(r) * P.words + w] = bits;
+}
+
+cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int max_words,
+                             const int8_t* d_init, uint32_t key_lo, uint32_t key_hi,
+                             cudaStream_t st) {
+  dim3 block(8, 32);
+  dim3 grid((max_words + 7) / 8, (maxR + 31) / 32, nprob);
+  init_bits_kernel<<<grid, block, 0, st>>>(d_probs, d_init, key_lo, key_hi);
+  return cudaGetLastError();
+}
+
+}  // namespace pim

@@ -1,0 +1,489 @@
+// Fused PIMI sweep kernel for sm_103a: tcgen05 field GEMM into TMEM, fused decision,
+// spin write-back and energy / best-state tracking, all sweeps of a replica tile inside one
+// CTA.
+//
+// Per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
+//   fields   D[r, i] = sum_j S[r, j] J[i, j]   (tcgen05.mma kind::f8f6f4, M = 128 replicas,
+//            N = n spins rounded up to 16, K in steps of 32; FP8 E4M3 operands hold the
+//            integer couplings and the +-1 spins exactly, FP32 accumulation is exact)
+//   energy   H(s(t)) = -1/2 sum_i s_i (I_i + h_i) from the same fields (Eq. 1)
+//   decision s_i(t+1) = +1 iff key(i, r, t) >= M_t[s_i(t)][I_i], the threshold form of the
+//            float32 rule tau_t(I) + xi s + eta_t z(key) >= 0 (Eq. 4)
+//   write    s(t+1) back into the shared-memory A operand, then the next sweep's MMA.
+// The GEMM is transposed with respect to the paper's J s: TMEM lane = replica, column =
+// spin, so that one thread owns one replica row and the energy of that replica is a
+// thread-local sum (plus one partner thread that holds the other half of the columns).
+#include <climits>
+
+#include "kernels.h"
+#include "philox.cuh"
+
+namespace pim {
+namespace {
+
+constexpr int kThreads = 256;   // 8 warps: 4 TMEM lane quadrants x 2 column halves
+constexpr int kTileM = 128;     // replicas per CTA (MMA M)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity; gives up after ~2 s and returns false.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand with 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), leading byte offset unused by swizzled K-major layouts.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f8f6f4: D = F32, A = B = E4M3, both K-major.
+__device__ __forceinline__ uint32_t idesc_e4m3(int m, int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Four spins (bits of `nib`) -> four FP8 E4M3 bytes: +1 = 0x38, -1 = 0xB8.
+__device__ __forceinline__ uint32_t fp8x4_from_bits(uint32_t nib) {
+  return 0xB8B8B8B8u ^ (((nib * 0x00204081u) & 0x01010101u) * 0x80u);
+}
+
+// The integer value I of an exactly integral float f (|f| < 2^22) appears in the low
+// mantissa bits of f + 1.5 * 2^23.
+constexpr float kMagic = 12582912.0f;
+constexpr int kMagicBits = 0x4B400000;
+
+template <int NPAD, bool HAS_H>
+__global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
+  constexpr int kMaxSlots = NPAD / 32;  // 16-column chunks per column half
+  constexpr int kWordsPerThread = kMaxSlots / 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int SW = L.stride_words_max;
+  uint8_t* sJ = smem;
+  uint8_t* sA = sJ + NPAD * NPAD;
+  uint32_t* sT = reinterpret_cast<uint32_t*>(sA + kTileM * NPAD);
+  int* sPart = reinterpret_cast<int*>(sT + 2 * SW);
+  int* sH = sPart + 2 * 2 * kTileM;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + (HAS_H ? NPAD : 0));
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2);
+  int* sAbort = reinterpret_cast<int*>(sTmem + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+
+  const WorkItem wk = L.work[blockIdx.x];
+  const Problem& P = L.probs[wk.prob];
+  const int n = P.n;
+  const int imax = P.imax;
+  const int stride = P.stride_words;
+  const int R = P.R;
+  const uint32_t q = P.q;
+  const int rg = wk.rbase + row;
+  const bool row_valid = rg < R;
+  const bool warp_active = (wk.rbase + quad * 32) < R;
+  const int nch = (n + 15) >> 4;
+  const int split = (nch + 1) >> 1;
+  const int c0 = half == 0 ? 0 : split;
+  const int myc = half == 0 ? split : nch - split;
+  const int ksteps = (n + 31) >> 5;
+  const int mma_n = (n + 15) & ~15;
+  const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
+  const uint32_t bar_mma = smem_u32(&bars[0]);
+  const uint32_t bar_j = smem_u32(&bars[1]);
+
+  // ---- prologue: TMEM, barriers, zeroed A operand, bias, first threshold table --------
+  if (warp == 0) {
+    tmem_alloc(smem_u32(sTmem), NPAD);
+    tmem_relinquish();
+  }
+  if (tid == 32) {
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_j, 1);
+    fence_mbar_init();
+    *sAbort = 0;
+  }
+  for (int k = tid; k < kTileM * NPAD / 16; k += kThreads)
+    reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
+  if (HAS_H)
+    for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.h != nullptr && k < n) ? P.h[k] : 0;
+  if (L.sweeps > 0) {
+    const uint4* src = reinterpret_cast<const uint4*>(P.thr + static_cast<size_t>(t_begin) * stride);
+    uint4* dst = reinterpret_cast<uint4*>(sT + (t_begin & 1) * SW);
+    for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t tmem_warp = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+
+  if (tid == 0) {
+    constexpr uint32_t kJBytes = NPAD * NPAD;
+    mbar_expect_tx(bar_j, kJBytes);
+    for (uint32_t off = 0; off < kJBytes; off += 16384)
+      bulk_g2s(smem_u32(sJ + off), P.jimg + off, 16384u < kJBytes - off ? 16384u : kJBytes - off,
+               bar_j);
+  }
+
+  // ---- per-thread replica state: 16-bit spin chunks of this thread's column half ------
+  uint32_t cur[kWordsPerThread], best[kWordsPerThread];
+  const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
+#pragma unroll
+  for (int w = 0; w < kWordsPerThread; ++w) cur[w] = 0;
+  if (row_valid) {
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) {
+        const uint32_t v = cur_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)];
+        cur[k >> 1] |= v << ((k & 1) * 16);
+      }
+  }
+  int best_E = INT_MAX, best_t = -1, first_hit = -1;
+  const long long target = P.target;
+  const bool has_target = P.has_target != 0;
+  if (L.cont && row_valid) {
+    best_E = static_cast<int>(P.best_E[rg]);
+    best_t = P.best_t[rg];
+    first_hit = P.first_hit[rg];
+    const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) best[w] = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) {
+        const uint32_t v = best_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)];
+        best[k >> 1] |= v << ((k & 1) * 16);
+      }
+  } else {
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+  }
+
+  // Write s(t_begin) into the A operand (row = replica, K = spin).
+  if (warp_active) {
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) {
+        const int c = c0 + k;
+        const uint32_t nb = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+        const uint4 bytes = make_uint4(fp8x4_from_bits(nb & 0xF), fp8x4_from_bits((nb >> 4) & 0xF),
+                                       fp8x4_from_bits((nb >> 8) & 0xF), fp8x4_from_bits(nb >> 12));
+        *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = bytes;
+      }
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  const uint32_t idesc = idesc_e4m3(kTileM, mma_n);
+  const uint32_t sA_addr = smem_u32(sA), sJ_addr = smem_u32(sJ);
+  auto issue_fields = [&]() {
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
+      mma_e4m3(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
+               sw128_desc(sJ_addr + kb * (NPAD * 128) + ko), idesc, ks > 0 ? 1u : 0u);
+    }
+    mma_commit(bar_mma);
+  };
+
+  if (tid == 0) {
+    if (!mbar_wait_bounded(bar_j, 0)) {
+      atomicOr(L.err, kDevErrTimeout);
+      *sAbort = 1;
+    } else {
+      tc_fence_after();
+      issue_fields();
+    }
+  }
+  __syncthreads();
+  bool aborted = *sAbort != 0;
+  uint32_t phase = 0;
+  const uint32_t ioff = static_cast<uint32_t>(kMagicBits - imax);
+  const uint32_t imax2 = static_cast<uint32_t>(2 * imax);
+
+  // ---- sweep loop ----------------------------------------------------------------------
+  for (int t = t_begin; t < t_end && !aborted; ++t) {
+    if (!mbar_wait_bounded(bar_mma, phase)) {
+      atomicOr(L.err, kDevErrTimeout);
+      *sAbort = 1;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    if (t + 1 < t_end) {  // stage the next step's thresholds (read after this sweep's barrier)
+      const uint4* src = reinterpret_cast<const uint4*>(P.thr + static_cast<size_t>(t + 1) * stride);
+      uint4* dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
+      for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
+    }
+    const uint32_t* tab = sT + (t & 1) * SW;
+    uint32_t nxt[kWordsPerThread];
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
+    int eacc = 0;
+    if (warp_active) {
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k) {
+        if (k < myc) {
+          const int c = c0 + k;
+          uint32_t v[16];
+          tmem_ld16(tmem_warp + c * 16, v);
+          tmem_wait_ld();
+          const PhiloxOut o0 = philox4x32_10(2u * c, static_cast<uint32_t>(rg),
+                                             static_cast<uint32_t>(t), q, L.key_lo, L.key_hi);
+          const PhiloxOut o1 = philox4x32_10(2u * c + 1u, static_cast<uint32_t>(rg),
+                                             static_cast<uint32_t>(t), q, L.key_lo, L.key_hi);
+          const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+          const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+          uint32_t nb = 0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            int ib = __float_as_int(__fadd_rn(__uint_as_float(v[e]), kMagic));
+            int hv = 0;
+            if (HAS_H) {
+              hv = sH[c * 16 + e];
+              ib += hv;
+            }
+            const uint32_t idx = min(static_cast<uint32_t>(ib) - ioff, imax2);
+            const uint32_t w = tab[idx];
+            const uint32_t s = (ob >> e) & 1u;
+            const uint32_t thr = s ? (w >> 16) : (w & 0xFFFFu);
+            const uint32_t word = rw[e >> 1];
+            const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+            nb |= (key >= thr ? 1u : 0u) << e;
+            const int term = ib - kMagicBits + hv;
+            eacc += s ? term : -term;
+          }
+          const int valid = n - c * 16;
+          if (valid < 16) nb &= (1u << valid) - 1u;
+          nxt[k >> 1] |= nb << ((k & 1) * 16);
+          const uint4 bytes = make_uint4(fp8x4_from_bits(nb & 0xF), fp8x4_from_bits((nb >> 4) & 0xF),
+                                         fp8x4_from_bits((nb >> 8) & 0xF), fp8x4_from_bits(nb >> 12));
+          *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = bytes;
+        }
+      }
+    }
+    sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    aborted = *sAbort != 0;
+    if (aborted) break;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_fields();  // fields of s(t+1)
+    }
+    const int etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    const int E = -(etot / 2);
+    if (E < best_E) {
+      best_E = E;
+      best_t = t;
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+    }
+    if (has_target && first_hit < 0 && E <= target) first_hit = t;
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) cur[w] = nxt[w];
+  }
+
+  // ---- energy of the final state s(t_end) ---------------------------------------------
+  if (!aborted) {
+    if (!mbar_wait_bounded(bar_mma, phase)) {
+      atomicOr(L.err, kDevErrTimeout);
+      *sAbort = 1;
+    }
+    tc_fence_after();
+    int eacc = 0;
+    if (warp_active) {
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k) {
+        if (k < myc) {
+          const int c = c0 + k;
+          uint32_t v[16];
+          tmem_ld16(tmem_warp + c * 16, v);
+          tmem_wait_ld();
+          const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            int term = __float_as_int(__fadd_rn(__uint_as_float(v[e]), kMagic)) - kMagicBits;
+            if (HAS_H) term += 2 * sH[c * 16 + e];
+            eacc += ((ob >> e) & 1u) ? term : -term;
+          }
+        }
+      }
+    }
+    sPart[(t_end & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    tc_fence_before();
+    __syncthreads();
+    aborted = *sAbort != 0;
+    const int etot = eacc + sPart[(t_end & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    const int E = -(etot / 2);
+    if (E < best_E) {
+      best_E = E;
+      best_t = t_end;
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+    }
+    if (has_target && first_hit < 0 && E <= target) first_hit = t_end;
+    if (row_valid && !aborted) {
+      uint16_t* cur_out = reinterpret_cast<uint16_t*>(P.cur_bits);
+      uint16_t* best_out = reinterpret_cast<uint16_t*>(P.best_bits);
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k)
+        if (k < myc) {
+          const size_t o = static_cast<size_t>(rg) * P.words * 2 + (c0 + k);
+          cur_out[o] = static_cast<uint16_t>(cur[k >> 1] >> ((k & 1) * 16));
+          best_out[o] = static_cast<uint16_t>(best[k >> 1] >> ((k & 1) * 16));
+        }
+      if (half == 0) {
+        P.best_E[rg] = static_cast<double>(best_E);
+        P.best_t[rg] = best_t;
+        P.first_hit[rg] = first_hit;
+        P.final_E[rg] = static_cast<double>(E);
+      }
+    }
+  } else if (tid == 0) {
+    // An earlier wait gave up: give the in-flight MMA a bounded chance to land before the
+    // tensor memory is released.
+    mbar_wait_bounded(bar_mma, phase);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NPAD);
+}
+
+template <int NPAD, bool HAS_H>
+cudaError_t launch_variant(const Launch& L, int blocks, cudaStream_t st) {
+  const int smem = sweep_tc_smem_bytes(NPAD, L.stride_words_max) + (HAS_H ? NPAD * 4 : 0);
+  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel<NPAD, HAS_H>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  sweep_tc_kernel<NPAD, HAS_H><<<blocks, kThreads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int sweep_tc_smem_bytes(int npad, int stride_words_max) {
+  return 1024 /* alignment slack */ + npad * npad + kTileM * npad + 2 * stride_words_max * 4 +
+         2 * 2 * kTileM * 4 + 64;
+}
+
+cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
+                            bool has_h) {
+  if (npad_max <= 128)
+    return has_h ? launch_variant<128, true>(L, blocks, st) : launch_variant<128, false>(L, blocks, st);
+  return has_h ? launch_variant<256, true>(L, blocks, st) : launch_variant<256, false>(L, blocks, st);
+}
+
+}  // namespace pim

@@ -1,0 +1,45 @@
+// Launch functions of the device kernels (host side, internal to the library).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pim_device.cuh"
+
+namespace pim {
+
+// Byte offset of element (row, k) inside a K-major, 128-byte-swizzled operand image with
+// `rows` rows: K-blocks of 128 bytes, each block rows x 128 bytes, 8-row atoms of 1024
+// bytes, 16-byte chunk index XOR-ed with (row % 8).
+__host__ __device__ inline uint32_t sw128_offset(int row, int k, int rows) {
+  const int kb = k >> 7;
+  const int chunk = (k & 127) >> 4;
+  return static_cast<uint32_t>(kb) * rows * 128u + (row >> 3) * 1024u + (row & 7) * 128u +
+         ((chunk ^ (row & 7)) << 4) + (k & 15);
+}
+
+// Staging (once per instance).
+cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+                                   cudaStream_t st);
+cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st);
+
+// Decision thresholds for all steps: tau [steps][2*imax+1], eta [steps], z [4096].
+cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const float* d_z,
+                              float xi, int steps, int imax, int stride_words,
+                              uint32_t* d_thr, cudaStream_t st);
+
+// Initial spin bits: from Philox (d_init == nullptr) or from int8 +-1 spins [R][n].
+cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int max_words,
+                             const int8_t* d_init, uint32_t key_lo, uint32_t key_hi,
+                             cudaStream_t st);
+
+// Fused tensor-core sweep kernel (n <= 256).
+cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
+                            bool has_h);
+int sweep_tc_smem_bytes(int npad, int stride_words_max);
+
+// Plain FP32 comparator path: per sweep one field GEMM and one update kernel.
+cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, int nprob,
+                              int t_begin, int sweeps, uint32_t key_lo, uint32_t key_hi,
+                              int cont, float* d_S, float* d_I, int* d_err, cudaStream_t st);
+
+}  // namespace pim

@@ -1,0 +1,53 @@
+// Device-visible launch descriptors shared by the runtime and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pim {
+
+// Device error bits, OR-ed into the launch's error word.
+enum : int {
+  kDevErrTimeout = 1,      // a bounded mbarrier wait gave up
+  kDevErrFieldRange = 2,   // a field fell outside the threshold table (cannot happen for
+                           // a valid instance; checked so a bad table never reads out of range)
+};
+
+// Per-instance parameters of one launch.  All pointers are device pointers.
+struct Problem {
+  const uint8_t* jimg;     // FP8 E4M3 couplings, npad x npad, 128B-swizzled K-major image
+  const float* jf;         // float32 row-major n x n (plain path)
+  const int32_t* h;        // int32 bias or nullptr
+  const uint32_t* thr;     // decision thresholds [steps][stride_words]
+  double* best_E;          // [R]
+  double* final_E;         // [R]
+  int32_t* best_t;         // [R]
+  int32_t* first_hit;      // [R]
+  uint32_t* best_bits;     // [R][words]   bit i of word i/32 set <=> spin i = +1
+  uint32_t* cur_bits;      // [R][words]   state in / state out
+  int n, npad, words;
+  int imax, stride_words;
+  int R;
+  uint32_t q;              // instance counter word of the noise stream
+  int has_target;
+  long long target;        // first-hit when energy <= target (integer couplings)
+};
+
+// One unit of work of the fused sweep kernel: (problem index, first replica).
+struct WorkItem {
+  int prob;
+  int rbase;
+};
+
+struct Launch {
+  const Problem* probs;
+  const WorkItem* work;
+  int nwork;
+  int t_begin;
+  int sweeps;
+  uint32_t key_lo, key_hi;
+  int cont;                // 1: keep previous best / first-hit records
+  int stride_words_max;    // largest table stride among the problems (smem sizing)
+  int* err;                // device error word
+};
+
+}  // namespace pim

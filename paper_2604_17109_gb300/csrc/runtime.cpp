@@ -1,0 +1,668 @@
+// Host runtime of the C ABI declared in include/pim.h: argument checking, device memory,
+// schedule tables, launch assembly and result copies.  Every sweep of the method runs in
+// the device kernels; this file only stages inputs and moves results.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host_tables.h"
+#include "kernels.h"
+#include "pim.h"
+
+#define PIM_API extern "C" __attribute__((visibility("default")))
+
+using namespace pim;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? PIM_ERR_NOMEM : PIM_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+  } while (0)
+
+constexpr int kMaxN = 8192;        // plain path limit
+constexpr int kMaxNTensor = 256;   // fused kernel limit
+constexpr int kMaxImaxTensor = 511;
+
+// Decision thresholds of one (schedule, c, field range), shared between instances.
+struct Schedule {
+  int steps = 0;
+  int imax = 0;          // table covers I = -imax .. imax
+  int stride_words = 0;  // per-step stride, multiple of 4 words (16 bytes)
+  uint32_t* d_thr = nullptr;
+  int device = 0;
+  ~Schedule() {
+    if (d_thr) {
+      int prev = 0;
+      cudaGetDevice(&prev);
+      cudaSetDevice(device);
+      cudaFree(d_thr);
+      cudaSetDevice(prev);
+    }
+  }
+};
+
+std::mutex g_sched_mu;
+std::map<std::string, std::weak_ptr<Schedule>> g_sched_cache;
+
+// Per-device error word written by the kernels.
+std::mutex g_err_mu;
+std::map<int, int*> g_err_word;
+
+int* device_error_word(int dev) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  auto it = g_err_word.find(dev);
+  if (it != g_err_word.end()) return it->second;
+  int* p = nullptr;
+  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+  cudaMemset(p, 0, sizeof(int));
+  g_err_word[dev] = p;
+  return p;
+}
+
+// CUDA events around one sweep-kernel launch, shared by the instances of that launch.
+struct LaunchTimer {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  ~LaunchTimer() {
+    if (start) cudaEventDestroy(start);
+    if (stop) cudaEventDestroy(stop);
+  }
+};
+
+}  // namespace
+
+struct pim_instance {
+  int device = 0;
+  int n = 0, npad = 0, words = 0;
+  double c = 1.0;
+  int imax = 0;  // exact max_i sum_j |J_ij| + |h_i|
+  bool has_h = false;
+  int8_t* d_J8 = nullptr;
+  uint8_t* d_img = nullptr;
+  float* d_jf = nullptr;
+  int32_t* d_h = nullptr;
+  std::shared_ptr<Schedule> sched;
+  // results of the last anneal
+  int R = 0, R_cap = 0;
+  double* d_bestE = nullptr;
+  double* d_finalE = nullptr;
+  int32_t* d_bestT = nullptr;
+  int32_t* d_first = nullptr;
+  uint32_t* d_best_bits = nullptr;
+  uint32_t* d_cur_bits = nullptr;
+  bool has_results = false;
+  cudaEvent_t done = nullptr;
+  uint64_t ticket = 0;
+  std::shared_ptr<LaunchTimer> timer;
+};
+
+namespace {
+
+void free_results(pim_instance* p) {
+  cudaFree(p->d_bestE);
+  cudaFree(p->d_finalE);
+  cudaFree(p->d_bestT);
+  cudaFree(p->d_first);
+  cudaFree(p->d_best_bits);
+  cudaFree(p->d_cur_bits);
+  p->d_bestE = p->d_finalE = nullptr;
+  p->d_bestT = p->d_first = nullptr;
+  p->d_best_bits = p->d_cur_bits = nullptr;
+  p->R_cap = 0;
+}
+
+int ensure_results(pim_instance* p, int R) {
+  if (R <= p->R_cap) return PIM_OK;
+  if (p->done) CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
+  free_results(p);
+  const size_t bits = static_cast<size_t>(R) * p->words * sizeof(uint32_t);
+  CK(cudaMalloc(&p->d_bestE, R * sizeof(double)), "cudaMalloc results");
+  CK(cudaMalloc(&p->d_finalE, R * sizeof(double)), "cudaMalloc results");
+  CK(cudaMalloc(&p->d_bestT, R * sizeof(int32_t)), "cudaMalloc results");
+  CK(cudaMalloc(&p->d_first, R * sizeof(int32_t)), "cudaMalloc results");
+  CK(cudaMalloc(&p->d_best_bits, bits), "cudaMalloc results");
+  CK(cudaMalloc(&p->d_cur_bits, bits), "cudaMalloc results");
+  p->R_cap = R;
+  return PIM_OK;
+}
+
+int check_device_errors(int dev) {
+  int* w = device_error_word(dev);
+  if (!w) return PIM_OK;
+  int h = 0;
+  CK(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost), "reading device error word");
+  if (h != 0) {
+    cudaMemset(w, 0, sizeof(int));
+    if (h & kDevErrTimeout) return fail(PIM_ERR_TIMEOUT, "a device-side bounded wait gave up");
+    return fail(PIM_ERR_CUDA, "device error bits 0x%x", h);
+  }
+  return PIM_OK;
+}
+
+int sync_instance(pim_instance* p) {
+  if (p->done) CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
+  return check_device_errors(p->device);
+}
+
+std::string schedule_key(int steps, const float* beta, const float* eta, float xi, int noise,
+                         int act, int lut, double c, int imax, int device) {
+  std::string k;
+  auto put = [&](const void* d, size_t b) { k.append(static_cast<const char*>(d), b); };
+  put(&steps, sizeof steps);
+  put(&xi, sizeof xi);
+  put(&noise, sizeof noise);
+  put(&act, sizeof act);
+  put(&lut, sizeof lut);
+  put(&c, sizeof c);
+  put(&imax, sizeof imax);
+  put(&device, sizeof device);
+  put(beta, steps * sizeof(float));
+  put(eta, steps * sizeof(float));
+  return k;
+}
+
+int build_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
+                   const float* eta, float xi, int noise, int act, int lut, double c, int imax,
+                   int device) {
+  auto s = std::make_shared<Schedule>();
+  s->steps = steps;
+  s->imax = imax;
+  s->device = device;
+  const int width = 2 * imax + 1;
+  s->stride_words = (width + 3) & ~3;
+  std::vector<float> tau(static_cast<size_t>(steps) * width);
+  for (int t = 0; t < steps; ++t)
+    activation_levels(scaled_beta(beta[t], c), imax, act, lut, &tau[static_cast<size_t>(t) * width]);
+  std::vector<float> z(kNoiseLevels);
+  noise_levels(noise == PIM_NOISE_GAUSS ? 0 : 1, z.data());
+  float *d_tau = nullptr, *d_eta = nullptr, *d_z = nullptr;
+  cudaStream_t st = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_tau);
+    cudaFree(d_eta);
+    cudaFree(d_z);
+    if (st) cudaStreamDestroy(st);
+  };
+  auto ck = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return PIM_OK;
+    cleanup();
+    return cuda_fail(e, what);
+  };
+  int rc;
+  if ((rc = ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate"))) return rc;
+  if ((rc = ck(cudaMalloc(&s->d_thr, static_cast<size_t>(steps) * s->stride_words * 4),
+               "cudaMalloc thresholds")))
+    return rc;
+  if ((rc = ck(cudaMalloc(&d_tau, tau.size() * 4), "cudaMalloc tau"))) return rc;
+  if ((rc = ck(cudaMalloc(&d_eta, steps * 4), "cudaMalloc eta"))) return rc;
+  if ((rc = ck(cudaMalloc(&d_z, kNoiseLevels * 4), "cudaMalloc z"))) return rc;
+  if ((rc = ck(cudaMemcpyAsync(d_tau, tau.data(), tau.size() * 4, cudaMemcpyHostToDevice, st),
+               "upload tau")))
+    return rc;
+  if ((rc = ck(cudaMemcpyAsync(d_eta, eta, steps * 4, cudaMemcpyHostToDevice, st), "upload eta")))
+    return rc;
+  if ((rc = ck(cudaMemcpyAsync(d_z, z.data(), kNoiseLevels * 4, cudaMemcpyHostToDevice, st),
+               "upload z")))
+    return rc;
+  if ((rc = ck(launch_thresholds(d_tau, d_eta, d_z, xi, steps, imax, s->stride_words, s->d_thr, st),
+               "threshold kernel")))
+    return rc;
+  if ((rc = ck(cudaStreamSynchronize(st), "threshold build"))) return rc;
+  cleanup();
+  out = s;
+  return PIM_OK;
+}
+
+int table_imax(const pim_instance* p) {
+  // Round the exact field bound up to 64k-1 so instances of similar size share tables.
+  return p->imax | 63;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------------------
+PIM_API const char* pim_last_error(void) { return g_last_error.c_str(); }
+
+PIM_API int pim_noise_levels(int noise_kind, float* out4096) {
+  if (!out4096 || (noise_kind != PIM_NOISE_GAUSS && noise_kind != PIM_NOISE_UNIFORM))
+    return fail(PIM_ERR_INVALID, "pim_noise_levels: bad arguments");
+  noise_levels(noise_kind == PIM_NOISE_GAUSS ? 0 : 1, out4096);
+  return PIM_OK;
+}
+
+PIM_API int pim_activation_levels(float b_t, int imax, int act_kind, int lut_levels, float* out) {
+  if (!out || imax < 0 || !std::isfinite(b_t) || (act_kind != PIM_ACT_TANH && act_kind != PIM_ACT_LUT) ||
+      (act_kind == PIM_ACT_LUT && lut_levels < 2))
+    return fail(PIM_ERR_INVALID, "pim_activation_levels: bad arguments");
+  activation_levels(b_t, imax, act_kind, lut_levels, out);
+  return PIM_OK;
+}
+
+PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, const void* h,
+                       double scale_c) {
+  if (!out) return fail(PIM_ERR_INVALID, "pim_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > kMaxN) return fail(PIM_ERR_INVALID, "pim_create: n=%d out of [1, %d]", n, kMaxN);
+  if (!J) return fail(PIM_ERR_INVALID, "pim_create: J is NULL");
+  if (!(scale_c > 0.0) || !std::isfinite(scale_c))
+    return fail(PIM_ERR_INVALID, "pim_create: scale_c must be finite and > 0");
+  if (j_type == PIM_J_FP32 || j_type == PIM_J_FP64)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_create: real-valued couplings are not supported yet");
+  if (j_type != PIM_J_INT8) return fail(PIM_ERR_INVALID, "pim_create: unknown j_type %d", j_type);
+  const int8_t* J8 = static_cast<const int8_t*>(J);
+  const int32_t* h32 = static_cast<const int32_t*>(h);
+  long long imax = 0;
+  for (int i = 0; i < n; ++i) {
+    if (J8[static_cast<size_t>(i) * n + i] != 0)
+      return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] != 0 (diagonal must be zero)", i, i);
+    long long row = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
+    for (int j = 0; j < n; ++j) {
+      const int v = J8[static_cast<size_t>(i) * n + j];
+      if (v != J8[static_cast<size_t>(j) * n + i])
+        return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", i, j);
+      if (v < -16 || v > 16)
+        return fail(PIM_ERR_INVALID, "pim_create: |J[%d][%d]| = %d > 16", i, j, v < 0 ? -v : v);
+      row += v < 0 ? -v : v;
+    }
+    if (row > imax) imax = row;
+  }
+  if (imax > (1 << 20)) return fail(PIM_ERR_INVALID, "pim_create: field range too large");
+  auto* p = new (std::nothrow) pim_instance();
+  if (!p) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");
+  cudaGetDevice(&p->device);
+  p->n = n;
+  p->npad = n <= 128 ? 128 : ((n + 255) / 256) * 256;
+  p->words = (n + 31) / 32;
+  if (p->words & 1) p->words += 1;  // even word count: rows of 16-bit chunks stay aligned
+  p->c = scale_c;
+  p->imax = static_cast<int>(imax);
+  p->has_h = false;
+  if (h32)
+    for (int i = 0; i < n; ++i) p->has_h |= h32[i] != 0;
+  auto bail = [&](cudaError_t e, const char* what) {
+    const int rc = cuda_fail(e, what);
+    pim_destroy(p);
+    return rc;
+  };
+  cudaError_t e;
+  const size_t nn = static_cast<size_t>(n) * n;
+  if ((e = cudaMalloc(&p->d_J8, nn)) != cudaSuccess) return bail(e, "cudaMalloc J");
+  if ((e = cudaMemcpy(p->d_J8, J8, nn, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "upload J");
+  if (p->has_h) {
+    if ((e = cudaMalloc(&p->d_h, n * sizeof(int32_t))) != cudaSuccess) return bail(e, "cudaMalloc h");
+    if ((e = cudaMemcpy(p->d_h, h32, n * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "upload h");
+  }
+  if (n <= kMaxNTensor) {
+    const size_t img = static_cast<size_t>(p->npad) * p->npad;
+    if ((e = cudaMalloc(&p->d_img, img)) != cudaSuccess) return bail(e, "cudaMalloc J image");
+    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->d_img, nullptr)) != cudaSuccess)
+      return bail(e, "stage J image");
+  }
+  if ((e = cudaMalloc(&p->d_jf, nn * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc Jf");
+  if ((e = launch_stage_f32(p->d_J8, n, p->d_jf, nullptr)) != cudaSuccess) return bail(e, "stage Jf");
+  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "staging");
+  *out = p;
+  return PIM_OK;
+}
+
+PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, const float* eta,
+                             float xi, int noise_kind, int act_kind, int lut_levels) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_set_schedule: instance is NULL");
+  if (steps < 1 || !beta || !eta) return fail(PIM_ERR_INVALID, "pim_set_schedule: bad steps/arrays");
+  if (!std::isfinite(xi) || xi < 0.0f) return fail(PIM_ERR_INVALID, "pim_set_schedule: xi must be finite, >= 0");
+  if (noise_kind != PIM_NOISE_GAUSS && noise_kind != PIM_NOISE_UNIFORM)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule: unknown noise kind %d", noise_kind);
+  if (act_kind != PIM_ACT_TANH && act_kind != PIM_ACT_LUT)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule: unknown activation %d", act_kind);
+  if (act_kind == PIM_ACT_LUT && lut_levels < 2)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule: lut_levels must be >= 2");
+  if (act_kind == PIM_ACT_TANH) lut_levels = 0;
+  for (int t = 0; t < steps; ++t)
+    if (!std::isfinite(beta[t]) || beta[t] < 0.0f || !std::isfinite(eta[t]) || eta[t] < 0.0f)
+      return fail(PIM_ERR_INVALID, "pim_set_schedule: beta/eta[%d] must be finite and >= 0", t);
+  const int imax = table_imax(inst);
+  const std::string key = schedule_key(steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
+                                       inst->c, imax, inst->device);
+  std::shared_ptr<Schedule> s;
+  {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched_cache.find(key);
+    if (it != g_sched_cache.end()) s = it->second.lock();
+  }
+  if (!s) {
+    const int rc = build_schedule(s, steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
+                                  inst->c, imax, inst->device);
+    if (rc != PIM_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched_cache[key] = s;
+  }
+  if (inst->done) cudaEventSynchronize(inst->done);
+  inst->sched = s;
+  return PIM_OK;
+}
+
+namespace {
+
+int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
+                int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
+                const int8_t* init_spins, int flags, cudaStream_t st) {
+  if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
+  if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
+  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF)) return fail(PIM_ERR_INVALID, "anneal: unknown flags");
+  const bool cont = (flags & PIM_CONTINUE) != 0;
+  const bool ref = (flags & PIM_PATH_FP32REF) != 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int maxR = 0, max_words = 0, stride_max = 4, npad_max = 0;
+  bool any_h = false;
+  for (int k = 0; k < count; ++k) {
+    pim_instance* p = insts[k];
+    if (!p) return fail(PIM_ERR_INVALID, "anneal: instance %d is NULL", k);
+    if (p->device != dev) return fail(PIM_ERR_INVALID, "anneal: instance %d lives on device %d", k, p->device);
+    if (!p->sched) return fail(PIM_ERR_STATE, "anneal: instance %d has no schedule", k);
+    if (replicas[k] < 1) return fail(PIM_ERR_INVALID, "anneal: replicas[%d] = %d < 1", k, replicas[k]);
+    if (static_cast<long long>(t_begin) + sweeps > p->sched->steps)
+      return fail(PIM_ERR_INVALID, "anneal: t_begin + sweeps = %lld exceeds the %d schedule steps",
+                  static_cast<long long>(t_begin) + sweeps, p->sched->steps);
+    if (cont && (!p->has_results || p->R != replicas[k]))
+      return fail(PIM_ERR_STATE, "anneal: CONTINUE needs a previous run with the same replicas");
+    if (!ref && p->n > kMaxNTensor)
+      return fail(PIM_ERR_UNSUPPORTED, "anneal: n = %d > %d needs the plain path (PIM_PATH_FP32REF)",
+                  p->n, kMaxNTensor);
+    if (!ref && p->sched->imax > kMaxImaxTensor)
+      return fail(PIM_ERR_UNSUPPORTED, "anneal: field range %d too large for the fused kernel",
+                  p->sched->imax);
+    for (int j = 0; j < k; ++j)
+      if (insts[j] == p) return fail(PIM_ERR_INVALID, "anneal: instance listed twice");
+    if (targets && std::isnan(targets[k]) == false && !std::isfinite(targets[k]))
+      return fail(PIM_ERR_INVALID, "anneal: target %d not finite", k);
+    maxR = std::max(maxR, replicas[k]);
+    max_words = std::max(max_words, p->words);
+    stride_max = std::max(stride_max, p->sched->stride_words);
+    npad_max = std::max(npad_max, p->npad);
+    any_h |= p->has_h;
+  }
+  if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
+  for (int k = 0; k < count; ++k) {
+    int rc = ensure_results(insts[k], replicas[k]);
+    if (rc != PIM_OK) return rc;
+  }
+  int* d_err = device_error_word(dev);
+  if (!d_err) return fail(PIM_ERR_NOMEM, "anneal: error word allocation failed");
+
+  std::vector<Problem> probs(count);
+  for (int k = 0; k < count; ++k) {
+    pim_instance* p = insts[k];
+    Problem& P = probs[k];
+    P.jimg = p->d_img;
+    P.jf = p->d_jf;
+    P.h = p->d_h;
+    P.thr = p->sched->d_thr;
+    P.best_E = p->d_bestE;
+    P.final_E = p->d_finalE;
+    P.best_t = p->d_bestT;
+    P.first_hit = p->d_first;
+    P.best_bits = p->d_best_bits;
+    P.cur_bits = p->d_cur_bits;
+    P.n = p->n;
+    P.npad = p->npad;
+    P.words = p->words;
+    P.imax = p->sched->imax;
+    P.stride_words = p->sched->stride_words;
+    P.R = replicas[k];
+    P.q = ids ? ids[k] : static_cast<uint32_t>(k);
+    const double tg = targets ? targets[k] : NAN;
+    P.has_target = std::isnan(tg) ? 0 : 1;
+    P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
+  }
+  std::vector<WorkItem> work[2];  // npad 128 / 256 groups
+  for (int k = 0; k < count; ++k)
+    for (int rb = 0; rb < replicas[k]; rb += 128) work[insts[k]->npad <= 128 ? 0 : 1].push_back({k, rb});
+
+  const size_t probs_bytes = probs.size() * sizeof(Problem);
+  const size_t work_bytes = (work[0].size() + work[1].size()) * sizeof(WorkItem);
+  const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
+  const size_t total = probs_bytes + work_bytes + init_bytes + 64;
+  char* d_buf = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
+  std::vector<char> h_buf(total);
+  std::memcpy(h_buf.data(), probs.data(), probs_bytes);
+  std::memcpy(h_buf.data() + probs_bytes, work[0].data(), work[0].size() * sizeof(WorkItem));
+  std::memcpy(h_buf.data() + probs_bytes + work[0].size() * sizeof(WorkItem), work[1].data(),
+              work[1].size() * sizeof(WorkItem));
+  if (init_bytes) std::memcpy(h_buf.data() + probs_bytes + work_bytes, init_spins, init_bytes);
+  const Problem* d_probs = reinterpret_cast<const Problem*>(d_buf);
+  const WorkItem* d_work0 = reinterpret_cast<const WorkItem*>(d_buf + probs_bytes);
+  const WorkItem* d_work1 = d_work0 + work[0].size();
+  const int8_t* d_init = init_bytes ? reinterpret_cast<const int8_t*>(d_buf + probs_bytes + work_bytes) : nullptr;
+  CK(cudaMemcpyAsync(d_buf, h_buf.data(), total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  if (!cont)
+    CK(launch_init_bits(d_probs, count, maxR, max_words, d_init, static_cast<uint32_t>(seed),
+                        static_cast<uint32_t>(seed >> 32), st),
+       "init kernel");
+  auto timer = std::make_shared<LaunchTimer>();
+  CK(cudaEventCreate(&timer->start), "cudaEventCreate");
+  CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
+  if (ref) {
+    float *d_S = nullptr, *d_I = nullptr;
+    size_t maxRn = 0;
+    for (int k = 0; k < count; ++k)
+      maxRn = std::max(maxRn, static_cast<size_t>(replicas[k]) * insts[k]->n);
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d_S), maxRn * 4, st), "cudaMallocAsync S");
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d_I), maxRn * 4, st), "cudaMallocAsync I");
+    CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
+    CK(launch_ref_anneal(probs.data(), d_probs, count, t_begin, sweeps, static_cast<uint32_t>(seed),
+                         static_cast<uint32_t>(seed >> 32), cont ? 1 : 0, d_S, d_I, d_err, st),
+       "plain path");
+    CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
+    CK(cudaFreeAsync(d_S, st), "cudaFreeAsync");
+    CK(cudaFreeAsync(d_I, st), "cudaFreeAsync");
+  } else {
+    CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
+    for (int g = 0; g < 2; ++g) {
+      if (work[g].empty()) continue;
+      Launch L{};
+      L.probs = d_probs;
+      L.work = g == 0 ? d_work0 : d_work1;
+      L.nwork = static_cast<int>(work[g].size());
+      L.t_begin = t_begin;
+      L.sweeps = sweeps;
+      L.key_lo = static_cast<uint32_t>(seed);
+      L.key_hi = static_cast<uint32_t>(seed >> 32);
+      L.cont = cont ? 1 : 0;
+      L.stride_words_max = stride_max;
+      L.err = d_err;
+      CK(launch_sweep_tc(L, g == 0 ? 128 : 256, L.nwork, st, any_h), "fused sweep kernel");
+    }
+    CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
+  }
+  CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
+  for (int k = 0; k < count; ++k) {
+    insts[k]->R = replicas[k];
+    insts[k]->has_results = true;
+    insts[k]->timer = timer;
+    CK(cudaEventRecord(insts[k]->done, st), "cudaEventRecord");
+  }
+  return PIM_OK;
+}
+
+}  // namespace
+
+PIM_API int pim_anneal(pim_instance* inst, int replicas, int t_begin, int sweeps, uint64_t seed,
+                       uint32_t instance_id, const int8_t* init_spins, double target_energy,
+                       int flags, void* cuda_stream) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_anneal: instance is NULL");
+  if (init_spins && !(flags & PIM_CONTINUE)) {
+    const size_t tot = static_cast<size_t>(replicas > 0 ? replicas : 0) * inst->n;
+    for (size_t k = 0; k < tot; ++k)
+      if (init_spins[k] != 1 && init_spins[k] != -1)
+        return fail(PIM_ERR_INVALID, "pim_anneal: init_spins must hold -1/+1");
+  }
+  return anneal_impl(&inst, 1, &replicas, t_begin, sweeps, seed, &instance_id, &target_energy,
+                     (flags & PIM_CONTINUE) ? nullptr : init_spins, flags,
+                     static_cast<cudaStream_t>(cuda_stream));
+}
+
+PIM_API int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
+                             int t_begin, int sweeps, uint64_t seed, const uint32_t* instance_ids,
+                             const double* targets, int flags, void* cuda_stream) {
+  return anneal_impl(insts, count, replicas, t_begin, sweeps, seed, instance_ids, targets, nullptr,
+                     flags, static_cast<cudaStream_t>(cuda_stream));
+}
+
+PIM_API int pim_sync(pim_instance* inst) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_sync: instance is NULL");
+  return sync_instance(inst);
+}
+
+PIM_API int pim_replicas(const pim_instance* inst) { return inst ? inst->R : 0; }
+
+PIM_API int pim_kernel_ms(pim_instance* inst, float* ms) {
+  if (!inst || !ms) return fail(PIM_ERR_INVALID, "pim_kernel_ms: NULL argument");
+  if (!inst->timer) return fail(PIM_ERR_STATE, "pim_kernel_ms: no anneal has run");
+  CK(cudaEventSynchronize(inst->timer->stop), "cudaEventSynchronize");
+  CK(cudaEventElapsedTime(ms, inst->timer->start, inst->timer->stop), "cudaEventElapsedTime");
+  return PIM_OK;
+}
+
+PIM_API int pim_energies(pim_instance* inst, double* best_E, int32_t* best_t,
+                         int32_t* first_hit_t, double* final_E) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_energies: instance is NULL");
+  if (!inst->has_results) return fail(PIM_ERR_STATE, "pim_energies: no anneal has run");
+  int rc = sync_instance(inst);
+  if (rc != PIM_OK) return rc;
+  const size_t R = inst->R;
+  if (best_E) CK(cudaMemcpy(best_E, inst->d_bestE, R * 8, cudaMemcpyDeviceToHost), "copy best_E");
+  if (best_t) CK(cudaMemcpy(best_t, inst->d_bestT, R * 4, cudaMemcpyDeviceToHost), "copy best_t");
+  if (first_hit_t) CK(cudaMemcpy(first_hit_t, inst->d_first, R * 4, cudaMemcpyDeviceToHost), "copy first_hit");
+  if (final_E) CK(cudaMemcpy(final_E, inst->d_finalE, R * 8, cudaMemcpyDeviceToHost), "copy final_E");
+  return PIM_OK;
+}
+
+namespace {
+int copy_state(pim_instance* inst, const uint32_t* d_bits, int8_t* out) {
+  if (!out) return fail(PIM_ERR_INVALID, "state copy: out is NULL");
+  if (!inst->has_results) return fail(PIM_ERR_STATE, "state copy: no anneal has run");
+  int rc = sync_instance(inst);
+  if (rc != PIM_OK) return rc;
+  std::vector<uint32_t> bits(static_cast<size_t>(inst->R) * inst->words);
+  CK(cudaMemcpy(bits.data(), d_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "copy state bits");
+  for (int r = 0; r < inst->R; ++r)
+    for (int i = 0; i < inst->n; ++i) {
+      const uint32_t w = bits[static_cast<size_t>(r) * inst->words + (i >> 5)];
+      out[static_cast<size_t>(r) * inst->n + i] = ((w >> (i & 31)) & 1u) ? 1 : -1;
+    }
+  return PIM_OK;
+}
+}  // namespace
+
+PIM_API int pim_best_state(pim_instance* inst, int8_t* out) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_best_state: instance is NULL");
+  return copy_state(inst, inst->d_best_bits, out);
+}
+
+PIM_API int pim_final_state(pim_instance* inst, int8_t* out) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_final_state: instance is NULL");
+  return copy_state(inst, inst->d_cur_bits, out);
+}
+
+namespace {
+std::mutex g_ticket_mu;
+std::map<uint64_t, pim_instance*> g_tickets;
+uint64_t g_next_ticket = 1;
+cudaStream_t g_submit_stream = nullptr;
+}  // namespace
+
+PIM_API int pim_submit(pim_instance* inst, int replicas, int sweeps, uint64_t seed, uint64_t* ticket) {
+  if (!inst || !ticket) return fail(PIM_ERR_INVALID, "pim_submit: NULL argument");
+  std::lock_guard<std::mutex> lk(g_ticket_mu);
+  if (!g_submit_stream)
+    CK(cudaStreamCreateWithFlags(&g_submit_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  const int rc = pim_anneal(inst, replicas, 0, sweeps, seed, 0, nullptr, NAN, 0, g_submit_stream);
+  if (rc != PIM_OK) return rc;
+  if (inst->ticket) g_tickets.erase(inst->ticket);
+  inst->ticket = g_next_ticket++;
+  g_tickets[inst->ticket] = inst;
+  *ticket = inst->ticket;
+  return PIM_OK;
+}
+
+PIM_API int pim_poll(uint64_t ticket) {
+  pim_instance* inst = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    auto it = g_tickets.find(ticket);
+    if (it == g_tickets.end()) return fail(PIM_ERR_INVALID, "pim_poll: unknown ticket %llu",
+                                           static_cast<unsigned long long>(ticket));
+    inst = it->second;
+  }
+  const cudaError_t e = cudaEventQuery(inst->done);
+  if (e == cudaErrorNotReady) return PIM_PENDING;
+  if (e != cudaSuccess) return cuda_fail(e, "pim_poll");
+  return check_device_errors(inst->device);
+}
+
+PIM_API void pim_destroy(pim_instance* inst) {
+  if (!inst) return;
+  if (inst->done) {
+    cudaEventSynchronize(inst->done);
+    cudaEventDestroy(inst->done);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_ticket_mu);
+    if (inst->ticket) g_tickets.erase(inst->ticket);
+  }
+  free_results(inst);
+  cudaFree(inst->d_J8);
+  cudaFree(inst->d_img);
+  cudaFree(inst->d_jf);
+  cudaFree(inst->d_h);
+  inst->sched.reset();
+  delete inst;
+}
+
+PIM_API int pim_thresholds(pim_instance* inst, uint32_t* out, size_t cap_words, int* steps,
+                           int* imax, int* stride_words) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_thresholds: instance is NULL");
+  if (!inst->sched) return fail(PIM_ERR_STATE, "pim_thresholds: no schedule");
+  const Schedule& s = *inst->sched;
+  if (steps) *steps = s.steps;
+  if (imax) *imax = s.imax;
+  if (stride_words) *stride_words = s.stride_words;
+  if (!out) return PIM_OK;
+  const size_t need = static_cast<size_t>(s.steps) * s.stride_words;
+  if (cap_words < need) return fail(PIM_ERR_INVALID, "pim_thresholds: need %zu words", need);
+  CK(cudaMemcpy(out, s.d_thr, need * 4, cudaMemcpyDeviceToHost), "copy thresholds");
+  return PIM_OK;
+}

@@ -1,0 +1,222 @@
+"""Python binding of the C ABI in include/pim.h (argument marshalling only).
+
+Each function has the name of the C entry point it calls and does nothing but convert
+numpy arrays and Python values to the C arguments and raise ``PimError`` on a non-zero
+status.  All computation happens in libpimi.so; importing this module without the built
+library raises immediately -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpimi.so")
+
+PIM_OK, PIM_PENDING = 0, 1
+PIM_ERR_INVALID, PIM_ERR_NOMEM, PIM_ERR_CUDA = -1, -2, -3
+PIM_ERR_STATE, PIM_ERR_TIMEOUT, PIM_ERR_UNSUPPORTED = -4, -5, -6
+PIM_J_INT8, PIM_J_FP32, PIM_J_FP64 = 0, 1, 2
+PIM_NOISE_GAUSS, PIM_NOISE_UNIFORM = 0, 1
+PIM_ACT_TANH, PIM_ACT_LUT = 0, 1
+PIM_CONTINUE, PIM_PATH_FP32REF = 1, 2
+
+# name -> (restype, argtypes); every symbol declared in include/pim.h
+SIGNATURES = {
+    "pim_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                             C.c_double]),
+    "pim_set_schedule": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
+                                   C.c_int, C.c_int, C.c_int]),
+    "pim_anneal": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                             C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
+    "pim_anneal_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                   C.c_uint64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pim_sync": (C.c_int, [C.c_void_p]),
+    "pim_energies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_best_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pim_final_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pim_replicas": (C.c_int, [C.c_void_p]),
+    "pim_kernel_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "pim_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "pim_poll": (C.c_int, [C.c_uint64]),
+    "pim_destroy": (None, [C.c_void_p]),
+    "pim_last_error": (C.c_char_p, []),
+    "pim_noise_levels": (C.c_int, [C.c_int, C.c_void_p]),
+    "pim_activation_levels": (C.c_int, [C.c_float, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "pim_thresholds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libpimi.so (built by ``paper_2604_17109_gb300.build``); raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libpimi.so not built at {_LIB_PATH}; run the package build first")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PimError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise PimError(rc, where, lib().pim_last_error().decode())
+    return rc
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+_NOISE = {"gauss": PIM_NOISE_GAUSS, "uniform": PIM_NOISE_UNIFORM}
+_ACT = {"tanh": PIM_ACT_TANH, "lut": PIM_ACT_LUT}
+
+
+def pim_last_error() -> str:
+    return lib().pim_last_error().decode()
+
+
+def pim_create(J: np.ndarray, h: np.ndarray | None = None, scale_c: float = 1.0) -> int:
+    """Stage an integer instance; returns the opaque handle (an int)."""
+    J = np.ascontiguousarray(J, dtype=np.int8)
+    n = J.shape[0]
+    if J.shape != (n, n):
+        raise ValueError("J must be square")
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.int32)
+    out = C.c_void_p()
+    _check(lib().pim_create(C.byref(out), n, PIM_J_INT8, _ptr(J), _ptr(hh), float(scale_c)),
+           "pim_create")
+    return out.value
+
+
+def pim_set_schedule(inst: int, beta, eta, xi: float, noise="gauss", act="tanh",
+                     lut_levels: int = 4) -> None:
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    eta = np.ascontiguousarray(eta, dtype=np.float32)
+    if beta.shape != eta.shape:
+        raise ValueError("beta and eta must have the same length")
+    noise = _NOISE.get(noise, noise)
+    act = _ACT.get(act, act)
+    _check(lib().pim_set_schedule(inst, beta.size, _ptr(beta), _ptr(eta), float(xi), int(noise),
+                                  int(act), int(lut_levels)), "pim_set_schedule")
+
+
+def pim_anneal(inst: int, replicas: int, sweeps: int, seed: int, instance_id: int = 0,
+               t_begin: int = 0, init_spins: np.ndarray | None = None, target=None,
+               flags: int = 0, stream=None) -> None:
+    init = None if init_spins is None else np.ascontiguousarray(init_spins, dtype=np.int8)
+    tgt = math.nan if target is None else float(target)
+    _check(lib().pim_anneal(inst, int(replicas), int(t_begin), int(sweeps), int(seed),
+                            int(instance_id), _ptr(init), tgt, int(flags), _stream(stream)),
+           "pim_anneal")
+
+
+def pim_anneal_batch(insts, replicas, sweeps: int, seed: int, t_begin: int = 0,
+                     instance_ids=None, targets=None, flags: int = 0, stream=None) -> None:
+    count = len(insts)
+    handles = (C.c_void_p * count)(*insts)
+    reps = np.ascontiguousarray(np.broadcast_to(np.asarray(replicas, np.int32), (count,)))
+    ids = None if instance_ids is None else np.ascontiguousarray(instance_ids, dtype=np.uint32)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
+    _check(lib().pim_anneal_batch(C.cast(handles, C.c_void_p), count, _ptr(reps), int(t_begin),
+                                  int(sweeps), int(seed), _ptr(ids), _ptr(tg), int(flags),
+                                  _stream(stream)), "pim_anneal_batch")
+
+
+def pim_sync(inst: int) -> None:
+    _check(lib().pim_sync(inst), "pim_sync")
+
+
+def pim_replicas(inst: int) -> int:
+    return lib().pim_replicas(inst)
+
+
+def pim_kernel_ms(inst: int) -> float:
+    ms = C.c_float()
+    _check(lib().pim_kernel_ms(inst, C.byref(ms)), "pim_kernel_ms")
+    return ms.value
+
+
+def pim_energies(inst: int) -> dict:
+    R = pim_replicas(inst)
+    best_E = np.empty(R, np.float64)
+    final_E = np.empty(R, np.float64)
+    best_t = np.empty(R, np.int32)
+    first = np.empty(R, np.int32)
+    _check(lib().pim_energies(inst, _ptr(best_E), _ptr(best_t), _ptr(first), _ptr(final_E)),
+           "pim_energies")
+    return dict(best_E=best_E, best_t=best_t, first_hit=first, final_E=final_E)
+
+
+def _state(fn, inst: int, n: int, where: str) -> np.ndarray:
+    out = np.empty((pim_replicas(inst), n), np.int8)
+    _check(fn(inst, _ptr(out)), where)
+    return out
+
+
+def pim_best_state(inst: int, n: int) -> np.ndarray:
+    return _state(lib().pim_best_state, inst, n, "pim_best_state")
+
+
+def pim_final_state(inst: int, n: int) -> np.ndarray:
+    return _state(lib().pim_final_state, inst, n, "pim_final_state")
+
+
+def pim_submit(inst: int, replicas: int, sweeps: int, seed: int) -> int:
+    t = C.c_uint64()
+    _check(lib().pim_submit(inst, int(replicas), int(sweeps), int(seed), C.byref(t)), "pim_submit")
+    return t.value
+
+
+def pim_poll(ticket: int) -> int:
+    return _check(lib().pim_poll(int(ticket)), "pim_poll")
+
+
+def pim_destroy(inst: int) -> None:
+    lib().pim_destroy(inst)
+
+
+def pim_noise_levels(noise="gauss") -> np.ndarray:
+    out = np.empty(4096, np.float32)
+    _check(lib().pim_noise_levels(int(_NOISE.get(noise, noise)), _ptr(out)), "pim_noise_levels")
+    return out
+
+
+def pim_activation_levels(b_t: float, imax: int, act="tanh", lut_levels: int = 4) -> np.ndarray:
+    out = np.empty(max(0, 2 * imax + 1), np.float32)
+    _check(lib().pim_activation_levels(float(b_t), int(imax), int(_ACT.get(act, act)),
+                                       int(lut_levels), _ptr(out)), "pim_activation_levels")
+    return out
+
+
+def pim_thresholds(inst: int) -> tuple[np.ndarray, int]:
+    """Device decision table as uint32 [steps, stride] and the field offset imax."""
+    steps, imax, stride = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().pim_thresholds(inst, None, 0, C.byref(steps), C.byref(imax), C.byref(stride)),
+           "pim_thresholds")
+    out = np.empty((steps.value, stride.value), np.uint32)
+    _check(lib().pim_thresholds(inst, _ptr(out), out.size, None, None, None), "pim_thresholds")
+    return out, imax.value

@@ -1,0 +1,236 @@
+"""GPU parity: the fused tensor-core sweep kernel and the plain FP32 path, called through
+the C ABI, against the CPU oracle -- bit-exact on integer instances (spins, energies,
+steps)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pimi
+from workloads import (Instance, eta_power, linear_beta, maxcut_er, random_spins, sk_batch,
+                       sk_pm1)
+
+from gpu_helpers import assert_same, collect, oracle_run, pim, run_library
+
+pytestmark = pytest.mark.gpu
+
+PATHS = [0, 2]  # fused tensor-core kernel, plain FP32 path (PIM_PATH_FP32REF)
+
+CASES = [
+    # kind, n, replicas, sweeps, seed
+    ("maxcut", 20, 32, 50, 1),
+    ("sk", 1, 5, 7, 0),         # degenerate: no couplings, pure noise
+    ("sk", 17, 40, 40, 2),      # ragged spins and replicas
+    ("sk", 100, 128, 80, 3),
+    ("maxcut", 128, 96, 30, 4),  # exactly one K block
+    ("sk", 129, 130, 25, 5),    # just past one K block and one replica tile
+    ("sk", 200, 200, 60, 6),    # two K blocks, ragged replica tile
+    ("maxcut", 256, 64, 20, 7),  # largest fused size
+]
+
+
+def _inst(kind, n, seed):
+    return sk_pm1(n, seed) if kind == "sk" else maxcut_er(n, seed)
+
+
+@pytest.mark.parametrize("flags", PATHS)
+@pytest.mark.parametrize("kind,n,R,T,seed", CASES)
+def test_matches_oracle(kind, n, R, T, seed, flags):
+    inst = _inst(kind, n, seed)
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    xi = 0.5 if kind == "sk" else 0.7
+    target = -0.5 * n
+    got = run_library(inst, beta, eta, xi, replicas=R, seed=seed * 7 + 1, q=3, target=target,
+                      flags=flags)
+    want = oracle_run(inst, beta, eta, xi, replicas=R, seed=seed * 7 + 1, q=3, target=target)
+    assert_same(got, want, label=f"{kind} n={n} path={flags}")
+
+
+@pytest.mark.parametrize("flags", PATHS)
+def test_bias_uniform_noise_lut_and_host_init(flags):
+    """Non-zero h, Eq. 3 uniform noise, the 4-level LUT activation and host-given spins."""
+    inst = sk_pm1(70, 11)
+    rng = np.random.default_rng(5)
+    inst = Instance("sk", 70, inst.J, rng.integers(-4, 5, 70).astype(np.int32), inst.c, 11)
+    T = 40
+    beta = linear_beta(T, 0.2, 2.0)
+    eta = np.full(T, 0.6, np.float32)
+    init = random_spins(70, 33, seed=4)
+    for noise, act in (("uniform", "tanh"), ("gauss", "lut")):
+        got = run_library(inst, beta, eta, 0.3, replicas=33, seed=9, init=init, noise=noise,
+                          act=act, lut_levels=4, flags=flags, target=-100)
+        want = oracle_run(inst, beta, eta, 0.3, replicas=33, seed=9, init=init, noise=noise,
+                          act=act, lut_levels=4, target=-100)
+        assert_same(got, want, label=f"{noise}/{act} path={flags}")
+
+
+@pytest.mark.parametrize("flags", PATHS)
+def test_resume_matches_uninterrupted(flags):
+    P = pim()
+    inst = maxcut_er(60, 3)
+    beta = linear_beta(90)
+    eta = eta_power(beta)
+    full = oracle_run(inst, beta, eta, 0.7, replicas=50, seed=2, target=-300)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.7)
+        P.pim_anneal(hd, 50, 41, 2, target=-300, flags=flags)
+        P.pim_anneal(hd, 50, 49, 2, t_begin=41, target=-300, flags=flags | P.PIM_CONTINUE)
+        assert_same(collect(hd, 60), full, label="resume")
+    finally:
+        P.pim_destroy(hd)
+
+
+def test_zero_sweeps_reports_initial_state():
+    inst = sk_pm1(33, 1)
+    beta = linear_beta(10)
+    got = run_library(inst, beta, eta_power(beta), 0.5, replicas=10, sweeps=0, seed=4)
+    want = oracle_run(inst, beta, eta_power(beta), 0.5, replicas=10, sweeps=0, seed=4)
+    assert_same(got, want)
+    assert np.all(got["best_t"] == 0)
+
+
+def test_thresholds_equal_direct_evaluation_exhaustively():
+    """Every entry of the device decision table equals the oracle's direct float32 decision
+    for every key m in [0, 4096), both spins and every field of the table."""
+    P = pim()
+    inst = sk_pm1(40, 0)
+    T = 12
+    beta = linear_beta(T, 0.05, 4.0)
+    eta = eta_power(beta)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.5)
+        tab, imax = P.pim_thresholds(hd)
+    finally:
+        P.pim_destroy(hd)
+    Q = pimi.gaussian_quantiles()
+    I = np.arange(-imax, imax + 1)
+    m = np.arange(4096)
+    for t in range(T):
+        b = np.float32(np.float64(beta[t]) * inst.c)
+        tau = oracle.activation(b, I)
+        for s, shift in ((-1, 0), (1, 16)):
+            M = (tab[t, : I.size] >> shift) & 0xFFFF
+            dec = pimi.decide(np.repeat(tau[:, None], 4096, 1), np.full((I.size, 4096), s), 0.5,
+                              eta[t], np.broadcast_to(Q, (I.size, 4096)))
+            assert np.array_equal(dec > 0, m[None, :] >= M[:, None]), (t, s)
+
+
+def test_batch_equals_per_instance_oracle():
+    """One launch over several instances (different n and R, both kernel sizes) gives each
+    instance exactly its own oracle run with counter word q = its instance id."""
+    P = pim()
+    insts = [sk_pm1(200, 0), maxcut_er(100, 1), sk_pm1(150, 2), maxcut_er(37, 3)]
+    reps = [300, 64, 129, 20]
+    ids = [10, 11, 12, 13]
+    T = 30
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.6)
+        targets = [-1000.0, -150.0, -1000.0, -40.0]
+        P.pim_anneal_batch(handles, reps, T, seed=77, instance_ids=ids, targets=targets)
+        for hd, inst, R, q, tg in zip(handles, insts, reps, ids, targets):
+            want = oracle_run(inst, beta, eta, 0.6, replicas=R, seed=77, q=q, target=tg)
+            assert_same(collect(hd, inst.n), want, label=f"n={inst.n}")
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+def test_maxcut_n100_full_run_matches_oracle():
+    """Max-Cut N = 100 (ER p = 0.5), 64 replicas x 1000 sweeps, linear beta 0.1 -> 3,
+    seed 0: the whole run, every replica."""
+    inst = maxcut_er(100, 0)
+    T = 1000
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    got = run_library(inst, beta, eta, 0.7, replicas=64, seed=0)
+    want = oracle_run(inst, beta, eta, 0.7, replicas=64, seed=0)
+    assert_same(got, want, label="maxcut-100")
+
+
+def test_sk200_batch_full_size_sampled():
+    """SK N = 200: 100 instances x 1024 replicas x 2000 sweeps in one launch (the
+    configuration the bench times).  Sampled replicas are compared with the oracle bit for
+    bit; every replica is checked for the energy identities."""
+    P = pim()
+    insts = sk_batch(200, 100)
+    T, R = 2000, 1024
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, R, T, seed=0)
+        for q in (0, 57, 99):
+            got = collect(handles[q], 200)
+            rows = [0, 127, 128, 1023]
+            want = oracle_run(insts[q], beta, eta, 0.5, replica_ids=rows, seed=0, q=q)
+            assert_same(got, want, rows=rows, label=f"q={q}")
+        for q in range(0, 100, 9):
+            got = collect(handles[q], 200)
+            J, h = insts[q].J, insts[q].h
+            assert np.array_equal(oracle.energy(J, h, got["best_state"]), got["best_E"])
+            assert np.array_equal(oracle.energy(J, h, got["final_state"]), got["final_E"])
+            assert np.all(got["best_E"] <= got["final_E"])
+            assert np.all((got["best_t"] >= 0) & (got["best_t"] <= T))
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+def test_errors_are_reported():
+    P = pim()
+    inst = sk_pm1(30, 0)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        with pytest.raises(P.PimError) as e:
+            P.pim_anneal(hd, 4, 5, 0)
+        assert e.value.code == P.PIM_ERR_STATE  # no schedule
+        P.pim_set_schedule(hd, linear_beta(10), eta_power(linear_beta(10)), 0.5)
+        with pytest.raises(P.PimError) as e:
+            P.pim_anneal(hd, 4, 11, 0)
+        assert e.value.code == P.PIM_ERR_INVALID  # more sweeps than schedule steps
+        with pytest.raises(P.PimError) as e:
+            P.pim_anneal(hd, 4, 3, 0, flags=P.PIM_CONTINUE)
+        assert e.value.code == P.PIM_ERR_STATE  # nothing to continue from
+        with pytest.raises(P.PimError) as e:
+            P.pim_anneal(hd, 0, 3, 0)
+        assert e.value.code == P.PIM_ERR_INVALID
+        big = sk_pm1(300, 0)
+        hb = P.pim_create(big.J, None, big.c)
+        try:
+            P.pim_set_schedule(hb, linear_beta(4), eta_power(linear_beta(4)), 0.5)
+            with pytest.raises(P.PimError) as e:
+                P.pim_anneal(hb, 4, 2, 0)
+            assert e.value.code == P.PIM_ERR_UNSUPPORTED
+        finally:
+            P.pim_destroy(hb)
+    finally:
+        P.pim_destroy(hd)
+
+
+def test_submit_poll_completes():
+    P = pim()
+    inst = sk_pm1(64, 0)
+    beta = linear_beta(100)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta_power(beta), 0.5)
+        ticket = P.pim_submit(hd, 128, 100, 5)
+        import time
+        t0 = time.time()
+        while P.pim_poll(ticket) == P.PIM_PENDING:
+            assert time.time() - t0 < 30
+            time.sleep(0.001)
+        want = oracle_run(inst, beta, eta_power(beta), 0.5, replicas=128, seed=5)
+        assert_same(collect(hd, 64), want)
+    finally:
+        P.pim_destroy(hd)
