@@ -44,15 +44,15 @@ SM_COUNT = 152
 LANES_PER_SM = 128
 
 
-def _schedule():
+def _schedule(sweeps: int = SWEEPS):
     from workloads import eta_power, linear_beta
-    beta = linear_beta(SWEEPS)
+    beta = linear_beta(sweeps)
     return beta, eta_power(beta)
 
 
-def _instances(rank: int):
+def _instances(rank: int, count: int = N_INST):
     from workloads import sk_batch
-    return sk_batch(N_SPINS, N_INST, first_seed=rank * N_INST)
+    return sk_batch(N_SPINS, count, first_seed=rank * count)
 
 
 def _peaks():
@@ -233,9 +233,10 @@ def run_ours(args):
     from paper_2604_17109_gb300 import pim
 
     pkg_build.build()
-    beta, eta = _schedule()
-    insts = _instances(rank)
-    ids = np.arange(rank * N_INST, (rank + 1) * N_INST, dtype=np.uint32)
+    n_inst, sweeps = args.instances, args.sweeps
+    beta, eta = _schedule(sweeps)
+    insts = _instances(rank, n_inst)
+    ids = np.arange(rank * n_inst, (rank + 1) * n_inst, dtype=np.uint32)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -243,10 +244,10 @@ def run_ours(args):
     handles = [pim.pim_create(i.J, None, i.c) for i in insts]
     for hd in handles:
         pim.pim_set_schedule(hd, beta, eta, XI)
-    updates_per_step = N_SPINS * REPLICAS * SWEEPS * N_INST
+    updates_per_step = N_SPINS * REPLICAS * sweeps * n_inst
 
     def step():
-        pim.pim_anneal_batch(handles, REPLICAS, SWEEPS, seed=0, instance_ids=ids, stream=stream)
+        pim.pim_anneal_batch(handles, REPLICAS, sweeps, seed=0, instance_ids=ids, stream=stream)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
@@ -283,8 +284,8 @@ def run_ours(args):
     e2e_steps = max(1, min(3, args.steps))
     h2d = sum(i.J.nbytes for i in insts)
     R = REPLICAS
-    d2h = N_INST * (R * (8 + 4 + 4 + 8) + R * 8 * 4)
-    out_E = [None] * N_INST
+    d2h = n_inst * (R * (8 + 4 + 4 + 8) + R * 8 * 4)
+    out_E = [None] * n_inst
     torch.cuda.synchronize()
     _barrier(world)
     e0 = time.perf_counter()
@@ -292,7 +293,7 @@ def run_ours(args):
         hs = [pim.pim_create(i.J, None, i.c) for i in insts]
         for hd in hs:
             pim.pim_set_schedule(hd, beta, eta, XI)
-        pim.pim_anneal_batch(hs, REPLICAS, SWEEPS, seed=0, instance_ids=ids, stream=stream)
+        pim.pim_anneal_batch(hs, REPLICAS, sweeps, seed=0, instance_ids=ids, stream=stream)
         for q, hd in enumerate(hs):
             out_E[q] = pim.pim_energies(hd)["best_E"]
             pim.pim_best_state(hd, N_SPINS)
@@ -311,7 +312,7 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
     alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
-    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * SWEEPS * N_INST
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * sweeps * n_inst
     fp8_peak = float(peaks["bf16_tflops"]) * 2.0
     tensor_achieved = flops / (k_ms * 1e-3) / 1e12
     line = {
@@ -319,8 +320,10 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8e4m3/i32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_SPINS, "instances_per_gpu": N_INST,
-                   "replicas": REPLICAS, "sweeps": SWEEPS, "couplings": "SK +-1, h=0",
+        "config": {"workload": (WORKLOAD if (n_inst, sweeps) == (N_INST, SWEEPS) else
+                                f"sk200_{n_inst}inst_1024rep_{sweeps}sweeps"),
+                   "n": N_SPINS, "instances_per_gpu": n_inst,
+                   "replicas": REPLICAS, "sweeps": sweeps, "couplings": "SK +-1, h=0",
                    "schedule": "linear beta 0.1->3, eta=sqrt(beta/5), xi=0.5",
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
@@ -352,6 +355,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--instances", type=int, default=N_INST,
+                    help="instances per GPU (smaller cases for profiling)")
+    ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per anneal")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

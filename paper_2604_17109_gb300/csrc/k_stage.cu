@@ -11,7 +11,7 @@ namespace pim {
 // the K-major layout in which the MMA reads the B operand: row i (output spin), K = j,
 // value J_ij; zero outside n x n.  One thread per image byte.
 // ---------------------------------------------------------------------------------------
-__global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int npad,
+__global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int npad, int diag,
                                        uint8_t* __restrict__ img) {
   const uint32_t off = blockIdx.x * blockDim.x + threadIdx.x;
   if (off >= static_cast<uint32_t>(npad) * npad) return;
@@ -24,18 +24,18 @@ __global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int 
   const int j = kb * 128 + chunk * 16 + (within & 15);
   uint8_t v = 0;
   if (i < n && j < n) {
+    const int val = i == j ? diag : J[static_cast<size_t>(i) * n + j];
     const __nv_fp8_storage_t e =
-        __nv_cvt_float_to_fp8(static_cast<float>(J[static_cast<size_t>(i) * n + j]),
-                              __NV_SATFINITE, __NV_E4M3);
+        __nv_cvt_float_to_fp8(static_cast<float>(val), __NV_SATFINITE, __NV_E4M3);
     v = static_cast<uint8_t>(e);
   }
   img[off] = v;
 }
 
-cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
                                    cudaStream_t st) {
   const uint32_t total = static_cast<uint32_t>(npad) * npad;
-  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, d_img);
+  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, diag, d_img);
   return cudaGetLastError();
 }
 
@@ -97,6 +97,37 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
                               uint32_t* d_thr, cudaStream_t st) {
   dim3 grid((stride_words + 127) / 128, steps);
   thresholds_kernel<<<grid, 128, 0, st>>>(d_tau, d_eta, d_z, xi, imax, stride_words, d_thr);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Thresholds re-indexed by D = I + 256 s: entry D + 512 holds M(s = sign D, I = D - 256 s).
+// With |I| <= imax <= 255 the two ranges D < 0 (s = -1) and D > 0 (s = +1) are disjoint;
+// unreachable entries are zero.
+// ---------------------------------------------------------------------------------------
+__global__ void diag_thresholds_kernel(const uint32_t* __restrict__ thr, int imax, int stride_words,
+                                       uint16_t* __restrict__ out) {
+  const int t = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0 .. 1023
+  if (k >= 1024) return;
+  const int D = k - 512;
+  uint16_t v = 0;
+  if (D != 0) {
+    const bool up = D > 0;
+    const int I = D - (up ? 256 : -256);
+    if (I >= -imax && I <= imax) {
+      const uint32_t w = thr[static_cast<size_t>(t) * stride_words + (I + imax)];
+      v = static_cast<uint16_t>(up ? (w >> 16) : (w & 0xFFFFu));
+    }
+  }
+  out[static_cast<size_t>(t) * 1024 + k] = v;
+}
+
+cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
+                                   uint32_t* d_thr_diag, cudaStream_t st) {
+  dim3 grid(1024 / 256, steps);
+  diag_thresholds_kernel<<<grid, 256, 0, st>>>(d_thr, imax, stride_words,
+                                               reinterpret_cast<uint16_t*>(d_thr_diag));
   return cudaGetLastError();
 }
 

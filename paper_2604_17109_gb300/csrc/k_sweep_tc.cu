@@ -152,30 +152,46 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Four spins (bits of `nib`) -> four FP8 E4M3 bytes: +1 = 0x38, -1 = 0xB8.
+// Four spins (low 4 bits of `nib`) -> four FP8 E4M3 bytes: +1 = 0x38, -1 = 0xB8.  The
+// multiply moves bit j to bit 8j+7 (the sign bit of byte j) without carries.
 __device__ __forceinline__ uint32_t fp8x4_from_bits(uint32_t nib) {
-  return 0xB8B8B8B8u ^ (((nib * 0x00204081u) & 0x01010101u) * 0x80u);
+  return ((nib * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u;
+}
+
+__device__ __forceinline__ uint4 fp8x16_from_bits(uint32_t nb) {
+  return make_uint4(fp8x4_from_bits(nb & 0xFu), fp8x4_from_bits((nb >> 4) & 0xFu),
+                    fp8x4_from_bits((nb >> 8) & 0xFu), fp8x4_from_bits((nb >> 12) & 0xFu));
 }
 
 // The integer value I of an exactly integral float f (|f| < 2^22) appears in the low
 // mantissa bits of f + 1.5 * 2^23.
 constexpr float kMagic = 12582912.0f;
-constexpr int kMagicBits = 0x4B400000;
+constexpr uint32_t kMagicBits = 0x4B400000u;
 
-template <int NPAD, bool HAS_H>
+// Two decision modes.
+//  kModeDiag: h = 0 and |I| <= 255.  The couplings are staged with 256 on the diagonal, so
+//    the MMA returns D = I + 256 s (sign(D) = s).  One 16-bit table entry per D gives the
+//    key threshold for (s, I) at once, and |D| = s I + 256 gives the energy by an add.
+//  kModeBias: general h; the table is indexed by I and holds both thresholds per word.
+constexpr int kModeDiag = 0;
+constexpr int kModeBias = 1;
+constexpr int kDiagOffset = 256;
+constexpr int kDiagEntries = 1024;  // D = -512 .. 511
+
+template <int NPAD, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   constexpr int kMaxSlots = NPAD / 32;  // 16-column chunks per column half
   constexpr int kWordsPerThread = kMaxSlots / 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int SW = L.stride_words_max;
+  const int SW = MODE == kModeDiag ? kDiagEntries / 2 : L.stride_words_max;  // words per table
   uint8_t* sJ = smem;
   uint8_t* sA = sJ + NPAD * NPAD;
   uint32_t* sT = reinterpret_cast<uint32_t*>(sA + kTileM * NPAD);
-  int* sPart = reinterpret_cast<int*>(sT + 2 * SW);
-  int* sH = sPart + 2 * 2 * kTileM;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + (HAS_H ? NPAD : 0));
+  float* sPart = reinterpret_cast<float*>(sT + 2 * SW);
+  int* sH = reinterpret_cast<int*>(sPart + 2 * 2 * kTileM);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + (MODE == kModeBias ? NPAD : 0));
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2);
   int* sAbort = reinterpret_cast<int*>(sTmem + 1);
 
@@ -187,14 +203,16 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   const Problem& P = L.probs[wk.prob];
   const int n = P.n;
   const int imax = P.imax;
-  const int stride = P.stride_words;
+  const int stride = MODE == kModeDiag ? kDiagEntries / 2 : P.stride_words;
+  const uint32_t* thr = MODE == kModeDiag ? P.thr_diag : P.thr;
   const int R = P.R;
   const uint32_t q = P.q;
   const int rg = wk.rbase + row;
   const bool row_valid = rg < R;
   const bool warp_active = (wk.rbase + quad * 32) < R;
+  // Column halves split at the 16-column boundary nearest n/2.
   const int nch = (n + 15) >> 4;
-  const int split = (nch + 1) >> 1;
+  const int split = (n + 16) >> 5;
   const int c0 = half == 0 ? 0 : split;
   const int myc = half == 0 ? split : nch - split;
   const int ksteps = (n + 31) >> 5;
@@ -202,6 +220,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
   const uint32_t bar_mma = smem_u32(&bars[0]);
   const uint32_t bar_j = smem_u32(&bars[1]);
+  const uint32_t key_lo = L.key_lo, key_hi = L.key_hi;
 
   // ---- prologue: TMEM, barriers, zeroed A operand, bias, first threshold table --------
   if (warp == 0) {
@@ -216,10 +235,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   }
   for (int k = tid; k < kTileM * NPAD / 16; k += kThreads)
     reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
-  if (HAS_H)
+  if (MODE == kModeBias)
     for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.h != nullptr && k < n) ? P.h[k] : 0;
   if (L.sweeps > 0) {
-    const uint4* src = reinterpret_cast<const uint4*>(P.thr + static_cast<size_t>(t_begin) * stride);
+    const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t_begin) * stride);
     uint4* dst = reinterpret_cast<uint4*>(sT + (t_begin & 1) * SW);
     for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
   }
@@ -278,9 +297,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
       if (k < myc) {
         const int c = c0 + k;
         const uint32_t nb = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        const uint4 bytes = make_uint4(fp8x4_from_bits(nb & 0xF), fp8x4_from_bits((nb >> 4) & 0xF),
-                                       fp8x4_from_bits((nb >> 8) & 0xF), fp8x4_from_bits(nb >> 12));
-        *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = bytes;
+        *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = fp8x16_from_bits(nb);
       }
   }
   fence_proxy_async_smem();
@@ -309,8 +326,8 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   __syncthreads();
   bool aborted = *sAbort != 0;
   uint32_t phase = 0;
-  const uint32_t ioff = static_cast<uint32_t>(kMagicBits - imax);
-  const uint32_t imax2 = static_cast<uint32_t>(2 * imax);
+  // kModeBias: word index of field I is (bits of I + 1.5*2^23) - (0x4B400000 - imax).
+  const uint32_t ioff = kMagicBits - static_cast<uint32_t>(imax);
 
   // ---- sweep loop ----------------------------------------------------------------------
   for (int t = t_begin; t < t_end && !aborted; ++t) {
@@ -321,15 +338,17 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
     phase ^= 1;
     tc_fence_after();
     if (t + 1 < t_end) {  // stage the next step's thresholds (read after this sweep's barrier)
-      const uint4* src = reinterpret_cast<const uint4*>(P.thr + static_cast<size_t>(t + 1) * stride);
+      const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t + 1) * stride);
       uint4* dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
       for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
     }
     const uint32_t* tab = sT + (t & 1) * SW;
+    // kModeDiag: byte address of entry D is 2 * (bits of D + 1.5*2^23) + this bias (mod 2^32).
+    const uint32_t diag_bias = smem_u32(tab) + 2u * (kDiagEntries / 2) - 2u * kMagicBits;
     uint32_t nxt[kWordsPerThread];
 #pragma unroll
     for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
-    int eacc = 0;
+    float eacc = 0.0f;
     if (warp_active) {
 #pragma unroll
       for (int k = 0; k < kMaxSlots; ++k) {
@@ -339,36 +358,49 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
           tmem_ld16(tmem_warp + c * 16, v);
           tmem_wait_ld();
           const PhiloxOut o0 = philox4x32_10(2u * c, static_cast<uint32_t>(rg),
-                                             static_cast<uint32_t>(t), q, L.key_lo, L.key_hi);
+                                             static_cast<uint32_t>(t), q, key_lo, key_hi);
           const PhiloxOut o1 = philox4x32_10(2u * c + 1u, static_cast<uint32_t>(rg),
-                                             static_cast<uint32_t>(t), q, L.key_lo, L.key_hi);
+                                             static_cast<uint32_t>(t), q, key_lo, key_hi);
           const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-          const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-          uint32_t nb = 0;
+          uint32_t nb;
+          if (MODE == kModeDiag) {
+            // Sign bits of (draw - 16 M) are shifted in from the top: after 16 steps bit e
+            // is set iff key(e) < M, i.e. the new spin is -1.
+            uint32_t neg = 0;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            int ib = __float_as_int(__fadd_rn(__uint_as_float(v[e]), kMagic));
-            int hv = 0;
-            if (HAS_H) {
-              hv = sH[c * 16 + e];
-              ib += hv;
+            for (int e = 15; e >= 0; --e) {
+              const float f = __uint_as_float(v[e]);
+              const uint32_t ib = __float_as_uint(__fadd_rn(f, kMagic));
+              uint32_t m;
+              asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(ib * 2u + diag_bias));
+              const uint32_t w = rw[e >> 1];
+              const uint32_t d = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+              const uint32_t diff = d - (m << 4);
+              neg = __funnelshift_l(diff, neg, 1);
+              eacc += fabsf(f);
             }
-            const uint32_t idx = min(static_cast<uint32_t>(ib) - ioff, imax2);
-            const uint32_t w = tab[idx];
-            const uint32_t s = (ob >> e) & 1u;
-            const uint32_t thr = s ? (w >> 16) : (w & 0xFFFFu);
-            const uint32_t word = rw[e >> 1];
-            const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
-            nb |= (key >= thr ? 1u : 0u) << e;
-            const int term = ib - kMagicBits + hv;
-            eacc += s ? term : -term;
+            nb = ~neg & 0xFFFFu;
+          } else {
+            const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+            nb = 0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int hv = sH[c * 16 + e];
+              const uint32_t ib = __float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic)) + hv;
+              const uint32_t w = tab[ib - ioff];
+              const uint32_t s = (ob >> e) & 1u;
+              const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
+              const uint32_t word = rw[e >> 1];
+              const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+              nb |= (key >= th ? 1u : 0u) << e;
+              const int term = static_cast<int>(ib - kMagicBits) + hv;
+              eacc += static_cast<float>(s ? term : -term);
+            }
           }
           const int valid = n - c * 16;
           if (valid < 16) nb &= (1u << valid) - 1u;
           nxt[k >> 1] |= nb << ((k & 1) * 16);
-          const uint4 bytes = make_uint4(fp8x4_from_bits(nb & 0xF), fp8x4_from_bits((nb >> 4) & 0xF),
-                                         fp8x4_from_bits((nb >> 8) & 0xF), fp8x4_from_bits(nb >> 12));
-          *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = bytes;
+          *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = fp8x16_from_bits(nb);
         }
       }
     }
@@ -382,8 +414,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
       tc_fence_after();
       issue_fields();  // fields of s(t+1)
     }
-    const int etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
-    const int E = -(etot / 2);
+    const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    const int E = MODE == kModeDiag
+                      ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
+                      : -(static_cast<int>(etot) / 2);
     if (E < best_E) {
       best_E = E;
       best_t = t;
@@ -402,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
       *sAbort = 1;
     }
     tc_fence_after();
-    int eacc = 0;
+    float eacc = 0.0f;
     if (warp_active) {
 #pragma unroll
       for (int k = 0; k < kMaxSlots; ++k) {
@@ -414,9 +448,13 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
           const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            int term = __float_as_int(__fadd_rn(__uint_as_float(v[e]), kMagic)) - kMagicBits;
-            if (HAS_H) term += 2 * sH[c * 16 + e];
-            eacc += ((ob >> e) & 1u) ? term : -term;
+            if (MODE == kModeDiag) {
+              eacc += fabsf(__uint_as_float(v[e]));
+            } else {
+              const int term = static_cast<int>(__float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic)) -
+                                                kMagicBits) + 2 * sH[c * 16 + e];
+              eacc += static_cast<float>(((ob >> e) & 1u) ? term : -term);
+            }
           }
         }
       }
@@ -425,8 +463,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
     tc_fence_before();
     __syncthreads();
     aborted = *sAbort != 0;
-    const int etot = eacc + sPart[(t_end & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
-    const int E = -(etot / 2);
+    const float etot = eacc + sPart[(t_end & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    const int E = MODE == kModeDiag
+                      ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
+                      : -(static_cast<int>(etot) / 2);
     if (E < best_E) {
       best_E = E;
       best_t = t_end;
@@ -462,13 +502,14 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   if (warp == 0) tmem_dealloc(tmem, NPAD);
 }
 
-template <int NPAD, bool HAS_H>
+template <int NPAD, int MODE>
 cudaError_t launch_variant(const Launch& L, int blocks, cudaStream_t st) {
-  const int smem = sweep_tc_smem_bytes(NPAD, L.stride_words_max) + (HAS_H ? NPAD * 4 : 0);
-  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel<NPAD, HAS_H>,
+  const int smem = sweep_tc_smem_bytes(NPAD, MODE == kModeDiag ? kDiagEntries / 2 : L.stride_words_max) +
+                   (MODE == kModeBias ? NPAD * 4 : 0);
+  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel<NPAD, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  sweep_tc_kernel<NPAD, HAS_H><<<blocks, kThreads, smem, st>>>(L);
+  sweep_tc_kernel<NPAD, MODE><<<blocks, kThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -480,10 +521,10 @@ int sweep_tc_smem_bytes(int npad, int stride_words_max) {
 }
 
 cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
-                            bool has_h) {
+                            bool diag) {
   if (npad_max <= 128)
-    return has_h ? launch_variant<128, true>(L, blocks, st) : launch_variant<128, false>(L, blocks, st);
-  return has_h ? launch_variant<256, true>(L, blocks, st) : launch_variant<256, false>(L, blocks, st);
+    return diag ? launch_variant<128, kModeDiag>(L, blocks, st) : launch_variant<128, kModeBias>(L, blocks, st);
+  return diag ? launch_variant<256, kModeDiag>(L, blocks, st) : launch_variant<256, kModeBias>(L, blocks, st);
 }
 
 }  // namespace pim

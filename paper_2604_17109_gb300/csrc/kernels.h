@@ -18,7 +18,8 @@ __host__ __device__ inline uint32_t sw128_offset(int row, int k, int rows) {
 }
 
 // Staging (once per instance).
-cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+// diag != 0 puts that value on the diagonal of the image (inside n x n).
+cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
                                    cudaStream_t st);
 cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st);
 
@@ -27,6 +28,10 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
                               float xi, int steps, int imax, int stride_words,
                               uint32_t* d_thr, cudaStream_t st);
 
+// Re-index the thresholds by D = I + 256 s (D = -512..511, 16-bit entries); needs imax <= 255.
+cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
+                                   uint32_t* d_thr_diag, cudaStream_t st);
+
 // Initial spin bits: from Philox (d_init == nullptr) or from int8 +-1 spins [R][n].
 cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int max_words,
                              const int8_t* d_init, uint32_t key_lo, uint32_t key_hi,
@@ -34,7 +39,7 @@ cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int ma
 
 // Fused tensor-core sweep kernel (n <= 256).
 cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
-                            bool has_h);
+                            bool diag);
 int sweep_tc_smem_bytes(int npad, int stride_words_max);
 
 // Plain FP32 comparator path: per sweep one field GEMM and one update kernel.

@@ -17,7 +17,8 @@ struct Problem {
   const uint8_t* jimg;     // FP8 E4M3 couplings, npad x npad, 128B-swizzled K-major image
   const float* jf;         // float32 row-major n x n (plain path)
   const int32_t* h;        // int32 bias or nullptr
-  const uint32_t* thr;     // decision thresholds [steps][stride_words]
+  const uint32_t* thr;     // decision thresholds [steps][stride_words], entry I + imax
+  const uint32_t* thr_diag;  // 16-bit thresholds by D = I + 256 s, [steps][1024], entry D+512
   double* best_E;          // [R]
   double* final_E;         // [R]
   int32_t* best_t;         // [R]

@@ -50,6 +50,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int kMaxN = 8192;        // plain path limit
 constexpr int kMaxNTensor = 256;   // fused kernel limit
 constexpr int kMaxImaxTensor = 511;
+constexpr int kMaxImaxDiag = 255;  // |I| < 256: D = I + 256 s keeps the sign of s
 
 // Decision thresholds of one (schedule, c, field range), shared between instances.
 struct Schedule {
@@ -57,13 +58,15 @@ struct Schedule {
   int imax = 0;          // table covers I = -imax .. imax
   int stride_words = 0;  // per-step stride, multiple of 4 words (16 bytes)
   uint32_t* d_thr = nullptr;
+  uint32_t* d_thr_diag = nullptr;  // by D = I + 256 s (only when imax <= 255)
   int device = 0;
   ~Schedule() {
-    if (d_thr) {
+    if (d_thr || d_thr_diag) {
       int prev = 0;
       cudaGetDevice(&prev);
       cudaSetDevice(device);
       cudaFree(d_thr);
+      cudaFree(d_thr_diag);
       cudaSetDevice(prev);
     }
   }
@@ -104,6 +107,7 @@ struct pim_instance {
   double c = 1.0;
   int imax = 0;  // exact max_i sum_j |J_ij| + |h_i|
   bool has_h = false;
+  bool diag = false;  // image carries 256 on the diagonal (h = 0, imax <= 255)
   int8_t* d_J8 = nullptr;
   uint8_t* d_img = nullptr;
   float* d_jf = nullptr;
@@ -234,6 +238,14 @@ int build_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
   if ((rc = ck(launch_thresholds(d_tau, d_eta, d_z, xi, steps, imax, s->stride_words, s->d_thr, st),
                "threshold kernel")))
     return rc;
+  if (imax <= kMaxImaxDiag) {
+    if ((rc = ck(cudaMalloc(&s->d_thr_diag, static_cast<size_t>(steps) * 1024 * 2),
+                 "cudaMalloc diagonal thresholds")))
+      return rc;
+    if ((rc = ck(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, s->d_thr_diag, st),
+                 "diagonal threshold kernel")))
+      return rc;
+  }
   if ((rc = ck(cudaStreamSynchronize(st), "threshold build"))) return rc;
   cleanup();
   out = s;
@@ -322,9 +334,11 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
       return bail(e, "upload h");
   }
   if (n <= kMaxNTensor) {
+    p->diag = !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
     const size_t img = static_cast<size_t>(p->npad) * p->npad;
     if ((e = cudaMalloc(&p->d_img, img)) != cudaSuccess) return bail(e, "cudaMalloc J image");
-    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->d_img, nullptr)) != cudaSuccess)
+    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, nullptr)) !=
+        cudaSuccess)
       return bail(e, "stage J image");
   }
   if ((e = cudaMalloc(&p->d_jf, nn * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc Jf");
@@ -385,7 +399,6 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   int dev = 0;
   cudaGetDevice(&dev);
   int maxR = 0, max_words = 0, stride_max = 4, npad_max = 0;
-  bool any_h = false;
   for (int k = 0; k < count; ++k) {
     pim_instance* p = insts[k];
     if (!p) return fail(PIM_ERR_INVALID, "anneal: instance %d is NULL", k);
@@ -411,7 +424,6 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     max_words = std::max(max_words, p->words);
     stride_max = std::max(stride_max, p->sched->stride_words);
     npad_max = std::max(npad_max, p->npad);
-    any_h |= p->has_h;
   }
   if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
   for (int k = 0; k < count; ++k) {
@@ -429,6 +441,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.jf = p->d_jf;
     P.h = p->d_h;
     P.thr = p->sched->d_thr;
+    P.thr_diag = p->sched->d_thr_diag;
     P.best_E = p->d_bestE;
     P.final_E = p->d_finalE;
     P.best_t = p->d_bestT;
@@ -446,25 +459,35 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.has_target = std::isnan(tg) ? 0 : 1;
     P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
   }
-  std::vector<WorkItem> work[2];  // npad 128 / 256 groups
-  for (int k = 0; k < count; ++k)
-    for (int rb = 0; rb < replicas[k]; rb += 128) work[insts[k]->npad <= 128 ? 0 : 1].push_back({k, rb});
+  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias).
+  std::vector<WorkItem> work[4];
+  for (int k = 0; k < count; ++k) {
+    const int g = (insts[k]->npad <= 128 ? 0 : 1) + (insts[k]->diag ? 0 : 2);
+    for (int rb = 0; rb < replicas[k]; rb += 128) work[g].push_back({k, rb});
+  }
+  size_t nwork_total = 0;
+  for (auto& w : work) nwork_total += w.size();
 
   const size_t probs_bytes = probs.size() * sizeof(Problem);
-  const size_t work_bytes = (work[0].size() + work[1].size()) * sizeof(WorkItem);
+  const size_t work_bytes = nwork_total * sizeof(WorkItem);
   const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
   const size_t total = probs_bytes + work_bytes + init_bytes + 64;
   char* d_buf = nullptr;
   CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf(total);
   std::memcpy(h_buf.data(), probs.data(), probs_bytes);
-  std::memcpy(h_buf.data() + probs_bytes, work[0].data(), work[0].size() * sizeof(WorkItem));
-  std::memcpy(h_buf.data() + probs_bytes + work[0].size() * sizeof(WorkItem), work[1].data(),
-              work[1].size() * sizeof(WorkItem));
+  const WorkItem* d_work[4];
+  {
+    size_t off = probs_bytes;
+    for (int g = 0; g < 4; ++g) {
+      if (!work[g].empty())
+        std::memcpy(h_buf.data() + off, work[g].data(), work[g].size() * sizeof(WorkItem));
+      d_work[g] = reinterpret_cast<const WorkItem*>(d_buf + off);
+      off += work[g].size() * sizeof(WorkItem);
+    }
+  }
   if (init_bytes) std::memcpy(h_buf.data() + probs_bytes + work_bytes, init_spins, init_bytes);
   const Problem* d_probs = reinterpret_cast<const Problem*>(d_buf);
-  const WorkItem* d_work0 = reinterpret_cast<const WorkItem*>(d_buf + probs_bytes);
-  const WorkItem* d_work1 = d_work0 + work[0].size();
   const int8_t* d_init = init_bytes ? reinterpret_cast<const int8_t*>(d_buf + probs_bytes + work_bytes) : nullptr;
   CK(cudaMemcpyAsync(d_buf, h_buf.data(), total, cudaMemcpyHostToDevice, st), "upload launch buffer");
   if (!cont)
@@ -490,11 +513,11 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     CK(cudaFreeAsync(d_I, st), "cudaFreeAsync");
   } else {
     CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
-    for (int g = 0; g < 2; ++g) {
+    for (int g = 0; g < 4; ++g) {
       if (work[g].empty()) continue;
       Launch L{};
       L.probs = d_probs;
-      L.work = g == 0 ? d_work0 : d_work1;
+      L.work = d_work[g];
       L.nwork = static_cast<int>(work[g].size());
       L.t_begin = t_begin;
       L.sweeps = sweeps;
@@ -503,7 +526,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.cont = cont ? 1 : 0;
       L.stride_words_max = stride_max;
       L.err = d_err;
-      CK(launch_sweep_tc(L, g == 0 ? 128 : 256, L.nwork, st, any_h), "fused sweep kernel");
+      CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
     }
     CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
   }

@@ -27,10 +27,14 @@ CASES = [
     ("sk", 129, 130, 25, 5),    # just past one K block and one replica tile
     ("sk", 200, 200, 60, 6),    # two K blocks, ragged replica tile
     ("maxcut", 256, 64, 20, 7),  # largest fused size
+    ("sk2", 150, 140, 30, 8),   # couplings +-2: field range past 255, general-bias kernel
 ]
 
 
 def _inst(kind, n, seed):
+    if kind == "sk2":
+        base = sk_pm1(n, seed)
+        return Instance("sk", n, (2 * base.J).astype(np.int8), base.h, base.c / 2, seed)
     return sk_pm1(n, seed) if kind == "sk" else maxcut_er(n, seed)
 
 
