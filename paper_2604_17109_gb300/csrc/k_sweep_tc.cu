@@ -148,8 +148,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
+}
+
+// Wait for outstanding tensor-memory loads; the registers they fill are passed as
+// read-write operands so no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
 }
 
 // Four spins (low 4 bits of `nib`) -> four FP8 E4M3 bytes: +1 = 0x38, -1 = 0xB8.  The
@@ -177,6 +200,61 @@ constexpr int kModeDiag = 0;
 constexpr int kModeBias = 1;
 constexpr int kDiagOffset = 256;
 constexpr int kDiagEntries = 1024;  // D = -512 .. 511
+constexpr int kMaxPrefetch = 1;     // 16-byte table pieces per thread: 256 x 16 B covers 4 KB
+
+// One chunk of W = 16 or 8 consecutive spins of one replica in kModeDiag: load the fields
+// D from tensor memory, draw the noise block(s), decide, and add |D| to the energy sum.
+// Returns the new spins as bits (bit e = spin c*16+e is +1).
+template <int W>
+__device__ __forceinline__ uint32_t diag_chunk(uint32_t taddr, uint32_t c, uint32_t rg,
+                                               uint32_t t, uint32_t q, const uint32_t* rk,
+                                               uint32_t diag_bias, float& eacc) {
+  uint32_t v[W];
+  if constexpr (W == 16)
+    tmem_ld16(taddr, v);
+  else
+    tmem_ld8(taddr, v);
+  // The tensor-memory load runs while the noise block is generated.
+  const PhiloxOut o0 = philox4x32_10_rk(2u * c, rg, t, q, rk);
+  uint32_t rw[W / 2];
+  rw[0] = o0.x0;
+  rw[1] = o0.x1;
+  rw[2] = o0.x2;
+  rw[3] = o0.x3;
+  if constexpr (W == 16) {
+    const PhiloxOut o1 = philox4x32_10_rk(2u * c + 1u, rg, t, q, rk);
+    rw[4] = o1.x0;
+    rw[5] = o1.x1;
+    rw[6] = o1.x2;
+    rw[7] = o1.x3;
+  }
+  tmem_wait_ld(v);
+  // Sign bits of (draw - 16 M) are shifted in from the top: after the last step bit e is set
+  // iff key(e) < M, i.e. the new spin is -1.  Two shift chains and two energy sums keep the
+  // dependent sequences short.
+  uint32_t neg_hi = 0, neg_lo = 0;
+  float e_a = 0.0f, e_b = 0.0f;
+#pragma unroll
+  for (int e = W - 1; e >= 0; --e) {
+    const float f = __uint_as_float(v[e]);
+    const uint32_t ib = __float_as_uint(__fadd_rn(f, kMagic));
+    uint32_t m;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(ib * 2u + diag_bias));
+    const uint32_t w = rw[e >> 1];
+    const uint32_t d = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+    const uint32_t diff = d + m * 0xFFFFFFF0u;  // d - 16 m
+    if (e >= W / 2)
+      neg_hi = __funnelshift_l(diff, neg_hi, 1);
+    else
+      neg_lo = __funnelshift_l(diff, neg_lo, 1);
+    if (e & 1)
+      e_a += fabsf(f);
+    else
+      e_b += fabsf(f);
+  }
+  eacc += e_a + e_b;
+  return ~((neg_hi << (W / 2)) | neg_lo) & ((1u << W) - 1u);
+}
 
 template <int NPAD, int MODE>
 __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
@@ -220,7 +298,6 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
   const uint32_t bar_mma = smem_u32(&bars[0]);
   const uint32_t bar_j = smem_u32(&bars[1]);
-  const uint32_t key_lo = L.key_lo, key_hi = L.key_hi;
 
   // ---- prologue: TMEM, barriers, zeroed A operand, bias, first threshold table --------
   if (warp == 0) {
@@ -337,10 +414,15 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
     }
     phase ^= 1;
     tc_fence_after();
-    if (t + 1 < t_end) {  // stage the next step's thresholds (read after this sweep's barrier)
-      const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t + 1) * stride);
-      uint4* dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
-      for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
+    // Next step's thresholds: loaded into registers now, stored to the other table buffer
+    // after this sweep's epilogue (so the load latency overlaps the epilogue).
+    uint4 pre[kMaxPrefetch];
+    const uint4* pre_src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t + 1) * stride);
+    const bool do_pre = t + 1 < t_end;
+#pragma unroll
+    for (int j = 0; j < kMaxPrefetch; ++j) {
+      const int k = tid + j * kThreads;
+      if (do_pre && k < stride / 4) pre[j] = __ldg(pre_src + k);
     }
     const uint32_t* tab = sT + (t & 1) * SW;
     // kModeDiag: byte address of entry D is 2 * (bits of D + 1.5*2^23) + this bias (mod 2^32).
@@ -354,33 +436,29 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
       for (int k = 0; k < kMaxSlots; ++k) {
         if (k < myc) {
           const int c = c0 + k;
-          uint32_t v[16];
-          tmem_ld16(tmem_warp + c * 16, v);
-          tmem_wait_ld();
-          const PhiloxOut o0 = philox4x32_10(2u * c, static_cast<uint32_t>(rg),
-                                             static_cast<uint32_t>(t), q, key_lo, key_hi);
-          const PhiloxOut o1 = philox4x32_10(2u * c + 1u, static_cast<uint32_t>(rg),
-                                             static_cast<uint32_t>(t), q, key_lo, key_hi);
-          const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+          const int valid = n - c * 16;
           uint32_t nb;
           if (MODE == kModeDiag) {
-            // Sign bits of (draw - 16 M) are shifted in from the top: after 16 steps bit e
-            // is set iff key(e) < M, i.e. the new spin is -1.
-            uint32_t neg = 0;
-#pragma unroll
-            for (int e = 15; e >= 0; --e) {
-              const float f = __uint_as_float(v[e]);
-              const uint32_t ib = __float_as_uint(__fadd_rn(f, kMagic));
-              uint32_t m;
-              asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(ib * 2u + diag_bias));
-              const uint32_t w = rw[e >> 1];
-              const uint32_t d = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
-              const uint32_t diff = d - (m << 4);
-              neg = __funnelshift_l(diff, neg, 1);
-              eacc += fabsf(f);
+            if (valid > 8) {
+              nb = diag_chunk<16>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
+              if (valid < 16) nb &= (1u << valid) - 1u;
+              *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                  fp8x16_from_bits(nb);
+            } else {  // last chunk with at most 8 spins: half the work
+              nb = diag_chunk<8>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
+              if (valid < 8) nb &= (1u << valid) - 1u;
+              *reinterpret_cast<uint2*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                  make_uint2(fp8x4_from_bits(nb & 0xFu), fp8x4_from_bits((nb >> 4) & 0xFu));
             }
-            nb = ~neg & 0xFFFFu;
           } else {
+            uint32_t v[16];
+            tmem_ld16(tmem_warp + c * 16, v);
+            const PhiloxOut o0 = philox4x32_10_rk(2u * c, static_cast<uint32_t>(rg),
+                                                  static_cast<uint32_t>(t), q, L.round_keys);
+            const PhiloxOut o1 = philox4x32_10_rk(2u * c + 1u, static_cast<uint32_t>(rg),
+                                                  static_cast<uint32_t>(t), q, L.round_keys);
+            tmem_wait_ld(v);
+            const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
             const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
             nb = 0;
 #pragma unroll
@@ -396,15 +474,23 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
               const int term = static_cast<int>(ib - kMagicBits) + hv;
               eacc += static_cast<float>(s ? term : -term);
             }
+            if (valid < 16) nb &= (1u << valid) - 1u;
+            *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                fp8x16_from_bits(nb);
           }
-          const int valid = n - c * 16;
-          if (valid < 16) nb &= (1u << valid) - 1u;
           nxt[k >> 1] |= nb << ((k & 1) * 16);
-          *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = fp8x16_from_bits(nb);
         }
       }
     }
     sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    {
+      uint4* pre_dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
+#pragma unroll
+      for (int j = 0; j < kMaxPrefetch; ++j) {
+        const int k = tid + j * kThreads;
+        if (do_pre && k < stride / 4) pre_dst[k] = pre[j];
+      }
+    }
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -444,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
           const int c = c0 + k;
           uint32_t v[16];
           tmem_ld16(tmem_warp + c * 16, v);
-          tmem_wait_ld();
+          tmem_wait_ld(v);
           const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {

@@ -39,6 +39,18 @@ struct WorkItem {
   int rbase;
 };
 
+// Philox4x32-10 round keys for a 64-bit seed: rk[2r] = lo + r * 0x9E3779B9 and
+// rk[2r+1] = hi + r * 0xBB67AE85 (mod 2^32), r = 0..9 (the Weyl key schedule).
+inline void philox_round_keys(uint64_t seed, uint32_t* rk) {
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0;
+    rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 struct Launch {
   const Problem* probs;
   const WorkItem* work;
@@ -46,6 +58,7 @@ struct Launch {
   int t_begin;
   int sweeps;
   uint32_t key_lo, key_hi;
+  uint32_t round_keys[20];  // Philox round keys of (key_lo, key_hi)
   int cont;                // 1: keep previous best / first-hit records
   int stride_words_max;    // largest table stride among the problems (smem sizing)
   int* err;                // device error word

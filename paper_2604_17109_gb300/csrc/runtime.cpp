@@ -523,6 +523,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.sweeps = sweeps;
       L.key_lo = static_cast<uint32_t>(seed);
       L.key_hi = static_cast<uint32_t>(seed >> 32);
+      philox_round_keys(seed, L.round_keys);
       L.cont = cont ? 1 : 0;
       L.stride_words_max = stride_max;
       L.err = d_err;

@@ -22,6 +22,7 @@ CASES = [
     ("maxcut", 20, 32, 50, 1),
     ("sk", 1, 5, 7, 0),         # degenerate: no couplings, pure noise
     ("sk", 17, 40, 40, 2),      # ragged spins and replicas
+    ("maxcut", 60, 70, 40, 9),  # last 16-spin chunk holds 12 spins
     ("sk", 100, 128, 80, 3),
     ("maxcut", 128, 96, 30, 4),  # exactly one K block
     ("sk", 129, 130, 25, 5),    # just past one K block and one replica tile
