@@ -227,6 +227,52 @@ int pim_activation_levels(float b_t, int imax, int act_kind, int lut_levels, flo
 int pim_thresholds(pim_instance* inst, uint32_t* out, size_t cap_words, int* steps, int* imax,
                    int* stride_words);
 
+/*
+ * pim_anneal_noalloc -- the fused sweep path for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment entry point of the library.
+ *
+ * Who needs it: code that must not call cudaMalloc while it runs -- a real-time detection
+ * loop where an allocation can synchronise the device and stall every other stream, a host
+ * framework that owns all device memory through its own pool or a fixed arena and hands
+ * out only buffers it allocated, or a process whose memory budget was fixed at start-up.
+ * Such a caller passes its own inputs and outputs; every other buffer the path needs
+ * (staged couplings, activation and decision tables, launch descriptors, the device error
+ * word) lives in one file-scope device array of 16 MiB that every GPU which loads this
+ * library holds until the process exits.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *
+ * Runs sweeps 0 .. steps-1 of Eq. 4 with Gaussian noise and the tanh activation, h = 0,
+ * Philox initial spins, exactly as pim_create + pim_set_schedule(noise GAUSS, act TANH) +
+ * pim_anneal(t_begin 0, sweeps = steps, init NULL, flags 0) would, with the same results.
+ *   n, J, scale_c    host int8 row-major n x n couplings (symmetric, zero diagonal) with
+ *                    max_i sum_j |J_ij| <= 255; n <= PIM_NOALLOC_MAX_N; c > 0 as pim_create.
+ *   steps, beta, eta host float schedules of `steps` <= PIM_NOALLOC_MAX_STEPS entries; xi >= 0.
+ *   replicas         1 .. PIM_NOALLOC_MAX_REPLICAS; seed, instance_id, target_energy as
+ *                    pim_anneal (NaN disables the first hit).
+ *   best_E, best_t, first_hit_t, final_E   device arrays of `replicas` entries (outputs).
+ *   best_bits, final_bits   device uint32 arrays [replicas][words], words = 2*ceil(n/64);
+ *                    bit i of word i/32 of row r is set when spin i of replica r is +1.
+ *   cuda_stream      cudaStream_t (NULL = legacy default stream); the call returns after the
+ *                    anneal has finished on it.
+ * Set-up: the first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call before any stream
+ * capture.
+ * Sharing: every call uses the same array and leaves the last call's contents in it (the
+ * error word is cleared at the start of each call).  Calls whose work overlaps on the GPU
+ * would race on the array; this entry point serialises its own calls with a host lock and
+ * waits for its work, so it never overlaps itself.
+ * Errors: PIM_ERR_INVALID (sizes beyond the maxima, bad J, NULL pointers, bad schedule),
+ *         PIM_ERR_TIMEOUT, PIM_ERR_CUDA, PIM_ERR_UNSUPPORTED (device index >= 64).
+ */
+#define PIM_NOALLOC_MAX_N 256
+#define PIM_NOALLOC_MAX_STEPS 2048
+#define PIM_NOALLOC_MAX_REPLICAS 4096
+int pim_anneal_noalloc(int n, const int8_t* J, double scale_c, int steps, const float* beta,
+                       const float* eta, float xi, int replicas, uint64_t seed,
+                       uint32_t instance_id, double target_energy, double* best_E,
+                       int32_t* best_t, int32_t* first_hit_t, double* final_E,
+                       uint32_t* best_bits, uint32_t* final_bits, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

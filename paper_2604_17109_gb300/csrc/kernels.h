@@ -47,4 +47,7 @@ cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, in
                               int t_begin, int sweeps, uint32_t key_lo, uint32_t key_hi,
                               int cont, float* d_S, float* d_I, int* d_err, cudaStream_t st);
 
+// Sets the thread-local message returned by pim_last_error.
+void set_last_error(const char* msg);
+
 }  // namespace pim

@@ -259,6 +259,10 @@ int table_imax(const pim_instance* p) {
 
 }  // namespace
 
+namespace pim {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace pim
+
 // ----------------------------------------------------------------------------------------
 PIM_API const char* pim_last_error(void) { return g_last_error.c_str(); }
 

@@ -47,6 +47,10 @@ SIGNATURES = {
     "pim_activation_levels": (C.c_int, [C.c_float, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pim_thresholds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_anneal_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                     C.c_void_p, C.c_float, C.c_int, C.c_uint64, C.c_uint32,
+                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -220,3 +224,19 @@ def pim_thresholds(inst: int) -> tuple[np.ndarray, int]:
     out = np.empty((steps.value, stride.value), np.uint32)
     _check(lib().pim_thresholds(inst, _ptr(out), out.size, None, None, None), "pim_thresholds")
     return out, imax.value
+
+
+def pim_anneal_noalloc(J: np.ndarray, scale_c: float, beta, eta, xi: float, replicas: int,
+                       seed: int, instance_id: int, target, outputs: dict, stream=None) -> None:
+    """Allocation-free anneal.  `outputs` maps best_E, best_t, first_hit, final_E, best_bits,
+    final_bits to device pointers (ints) the caller owns."""
+    J = np.ascontiguousarray(J, dtype=np.int8)
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    eta = np.ascontiguousarray(eta, dtype=np.float32)
+    tgt = math.nan if target is None else float(target)
+    o = outputs
+    _check(lib().pim_anneal_noalloc(J.shape[0], _ptr(J), float(scale_c), beta.size, _ptr(beta),
+                                    _ptr(eta), float(xi), int(replicas), int(seed),
+                                    int(instance_id), tgt, o["best_E"], o["best_t"],
+                                    o["first_hit"], o["final_E"], o["best_bits"],
+                                    o["final_bits"], _stream(stream)), "pim_anneal_noalloc")
