@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,12 +35,14 @@ XI = 0.5
 WORKLOAD = "sk200_100inst_1024rep_2000sweeps"
 METRIC = "spin-updates/s"
 
-# Algorithmic operation count per spin update of the sweep (integer / FP32 ALU):
-#   noise: one Philox4x32-10 block per 8 spins; a round = 2 mul.lo + 2 mul.hi + 4 xor +
-#          2 key adds = 10 ops -> 100 ops per block -> 12.5 per spin
-#   key extraction 2, field-to-index 1, threshold lookup 1, spin select 1, compare 1,
-#   new-spin insert 1, energy accumulate 2, spin-to-operand write-back 1
-ALU_OPS_PER_SPIN_UPDATE = 12.5 + 2 + 1 + 1 + 1 + 1 + 1 + 2 + 1
+# Algorithmic work per spin update, in lane issue slots of the minimal instruction
+# sequence of the sweep epilogue (integer / FP32 issue is the binding resource; the tensor
+# work, 2N flops, runs on an otherwise idle pipe):
+#   noise: a Philox4x32-10 block per 8 spins; a round = 2 wide multiplies (hi and lo in one
+#          instruction each) + 2 three-input XORs with the round key = 4 -> 40 per block -> 5
+#   field to table index 2 (float-to-int, address), threshold lookup 1, key extraction 1,
+#   compare and collect the new spin 2, energy accumulate 1, spin write-back 0.75
+ALU_OPS_PER_SPIN_UPDATE = 5.0 + 2 + 1 + 1 + 2 + 1 + 0.75
 SM_COUNT = 152
 LANES_PER_SM = 128
 
@@ -302,6 +305,34 @@ def run_ours(args):
     e2e_s = _max_over_ranks(time.perf_counter() - e0, world) / e2e_steps
     e2e_value = updates_per_step * world / e2e_s
 
+    # ---- TTS99 against the plain FP32 path (same decisions, same success) ---------------
+    # Success of a replica: best energy <= 0.999 x the best energy found for its instance
+    # by any replica (the relaxed criterion of the supplementary CCTS section, with the
+    # putative ground state of this run in place of the unavailable reference energy).
+    step()
+    torch.cuda.synchronize()
+    best = [pim.pim_energies(hd)["best_E"] for hd in handles]
+    p_bar = float(np.mean([np.mean(b <= 0.999 * b.min()) for b in best]))
+    n_plain = 2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pim.pim_anneal_batch(handles[:n_plain], REPLICAS, sweeps, seed=0, instance_ids=ids[:n_plain],
+                         flags=pim.PIM_PATH_FP32REF, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms_per_instance = ev0.elapsed_time(ev1) / n_plain
+    plain_same = all(np.array_equal(pim.pim_energies(handles[k])["best_E"], best[k])
+                     for k in range(n_plain))
+    trials = math.log(0.01) / math.log(1.0 - p_bar) if 0.0 < p_bar < 1.0 else 1.0
+    ours_ms_per_instance = ms_per_step / n_inst
+    tts = {"p_bar": p_bar, "target": "0.999 x best energy found per instance",
+           "trials_for_99pct": trials,
+           "ours_ms": ours_ms_per_instance / REPLICAS * trials,
+           "plain_fp32_ms": plain_ms_per_instance / REPLICAS * trials,
+           "speedup_vs_plain_fp32": plain_ms_per_instance / ours_ms_per_instance,
+           "plain_fp32_identical_results": bool(plain_same),
+           "plain_sample": f"{n_plain} instances, one launch pair per sweep"}
+
     for hd in handles:
         pim.pim_destroy(hd)
 
@@ -334,6 +365,7 @@ def run_ours(args):
         "tensor_pipe": {"achieved_tflops": tensor_achieved, "peak_tflops": fp8_peak,
                         "frac": tensor_achieved / fp8_peak,
                         "peak_basis": f"bf16 {peak_kind} x 2 (fp8 nominal ratio)"},
+        "tts99": tts,
         "cpu_baseline": cpu_baseline(),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
