@@ -42,6 +42,11 @@ cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStrea
                             bool diag);
 int sweep_tc_smem_bytes(int npad, int stride_words_max);
 
+// Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs.
+cudaError_t launch_sweep_big(const BigLaunch& L, int blocks, cudaStream_t st);
+int sweep_big_tile_n();
+int sweep_big_max_blocks();  // co-resident CTAs on the current device (0 on error)
+
 // Plain FP32 comparator path: per sweep one field GEMM and one update kernel.
 cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, int nprob,
                               int t_begin, int sweeps, uint32_t key_lo, uint32_t key_hi,

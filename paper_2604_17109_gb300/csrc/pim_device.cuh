@@ -64,4 +64,21 @@ struct Launch {
   int* err;                // device error word
 };
 
+// Launch of the large-N kernel: one instance, all sweeps, cooperative grid of
+// (replica tiles) x (64-spin column blocks).
+struct BigLaunch {
+  Problem P;
+  uint8_t* s_img[2];       // FP8 spin images [npad/128][rpad][128 B] (A operand), ping-pong
+  float* energy;           // [3][rpad] rotating per-replica energy accumulators (zeroed)
+  unsigned int* bar;       // grid barrier {arrivals, generation, abort} (zeroed)
+  int rbase;               // first replica of this launch
+  int rpad;                // replica rows of this launch (multiple of 128)
+  int ncb;                 // column blocks = npad / 64
+  int t_begin;
+  int sweeps;
+  int cont;
+  uint32_t round_keys[20];
+  int* err;
+};
+
 }  // namespace pim

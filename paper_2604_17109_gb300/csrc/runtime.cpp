@@ -337,8 +337,8 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     if ((e = cudaMemcpy(p->d_h, h32, n * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e, "upload h");
   }
-  if (n <= kMaxNTensor) {
-    p->diag = !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
+  {
+    p->diag = n <= kMaxNTensor && !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
     const size_t img = static_cast<size_t>(p->npad) * p->npad;
     if ((e = cudaMalloc(&p->d_img, img)) != cudaSuccess) return bail(e, "cudaMalloc J image");
     if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, nullptr)) !=
@@ -392,6 +392,48 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
 
 namespace {
 
+// Large-N anneal of one instance: the replicas are split into groups of tiles that fit the
+// co-resident grid (each group is an independent cooperative launch); per launch scratch
+// (two spin images, energy accumulators, barrier words) comes from the stream-ordered pool.
+int launch_big(const Problem& P, int npad, int t_begin, int sweeps, uint64_t seed, bool cont,
+               int* d_err, cudaStream_t st) {
+  const int nt = sweep_big_tile_n();
+  const int ncb = npad / nt;
+  const int cap = sweep_big_max_blocks();
+  if (cap < ncb)
+    return fail(PIM_ERR_UNSUPPORTED, "anneal: n = %d needs %d co-resident CTAs, device holds %d",
+                P.n, ncb, cap);
+  const int tiles_total = (P.R + 127) / 128;
+  const int tiles_per_launch = std::min(tiles_total, cap / ncb);
+  for (int tile0 = 0; tile0 < tiles_total; tile0 += tiles_per_launch) {
+    const int tiles = std::min(tiles_per_launch, tiles_total - tile0);
+    const int rpad = tiles * 128;
+    const size_t img_bytes = static_cast<size_t>(rpad) * npad;
+    const size_t energy_bytes = sizeof(float) * 3 * rpad;
+    const size_t bytes = 2 * img_bytes + energy_bytes + 256;
+    char* d = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st), "cudaMallocAsync large-N scratch");
+    CK(cudaMemsetAsync(d + 2 * img_bytes, 0, energy_bytes + 256, st), "clear large-N scratch");
+    BigLaunch L{};
+    L.P = P;
+    L.s_img[0] = reinterpret_cast<uint8_t*>(d);
+    L.s_img[1] = reinterpret_cast<uint8_t*>(d + img_bytes);
+    L.energy = reinterpret_cast<float*>(d + 2 * img_bytes);
+    L.bar = reinterpret_cast<unsigned int*>(d + 2 * img_bytes + energy_bytes);
+    L.rbase = tile0 * 128;
+    L.rpad = rpad;
+    L.ncb = ncb;
+    L.t_begin = t_begin;
+    L.sweeps = sweeps;
+    L.cont = cont ? 1 : 0;
+    philox_round_keys(seed, L.round_keys);
+    L.err = d_err;
+    CK(launch_sweep_big(L, tiles * ncb, st), "large-N sweep kernel");
+    CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
+  }
+  return PIM_OK;
+}
+
 int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
                 int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
                 const int8_t* init_spins, int flags, cudaStream_t st) {
@@ -414,10 +456,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
                   static_cast<long long>(t_begin) + sweeps, p->sched->steps);
     if (cont && (!p->has_results || p->R != replicas[k]))
       return fail(PIM_ERR_STATE, "anneal: CONTINUE needs a previous run with the same replicas");
-    if (!ref && p->n > kMaxNTensor)
-      return fail(PIM_ERR_UNSUPPORTED, "anneal: n = %d > %d needs the plain path (PIM_PATH_FP32REF)",
-                  p->n, kMaxNTensor);
-    if (!ref && p->sched->imax > kMaxImaxTensor)
+    if (!ref && p->n <= kMaxNTensor && p->sched->imax > kMaxImaxTensor)
       return fail(PIM_ERR_UNSUPPORTED, "anneal: field range %d too large for the fused kernel",
                   p->sched->imax);
     for (int j = 0; j < k; ++j)
@@ -466,6 +505,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias).
   std::vector<WorkItem> work[4];
   for (int k = 0; k < count; ++k) {
+    if (insts[k]->n > kMaxNTensor) continue;  // large-N kernel, launched per instance below
     const int g = (insts[k]->npad <= 128 ? 0 : 1) + (insts[k]->diag ? 0 : 2);
     for (int rb = 0; rb < replicas[k]; rb += 128) work[g].push_back({k, rb});
   }
@@ -532,6 +572,11 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.stride_words_max = stride_max;
       L.err = d_err;
       CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
+    }
+    for (int k = 0; k < count; ++k) {
+      if (insts[k]->n <= kMaxNTensor) continue;
+      const int rc = launch_big(probs[k], insts[k]->npad, t_begin, sweeps, seed, cont, d_err, st);
+      if (rc != PIM_OK) return rc;
     }
     CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
   }

@@ -29,6 +29,8 @@ CASES = [
     ("sk", 200, 200, 60, 6),    # two K blocks, ragged replica tile
     ("maxcut", 256, 64, 20, 7),  # largest fused size
     ("sk2", 150, 140, 30, 8),   # couplings +-2: field range past 255, general-bias kernel
+    ("sk", 300, 200, 25, 10),   # large-N kernel: 6 column blocks x 2 replica tiles
+    ("maxcut", 520, 129, 15, 11),  # large-N kernel: ragged spins (last block) and replicas
 ]
 
 
@@ -209,12 +211,15 @@ def test_errors_are_reported():
         with pytest.raises(P.PimError) as e:
             P.pim_anneal(hd, 0, 3, 0)
         assert e.value.code == P.PIM_ERR_INVALID
-        big = sk_pm1(300, 0)
-        hb = P.pim_create(big.J, None, big.c)
+        rng = np.random.default_rng(0)
+        b40 = sk_pm1(40, 0)
+        wide = Instance("sk", 40, (16 * b40.J).astype(np.int8),
+                        rng.integers(-9, 9, 40).astype(np.int32), b40.c, 0)
+        hb = P.pim_create(wide.J, wide.h, wide.c)
         try:
             P.pim_set_schedule(hb, linear_beta(4), eta_power(linear_beta(4)), 0.5)
             with pytest.raises(P.PimError) as e:
-                P.pim_anneal(hb, 4, 2, 0)
+                P.pim_anneal(hb, 4, 2, 0)  # field range 16*39 > 511 for the fused kernel
             assert e.value.code == P.PIM_ERR_UNSUPPORTED
         finally:
             P.pim_destroy(hb)
@@ -239,3 +244,47 @@ def test_submit_poll_completes():
         assert_same(collect(hd, 64), want)
     finally:
         P.pim_destroy(hd)
+
+
+@pytest.mark.parametrize("flags", PATHS)
+def test_large_n_bias_and_resume(flags):
+    """Large-N kernel with a bias h and a resumed second segment."""
+    P = pim()
+    base = sk_pm1(400, 12)
+    rng = np.random.default_rng(2)
+    inst = Instance("sk", 400, base.J, rng.integers(-3, 4, 400).astype(np.int32), base.c, 12)
+    T = 24
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    full = oracle_run(inst, beta, eta, 0.5, replicas=70, seed=5, q=2, target=-2000)
+    hd = P.pim_create(inst.J, inst.h, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal(hd, 70, 10, 5, instance_id=2, target=-2000, flags=flags)
+        P.pim_anneal(hd, 70, 14, 5, instance_id=2, t_begin=10, target=-2000,
+                     flags=flags | P.PIM_CONTINUE)
+        assert_same(collect(hd, 400), full, label=f"large-N resume path={flags}")
+    finally:
+        P.pim_destroy(hd)
+
+
+def test_sk4096_sampled_replicas():
+    """SK N = 4096, 256 replicas: sampled replicas bit for bit against the oracle, every
+    replica's reported energies against its reported states."""
+    P = pim()
+    inst = sk_pm1(4096, 0)
+    T = 40
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal(hd, 256, T, 3, instance_id=1)
+        got = collect(hd, 4096)
+    finally:
+        P.pim_destroy(hd)
+    rows = [0, 77, 128, 255]
+    want = oracle_run(inst, beta, eta, 0.5, replica_ids=rows, seed=3, q=1)
+    assert_same(got, want, rows=rows, label="sk4096")
+    assert np.array_equal(oracle.energy(inst.J, inst.h, got["final_state"]), got["final_E"])
+    assert np.array_equal(oracle.energy(inst.J, inst.h, got["best_state"]), got["best_E"])
