@@ -1,13 +1,17 @@
 """Benchmark of the PIMI sweep path on GB300 (one JSON line on stdout, rank 0).
 
-Workload (default): SK-1 spin glasses, N = 200, J_ij = +-1 symmetric, zero diagonal,
+Default workload (sk200): SK-1 spin glasses, N = 200, J_ij = +-1 symmetric, zero diagonal,
 h = 0, 100 seeded instances x 1024 replicas x 2000 synchronous sweeps, linear beta
-0.1 -> 3, eta = sqrt(beta/5), xi = 0.5, c = 1/sqrt(N), Philox seed 0.  A step is one
-pass of the whole hot path over that batch: initial spins, 2000 fused sweeps (fields,
-decisions, spin write-back, energy and best-state tracking) and the final energy, in one
-batched launch.  Inputs are synthetic (generated, seeded).
+0.1 -> 3, eta = sqrt(beta/5), xi = 0.5, c = 1/sqrt(N), Philox seed 0.  A step is one pass
+of the whole hot path over that batch: initial spins, all fused sweeps (fields, decisions,
+spin write-back, energy and best-state tracking) and the final energies, in one batched
+launch.  Inputs are synthetic (generated, seeded).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Other workloads (for measurements of the other kernels, `--workload`):
+  sk4096     one SK-1 instance, N = 4096, 256 replicas x 10000 sweeps (large-N kernel)
+  maxcut100  one Erdos-Renyi Max-Cut instance, N = 100, 64 replicas x 1000 sweeps, xi = 0.7
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 
 Under torchrun every rank runs the same per-GPU workload on its own instance ids (weak
 scaling, no collective on the data path); times are max-reduced over ranks.
@@ -15,6 +19,7 @@ scaling, no collective on the data path); times are max-reduced over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -27,17 +32,33 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_SPINS = 200
-N_INST = 100
-REPLICAS = 1024
-SWEEPS = 2000
-XI = 0.5
-WORKLOAD = "sk200_100inst_1024rep_2000sweeps"
 METRIC = "spin-updates/s"
 
-# Algorithmic work per spin update, in lane issue slots of the minimal instruction
-# sequence of the sweep epilogue (integer / FP32 issue is the binding resource; the tensor
-# work, 2N flops, runs on an otherwise idle pipe):
+
+@dataclasses.dataclass
+class Workload:
+    key: str
+    kind: str      # "sk" or "maxcut"
+    n: int
+    count: int     # instances per GPU
+    replicas: int
+    sweeps: int
+    xi: float
+
+    @property
+    def name(self) -> str:
+        return f"{self.kind}{self.n}_{self.count}inst_{self.replicas}rep_{self.sweeps}sweeps"
+
+
+WORKLOADS = {
+    "sk200": Workload("sk200", "sk", 200, 100, 1024, 2000, 0.5),
+    "sk4096": Workload("sk4096", "sk", 4096, 1, 256, 10000, 0.5),
+    "maxcut100": Workload("maxcut100", "maxcut", 100, 1, 64, 1000, 0.7),
+}
+
+# Fused small-N kernel: algorithmic work per spin update, in lane issue slots of the
+# minimal instruction sequence of the sweep epilogue (integer / FP32 issue is the binding
+# resource; the tensor work, 2N flops, runs on an otherwise idle pipe):
 #   noise: a Philox4x32-10 block per 8 spins; a round = 2 wide multiplies (hi and lo in one
 #          instruction each) + 2 three-input XORs with the round key = 4 -> 40 per block -> 5
 #   field to table index 2 (float-to-int, address), threshold lookup 1, key extraction 1,
@@ -47,15 +68,15 @@ SM_COUNT = 152
 LANES_PER_SM = 128
 
 
-def _schedule(sweeps: int = SWEEPS):
+def _schedule(sweeps: int):
     from workloads import eta_power, linear_beta
     beta = linear_beta(sweeps)
     return beta, eta_power(beta)
 
 
-def _instances(rank: int, count: int = N_INST):
-    from workloads import sk_batch
-    return sk_batch(N_SPINS, count, first_seed=rank * count)
+def _instance(w: Workload, seed: int):
+    from workloads import maxcut_er, sk_pm1
+    return sk_pm1(w.n, seed) if w.kind == "sk" else maxcut_er(w.n, seed)
 
 
 def _peaks():
@@ -126,40 +147,50 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------- oracle (CPU)
-def _oracle_sample(budget_s: float, max_instances: int, replicas: int):
-    """Time the oracle as it stands on a bounded sample of the workload: whole 2000-sweep
-    runs of the first instances with `replicas` replicas each, until the time budget is
-    spent.  Returns (spin updates, seconds, description)."""
-    import numpy as np  # noqa: F401
+def _oracle_sample(w: Workload, budget_s: float, max_instances: int, replicas: int,
+                   sweeps: int):
+    """Time the oracle as it stands on a bounded sample of the workload: the first
+    `sweeps` sweeps of the first instances with `replicas` replicas each (the same
+    per-replica work per sweep as the workload), until the time budget is spent.
+    Returns (spin updates, seconds, description)."""
     import oracle
-    from workloads import sk_pm1
-    beta, eta = _schedule()
+    beta, eta = _schedule(w.sweeps)
     done, t0 = 0, time.perf_counter()
     k = 0
     while k < max_instances:
-        inst = sk_pm1(N_SPINS, k)
-        oracle.anneal(inst.J, inst.h, inst.c, beta, eta, XI, replicas=replicas, seed=0, q=k)
-        done += N_SPINS * replicas * SWEEPS
+        inst = _instance(w, k)
+        oracle.anneal(inst.J, inst.h, inst.c, beta, eta, w.xi, replicas=replicas, seed=0, q=k,
+                      sweeps=sweeps)
+        done += w.n * replicas * sweeps
         k += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return done, dt, (f"{k} instance(s) x {replicas} replicas x {SWEEPS} sweeps of the "
-                      f"{WORKLOAD} workload, single thread")
+    return done, dt, (f"{k} instance(s) x {replicas} replicas x {sweeps} sweeps of the "
+                      f"{w.name} workload, single thread")
+
+
+def _cpu_plan(w: Workload):
+    """(budget s, max instances, replicas, sweeps) of the CPU-baseline sample."""
+    if w.n <= 256:
+        return 15.0, 8, 16, w.sweeps
+    return 10.0, 1, 4, 20
 
 
 def _cpu_worker(argv):
-    budget, max_inst, reps = float(argv[0]), int(argv[1]), int(argv[2])
-    n, dt, desc = _oracle_sample(budget, max_inst, reps)
+    w = WORKLOADS[argv[0]]
+    budget, max_inst, reps, sweeps = float(argv[1]), int(argv[2]), int(argv[3]), int(argv[4])
+    n, dt, desc = _oracle_sample(w, budget, max_inst, reps, sweeps)
     print(json.dumps({"updates": n, "seconds": dt, "sample": desc}))
 
 
-def cpu_baseline(budget_s=15.0, max_instances=8, replicas=16):
+def cpu_baseline(w: Workload):
+    budget, max_inst, reps, sweeps = _cpu_plan(w)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
-                          str(budget_s), str(max_instances), str(replicas)],
-                         capture_output=True, text=True, env=env, timeout=600)
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", w.key,
+                          str(budget), str(max_inst), str(reps), str(sweeps)],
+                         capture_output=True, text=True, env=env, timeout=900)
     if res.returncode != 0:
         raise RuntimeError(res.stderr[-2000:])
     d = json.loads(res.stdout.strip().splitlines()[-1])
@@ -192,38 +223,37 @@ def _barrier(world: int):
 
 
 # ------------------------------------------------------------------------- reference arm
-def run_reference(args):
-    world, rank, _ = _dist()
+def run_reference(args, w: Workload):
+    _, rank, _ = _dist()
     if rank != 0:
         return 0
-    base = cpu_baseline(budget_s=5.0, max_instances=2, replicas=8)
-    vals = []
-    sample = None
+    _, _, reps, sweeps = _cpu_plan(w)
+    reps = min(reps, 8)
+    vals, sample = [], None
     for k in range(args.warmup + args.steps):
-        n, dt, sample = _oracle_sample(0.0, 1, 8)
+        n, dt, sample = _oracle_sample(w, 0.0, 1, reps, sweeps)
         if k >= args.warmup:
             vals.append(n / dt)
     value = statistics.mean(vals)
-    per_step_updates = N_SPINS * 8 * SWEEPS
+    per_step_updates = w.n * reps * sweeps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per_step_updates / value * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_SPINS, "instances": N_INST,
-                   "replicas": REPLICAS, "sweeps": SWEEPS,
-                   "sample_per_step": "1 instance x 8 replicas x 2000 sweeps"},
+        "config": {"workload": w.name, "n": w.n, "instances": w.count,
+                   "replicas": w.replicas, "sweeps": w.sweeps,
+                   "sample_per_step": f"1 instance x {reps} replicas x {sweeps} sweeps"},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "oracle_calibration": base,
     }
     print(json.dumps(line))
     return 0
 
 
 # ------------------------------------------------------------------------- our arm
-def run_ours(args):
+def run_ours(args, w: Workload):
     world, rank, local = _dist()
     import numpy as np
     import torch
@@ -236,9 +266,9 @@ def run_ours(args):
     from paper_2604_17109_gb300 import pim
 
     pkg_build.build()
-    n_inst, sweeps = args.instances, args.sweeps
+    n_inst, sweeps, R, N = w.count, w.sweeps, w.replicas, w.n
     beta, eta = _schedule(sweeps)
-    insts = _instances(rank, n_inst)
+    insts = [_instance(w, rank * n_inst + k) for k in range(n_inst)]
     ids = np.arange(rank * n_inst, (rank + 1) * n_inst, dtype=np.uint32)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -246,11 +276,11 @@ def run_ours(args):
     # ---- device-resident inputs: staged once, reused by every timed step -------------
     handles = [pim.pim_create(i.J, None, i.c) for i in insts]
     for hd in handles:
-        pim.pim_set_schedule(hd, beta, eta, XI)
-    updates_per_step = N_SPINS * REPLICAS * sweeps * n_inst
+        pim.pim_set_schedule(hd, beta, eta, w.xi)
+    updates_per_step = N * R * sweeps * n_inst
 
     def step():
-        pim.pim_anneal_batch(handles, REPLICAS, sweeps, seed=0, instance_ids=ids, stream=stream)
+        pim.pim_anneal_batch(handles, R, sweeps, seed=0, instance_ids=ids, stream=stream)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
@@ -271,9 +301,8 @@ def run_ours(args):
             starts[k].record(stream)
             step()
             ends[k].record(stream)
-            kernel_ms.append(None)
             ends[k].synchronize()
-            kernel_ms[-1] = pim.pim_kernel_ms(handles[0])
+            kernel_ms.append(pim.pim_kernel_ms(handles[0]))
         torch.cuda.synchronize()
         _barrier(world)
         wall = time.perf_counter() - wall0
@@ -286,8 +315,8 @@ def run_ours(args):
     # ---- end to end through the public API from host buffers ---------------------------
     e2e_steps = max(1, min(3, args.steps))
     h2d = sum(i.J.nbytes for i in insts)
-    R = REPLICAS
-    d2h = n_inst * (R * (8 + 4 + 4 + 8) + R * 8 * 4)
+    words = ((N + 63) // 64) * 2
+    d2h = n_inst * (R * (8 + 4 + 4 + 8) + R * words * 4)
     out_E = [None] * n_inst
     torch.cuda.synchronize()
     _barrier(world)
@@ -295,11 +324,11 @@ def run_ours(args):
     for _ in range(e2e_steps):
         hs = [pim.pim_create(i.J, None, i.c) for i in insts]
         for hd in hs:
-            pim.pim_set_schedule(hd, beta, eta, XI)
-        pim.pim_anneal_batch(hs, REPLICAS, sweeps, seed=0, instance_ids=ids, stream=stream)
+            pim.pim_set_schedule(hd, beta, eta, w.xi)
+        pim.pim_anneal_batch(hs, R, sweeps, seed=0, instance_ids=ids, stream=stream)
         for q, hd in enumerate(hs):
             out_E[q] = pim.pim_energies(hd)["best_E"]
-            pim.pim_best_state(hd, N_SPINS)
+            pim.pim_best_state(hd, N)
         for hd in hs:
             pim.pim_destroy(hd)
     e2e_s = _max_over_ranks(time.perf_counter() - e0, world) / e2e_steps
@@ -309,29 +338,31 @@ def run_ours(args):
     # Success of a replica: best energy <= 0.999 x the best energy found for its instance
     # by any replica (the relaxed criterion of the supplementary CCTS section, with the
     # putative ground state of this run in place of the unavailable reference energy).
-    step()
-    torch.cuda.synchronize()
-    best = [pim.pim_energies(hd)["best_E"] for hd in handles]
-    p_bar = float(np.mean([np.mean(b <= 0.999 * b.min()) for b in best]))
-    n_plain = 2
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    pim.pim_anneal_batch(handles[:n_plain], REPLICAS, sweeps, seed=0, instance_ids=ids[:n_plain],
-                         flags=pim.PIM_PATH_FP32REF, stream=stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms_per_instance = ev0.elapsed_time(ev1) / n_plain
-    plain_same = all(np.array_equal(pim.pim_energies(handles[k])["best_E"], best[k])
-                     for k in range(n_plain))
-    trials = math.log(0.01) / math.log(1.0 - p_bar) if 0.0 < p_bar < 1.0 else 1.0
-    ours_ms_per_instance = ms_per_step / n_inst
-    tts = {"p_bar": p_bar, "target": "0.999 x best energy found per instance",
-           "trials_for_99pct": trials,
-           "ours_ms": ours_ms_per_instance / REPLICAS * trials,
-           "plain_fp32_ms": plain_ms_per_instance / REPLICAS * trials,
-           "speedup_vs_plain_fp32": plain_ms_per_instance / ours_ms_per_instance,
-           "plain_fp32_identical_results": bool(plain_same),
-           "plain_sample": f"{n_plain} instances, one launch pair per sweep"}
+    tts = None
+    if N <= 256:
+        step()
+        torch.cuda.synchronize()
+        best = [pim.pim_energies(hd)["best_E"] for hd in handles]
+        p_bar = float(np.mean([np.mean(b <= 0.999 * b.min()) for b in best]))
+        n_plain = min(2, n_inst)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pim.pim_anneal_batch(handles[:n_plain], R, sweeps, seed=0, instance_ids=ids[:n_plain],
+                             flags=pim.PIM_PATH_FP32REF, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms_per_instance = ev0.elapsed_time(ev1) / n_plain
+        plain_same = all(np.array_equal(pim.pim_energies(handles[k])["best_E"], best[k])
+                         for k in range(n_plain))
+        trials = math.log(0.01) / math.log(1.0 - p_bar) if 0.0 < p_bar < 1.0 else 1.0
+        ours_ms_per_instance = ms_per_step / n_inst
+        tts = {"p_bar": p_bar, "target": "0.999 x best energy found per instance",
+               "trials_for_99pct": trials,
+               "ours_ms": ours_ms_per_instance / R * trials,
+               "plain_fp32_ms": plain_ms_per_instance / R * trials,
+               "speedup_vs_plain_fp32": plain_ms_per_instance / ours_ms_per_instance,
+               "plain_fp32_identical_results": bool(plain_same),
+               "plain_sample": f"{n_plain} instance(s), one launch pair per sweep"}
 
     for hd in handles:
         pim.pim_destroy(hd)
@@ -341,32 +372,37 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     clk = clocks.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
-    alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
-    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * sweeps * n_inst
+    flops = 2.0 * N * N * R * sweeps * n_inst
     fp8_peak = float(peaks["bf16_tflops"]) * 2.0
     tensor_achieved = flops / (k_ms * 1e-3) / 1e12
+    tensor = {"bound": "tensor", "achieved": tensor_achieved, "peak": fp8_peak,
+              "unit": "TFLOP/s", "frac": tensor_achieved / fp8_peak, "traffic": None,
+              "kernel_ms": k_ms,
+              "peak_basis": f"bf16 {peak_kind} burst x 2 (FP8/BF16 nominal ratio)"}
+    if N <= 256:
+        alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
+        alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                    "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": None,
+                    "kernel": "sweep_tc_kernel<256>", "kernel_ms": k_ms,
+                    "ops_per_spin_update": ALU_OPS_PER_SPIN_UPDATE,
+                    "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
+    else:
+        roofline = dict(tensor, kernel="sweep_big_kernel")
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8e4m3/i32",
         "data": "synthetic",
-        "config": {"workload": (WORKLOAD if (n_inst, sweeps) == (N_INST, SWEEPS) else
-                                f"sk200_{n_inst}inst_1024rep_{sweeps}sweeps"),
-                   "n": N_SPINS, "instances_per_gpu": n_inst,
-                   "replicas": REPLICAS, "sweeps": sweeps, "couplings": "SK +-1, h=0",
-                   "schedule": "linear beta 0.1->3, eta=sqrt(beta/5), xi=0.5",
+        "config": {"workload": w.name, "n": N, "instances_per_gpu": n_inst, "replicas": R,
+                   "sweeps": sweeps,
+                   "couplings": "SK +-1, h=0" if w.kind == "sk" else "ER(0.5) Max-Cut, J=-A",
+                   "schedule": f"linear beta 0.1->3, eta=sqrt(beta/5), xi={w.xi}",
                    "l2": "flushed between timed steps (256 MiB write)"},
-        "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
-                     "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": None,
-                     "kernel": "sweep_tc_kernel<256>", "kernel_ms": k_ms,
-                     "ops_per_spin_update": ALU_OPS_PER_SPIN_UPDATE,
-                     "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"},
-        "tensor_pipe": {"achieved_tflops": tensor_achieved, "peak_tflops": fp8_peak,
-                        "frac": tensor_achieved / fp8_peak,
-                        "peak_basis": f"bf16 {peak_kind} x 2 (fp8 nominal ratio)"},
+        "roofline": roofline,
+        "tensor_pipe": tensor,
         "tts99": tts,
-        "cpu_baseline": cpu_baseline(),
+        "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": 2 * args.steps,
@@ -387,13 +423,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--instances", type=int, default=N_INST,
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sk200")
+    ap.add_argument("--instances", type=int, default=None,
                     help="instances per GPU (smaller cases for profiling)")
-    ap.add_argument("--sweeps", type=int, default=SWEEPS, help="sweeps per anneal")
+    ap.add_argument("--sweeps", type=int, default=None, help="sweeps per anneal")
     args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.instances is not None or args.sweeps is not None:
+        w = dataclasses.replace(w, count=args.instances or w.count, sweeps=args.sweeps or w.sweeps)
     if args.impl == "reference":
-        return run_reference(args)
-    return run_ours(args)
+        return run_reference(args, w)
+    return run_ours(args, w)
 
 
 if __name__ == "__main__":
