@@ -3,13 +3,14 @@
 //
 // Per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
 //   fields   D[r, i] = sum_j S[r, j] J[i, j] for the CTA's 128 replicas and 64 spins: the
-//            K dimension (all N spins) streams through a 4-stage shared-memory ring filled
+//            K dimension (all N spins) streams through a 7-stage shared-memory ring filled
 //            by cp.async.bulk (spins of the tile from the global spin image, rows of J from
 //            the FP8 coupling image), consumed by tcgen05.mma kind::f8f6f4 into TMEM.
 //   decision 16 epilogue warps (4 TMEM lane quadrants x 4 column groups); each thread owns
 //            one replica and 16 spins for the whole anneal, keeps their old / new / best
 //            bits in registers, draws the Philox block, looks the threshold up by field
-//            I = D + h in the general table (read through L1), writes the new spins as FP8
+//            I = D + h in the step's threshold table (staged into shared memory while the
+//            MMAs run, or read through L1 when it is larger), writes the new spins as FP8
 //            bytes into the other spin image, and adds its share of sum_i s_i (I_i + h_i)
 //            to the replica's energy accumulator (global atomics, three rotating buffers).
 //   exchange a bounded grid barrier; every CTA then reads the replica energies of s(t),
@@ -25,7 +26,8 @@ namespace pim {
 namespace {
 
 constexpr int kNT = 64;           // spins (output columns) per CTA
-constexpr int kStages = 4;        // K-block ring depth
+constexpr int kStages = 7;        // K-block ring depth
+constexpr int kTabWords = 8192;   // threshold table of one step staged in shared memory
 constexpr int kABytes = 128 * 128;  // one K-block of the spin tile (128 rows x 128 B)
 constexpr int kBBytes = kNT * 128;  // one K-block of the coupling rows (64 rows x 128 B)
 constexpr int kEpiWarps = 16;
@@ -87,7 +89,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* sA = smem;                           // kStages x kABytes
   uint8_t* sB = sA + kStages * kABytes;         // kStages x kBBytes
-  float* sRed = reinterpret_cast<float*>(sB + kStages * kBBytes);  // [4 groups][128 rows]
+  uint32_t* sTab = reinterpret_cast<uint32_t*>(sB + kStages * kBBytes);  // [kTabWords]
+  float* sRed = reinterpret_cast<float*>(sTab + kTabWords);  // [4 groups][128 rows]
   int* sH = reinterpret_cast<int*>(sRed + 4 * 128);                // [kNT]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sH + kNT);          // full[S], empty[S], done
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
@@ -175,11 +178,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     uint32_t loads = 0, mmas = 0, done_phase = 0;
     const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(kNT >> 3) << 17) |
                            (static_cast<uint32_t>(128 >> 4) << 24);
-    // Stream the K blocks of image `img` and multiply: D = S_tile x J_block^T.
-    auto fields = [&](const uint8_t* img) -> bool {
+    // Producer (thread 0): stream the K blocks of image `img` (spins of the tile) and of the
+    // coupling rows of the column block into the ring.  A stage is refilled once the MMAs
+    // that read it have completed (its empty barrier).
+    auto produce = [&](const uint8_t* img) -> bool {
       const uint8_t* a_src = img + static_cast<size_t>(rt) * 128 * 128;
       const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * kNT * 128;
-      auto issue_load = [&](int kb) -> bool {
+      for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = loads % kStages, use = loads / kStages;
         if (use > 0 && !mbar_wait_bounded(bar_empty0 + 8 * s, (use - 1) & 1)) return false;
         mbar_expect_tx(bar_full0 + 8 * s, kABytes + kBBytes);
@@ -188,12 +193,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         bulk_g2s(smem_u32(sB + s * kBBytes), b_src + static_cast<size_t>(kb) * npad * 128, kBBytes,
                  bar_full0 + 8 * s);
         ++loads;
-        return true;
-      };
-      for (int kb = 0; kb < kStages - 1 && kb < kblocks; ++kb)
-        if (!issue_load(kb)) return false;
+      }
+      return true;
+    };
+    // MMA issuer (thread 32): D = S_tile x J_block^T, K block by K block as stages land; it
+    // never waits for an MMA to finish, only for data.
+    auto multiply = [&]() -> bool {
       for (int kb = 0; kb < kblocks; ++kb) {
-        if (kb + kStages - 1 < kblocks && !issue_load(kb + kStages - 1)) return false;
         const uint32_t s = mmas % kStages, use = mmas / kStages;
         if (!mbar_wait_bounded(bar_full0 + 8 * s, use & 1)) return false;
         tc_fence_after();
@@ -214,19 +220,31 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       const bool last = t == t_end;
       if (tid == 0) {
         fence_proxy_async_global();
-        if (!fields(L.s_img[cur_img])) {
+        if (!produce(L.s_img[cur_img])) {
+          atomicOr(L.err, kDevErrTimeout);
+          atomicExch(&L.bar[2], 1u);
+        }
+      } else if (tid == 32) {
+        if (!multiply()) {
           atomicOr(L.err, kDevErrTimeout);
           atomicExch(&L.bar[2], 1u);
         }
       }
       // Zero the energy buffer that sweep t+1 will accumulate into (see header).
-      if (cb == 0 && epi && grp == 0) {
-        __stcg(&L.energy[((t - t_begin + 1) % 3) * rpad + rl], 0.0f);
-        __threadfence();
-      }
+      if (cb == 0 && epi && grp == 0) __stcg(&L.energy[((t - t_begin + 1) % 3) * rpad + rl], 0.0f);
       float eacc = 0.0f;
       uint32_t nxt = 0;
+      const bool tab_in_smem = P.stride_words <= kTabWords;
       if (epi) {
+        // Stage this step's thresholds while the MMAs run (the previous step's reads ended
+        // before the last grid barrier), then sync the 16 epilogue warps.
+        if (tab_in_smem && !last) {
+          const uint4* src =
+              reinterpret_cast<const uint4*>(P.thr + static_cast<size_t>(t) * P.stride_words);
+          for (int k = tid - 64; k < P.stride_words / 4; k += kEpiWarps * 32)
+            reinterpret_cast<uint4*>(sTab)[k] = __ldg(src + k);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
         const bool ok = mbar_wait_bounded(bar_done, done_phase);
         if (!ok) {
           atomicOr(L.err, kDevErrTimeout);
@@ -245,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
           }
           tmem_wait_ld(v);
           const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-          const uint32_t* tab = P.thr + static_cast<size_t>(last ? t_begin : t) * P.stride_words;
+          const uint32_t* tab =
+              tab_in_smem ? sTab : P.thr + static_cast<size_t>(last ? t_begin : t) * P.stride_words;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int hv = sH[grp * 16 + e];
@@ -254,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
             const int term = I + hv;
             eacc += static_cast<float>(s ? term : -term);
             if (!last) {
-              const uint32_t w = __ldg(tab + (I + P.imax));
+              const uint32_t w = tab[I + P.imax];
               const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
               const uint32_t word = rw[e >> 1];
               const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
@@ -272,7 +291,6 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       if (epi && grp == 0) {
         const float tot = sRed[row] + sRed[128 + row] + sRed[256 + row] + sRed[384 + row];
         atomicAdd(&L.energy[((t - t_begin) % 3) * rpad + rl], tot);
-        __threadfence();
       }
       fence_proxy_async_global();
       if (!grid_barrier(L.bar, nblocks, L.err, sFlag)) goto teardown;
@@ -316,7 +334,8 @@ teardown:
 }  // namespace
 
 int sweep_big_smem_bytes() {
-  return 1024 + kStages * (kABytes + kBBytes) + 4 * 128 * 4 + kNT * 4 + (2 * kStages + 1) * 8 + 16;
+  return 1024 + kStages * (kABytes + kBBytes) + kTabWords * 4 + 4 * 128 * 4 + kNT * 4 +
+         (2 * kStages + 1) * 8 + 16;
 }
 
 int sweep_big_tile_n() { return kNT; }
