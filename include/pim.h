@@ -51,8 +51,8 @@ typedef enum pim_status {
 /* Element type of the host coupling matrix passed to pim_create. */
 typedef enum pim_j_type {
   PIM_J_INT8 = 0,  /* int8, integer couplings |J_ij| <= 16 (held exactly as FP8 E4M3) */
-  PIM_J_FP32 = 1,  /* float32 real couplings (not yet accepted: PIM_ERR_UNSUPPORTED) */
-  PIM_J_FP64 = 2   /* float64 real couplings (not yet accepted: PIM_ERR_UNSUPPORTED) */
+  PIM_J_FP32 = 1,  /* float32 real couplings, rounded to BF16 for the tensor cores (n <= 256) */
+  PIM_J_FP64 = 2   /* float64 real couplings, rounded to BF16 for the tensor cores (n <= 256) */
 } pim_j_type;
 
 /* Noise term of the update rule. */
@@ -81,17 +81,22 @@ typedef struct pim_instance pim_instance;
  * pim_create -- stage one Ising instance (J, h) on the device.
  * Defines the problem of Eq. 1 / Eq. 2 (Ising Hamiltonian and local field).
  *   out      receives the new handle (set to NULL on failure).
- *   n        number of spins, 1 <= n <= 256 for the fused kernel path.
+ *   n        number of spins, 1 <= n <= 8192 (integer couplings; the fused kernel serves
+ *            n <= 256, the large-N kernel n > 256); real couplings n <= 256.
  *   j_type   element type of J (pim_j_type).
  *   J        host, row-major n x n; must be symmetric with a zero diagonal.
  *   h        host bias, n entries: int32 when j_type == PIM_J_INT8, else the float type
- *            of J; NULL means h = 0.
+ *            of J (kept as float32); NULL means h = 0.
+ *            Real couplings are rounded to the nearest BF16 value (ties to even); fields
+ *            accumulate in FP32 and the decision of Eq. 4 is evaluated in FP32 on the device
+ *            (tanhf), so results agree with a float64 evaluation within FP32 error rather
+ *            than bit for bit.
  *   scale_c  coupling scale c > 0 applied after the multiply-accumulate (the paper's
  *            2/sqrt(N) for Max-Cut, 1/sqrt(N) for SK-1): the activation sees beta_t*c*I.
  *            Energies are reported in unscaled units of J and h.
- * Errors: PIM_ERR_INVALID (n out of range, J asymmetric, diagonal non-zero, |J| > 16,
- *         scale_c <= 0 or not finite), PIM_ERR_UNSUPPORTED (real-valued J),
- *         PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ * Errors: PIM_ERR_INVALID (n out of range, J asymmetric, diagonal non-zero, |J| > 16 for
+ *         integer J, non-finite values, scale_c <= 0 or not finite), PIM_ERR_UNSUPPORTED
+ *         (real-valued J with n > 256), PIM_ERR_NOMEM, PIM_ERR_CUDA.
  */
 int pim_create(pim_instance** out, int n, int j_type, const void* J, const void* h,
                double scale_c);

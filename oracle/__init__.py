@@ -14,6 +14,8 @@ from .pimi import (  # noqa: F401
     lut_tanh,
     activation,
     decide,
+    delta,
+    round_bf16,
     field,
     energy,
     anneal,

@@ -151,14 +151,26 @@ def activation(b_t: np.float32, I: np.ndarray, act: str = "tanh", lut_levels: in
     return vals.astype(np.float32)[inv].reshape(I.shape)
 
 
-def decide(tau: np.ndarray, s: np.ndarray, xi: float, eta_t: float, z: np.ndarray) -> np.ndarray:
-    """Eq. 4 sign decision in float32: delta = (tau + xi*s) + eta*z, s' = +1 iff delta >= 0."""
+def delta(tau: np.ndarray, s: np.ndarray, xi: float, eta_t: float, z: np.ndarray) -> np.ndarray:
+    """The argument of the sign in Eq. 4, in float32: (tau + xi*s) + eta*z."""
     tau = np.asarray(tau, dtype=np.float32)
     xi32 = np.float32(xi)
     a = tau + np.where(s > 0, xi32, -xi32).astype(np.float32)
     n = np.float32(eta_t) * np.asarray(z, dtype=np.float32)
-    delta = (a + n).astype(np.float32)
-    return np.where(delta >= np.float32(0.0), 1, -1).astype(np.int8)
+    return (a + n).astype(np.float32)
+
+
+def decide(tau: np.ndarray, s: np.ndarray, xi: float, eta_t: float, z: np.ndarray) -> np.ndarray:
+    """Eq. 4 sign decision in float32: s' = +1 iff delta >= 0 (sign(0) = +1)."""
+    return np.where(delta(tau, s, xi, eta_t, z) >= np.float32(0.0), 1, -1).astype(np.int8)
+
+
+def round_bf16(x) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16 value (8 significant bits, ties to even),
+    returned as float64: x = m 2^e with 1/2 <= |m| < 1, kept as rint(256 m) 2^(e-8)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0), e - 8)
 
 
 # ---------------------------------------------------------------------------------------

@@ -1,0 +1,335 @@
+// Fused PIMI sweep kernel for real-valued couplings (n <= 256): BF16 operands on the
+// tcgen05 tensor path (kind::f16, FP32 accumulation), decision in FP32.
+//
+// Same structure as the integer kernel (one CTA = one instance x 128-replica tile, all
+// sweeps inside, TMEM lane = replica, 4 lane quadrants x 2 column halves of threads), with:
+//   operands  A = spins as BF16 +-1 (exact), B = J rounded to BF16, both K-major with the
+//             128-byte swizzle; K advances 16 elements (32 bytes) per MMA.
+//   decision  Eq. 4 evaluated directly: x = b_t (I + h), tau = tanh(x) (or the L-level
+//             staircase of Algorithm "LUT-based tanh approximation"),
+//             delta = (tau + xi s) + eta_t z(key), s' = +1 iff delta >= 0, with the same
+//             Philox draws and 4096 noise levels as the integer path.
+//   energy    H = -1/2 sum_i s_i (I_i + h_i) accumulated in FP32.
+#include <cfloat>
+
+#include "kernels.h"
+#include "philox.cuh"
+#include "sm100_ptx.cuh"
+
+namespace pim {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTileM = 128;
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Eight spins (low 8 bits) -> eight BF16 values (+1 = 0x3F80, -1 = 0xBF80), 16 bytes.
+__device__ __forceinline__ uint4 bf16x8_from_bits(uint32_t b) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t lo = (b >> (2 * k)) & 1u, hi = (b >> (2 * k + 1)) & 1u;
+    w[k] = 0x3F803F80u | ((lo ^ 1u) << 15) | ((hi ^ 1u) << 31);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ float staircase(float x, int levels) {
+  if (x < -1.0f) return -1.0f;
+  if (x > 1.0f) return 1.0f;
+  int k = 0;
+  for (int kk = 1; kk < levels; ++kk)
+    if (x >= -1.0f + 2.0f * kk / levels) k = kk;
+  return -1.0f + 2.0f * k / (levels - 1);
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L) {
+  constexpr int kMaxSlots = NPAD / 32;
+  constexpr int kWordsPerThread = kMaxSlots / 2;
+  constexpr int kRowBytes = 2 * NPAD;  // bytes of one operand row (K = NPAD BF16 values)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sJ = smem;                                  // NPAD x kRowBytes
+  uint8_t* sA = sJ + NPAD * kRowBytes;                 // 128 x kRowBytes
+  float* sZ = reinterpret_cast<float*>(sA + kTileM * kRowBytes);  // 4096
+  float* sH = sZ + 4096;                               // NPAD
+  float* sPart = sH + NPAD;                            // [2][2][128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sPart + 2 * 2 * kTileM);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2);
+  int* sAbort = reinterpret_cast<int*>(sTmem + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;
+  const WorkItem wk = L.work[blockIdx.x];
+  const Problem& P = L.probs[wk.prob];
+  const int n = P.n, R = P.R;
+  const uint32_t q = P.q;
+  const int rg = wk.rbase + row;
+  const bool row_valid = rg < R;
+  const bool warp_active = (wk.rbase + quad * 32) < R;
+  const int nch = (n + 15) >> 4;
+  const int split = (n + 16) >> 5;
+  const int c0 = half == 0 ? 0 : split;
+  const int myc = half == 0 ? split : nch - split;
+  const int ksteps = (n + 15) >> 4;      // 16 BF16 values per MMA
+  const int mma_n = (n + 15) & ~15;
+  const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
+  const uint32_t bar_mma = smem_u32(&bars[0]);
+  const uint32_t bar_j = smem_u32(&bars[1]);
+  const float xi = P.xi;
+  const int act = P.act, levels = P.lut_levels;
+
+  if (warp == 0) {
+    tmem_alloc(smem_u32(sTmem), NPAD);
+    tmem_relinquish();
+  }
+  if (tid == 32) {
+    mbar_init(bar_mma, 1);
+    mbar_init(bar_j, 1);
+    fence_mbar_init();
+    *sAbort = 0;
+  }
+  for (int k = tid; k < kTileM * kRowBytes / 16; k += kThreads)
+    reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
+  for (int k = tid; k < 4096; k += kThreads) sZ[k] = P.zlev[k];
+  for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.hf != nullptr && k < n) ? P.hf[k] : 0.0f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+  const uint32_t tmem_warp = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+  if (tid == 0) {
+    constexpr uint32_t kJBytes = NPAD * kRowBytes;
+    mbar_expect_tx(bar_j, kJBytes);
+    for (uint32_t off = 0; off < kJBytes; off += 16384)
+      bulk_g2s(smem_u32(sJ + off), P.jimg + off, 16384u < kJBytes - off ? 16384u : kJBytes - off,
+               bar_j);
+  }
+
+  uint32_t cur[kWordsPerThread], best[kWordsPerThread];
+  const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
+#pragma unroll
+  for (int w = 0; w < kWordsPerThread; ++w) cur[w] = 0;
+  if (row_valid) {
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) cur[k >> 1] |= static_cast<uint32_t>(cur_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)]) << ((k & 1) * 16);
+  }
+  float best_E = FLT_MAX;
+  int best_t = -1, first_hit = -1;
+  const bool has_target = P.has_target != 0;
+  const double target = P.target_f;
+  if (L.cont && row_valid) {
+    best_E = static_cast<float>(P.best_E[rg]);
+    best_t = P.best_t[rg];
+    first_hit = P.first_hit[rg];
+    const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) best[w] = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) best[k >> 1] |= static_cast<uint32_t>(best_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)]) << ((k & 1) * 16);
+  } else {
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+  }
+
+  // Spins of 16 columns (chunk c) -> 32 bytes of the A operand row.
+  auto write_chunk = [&](int c, uint32_t nb) {
+    const int kbyte = c * 32;
+    *reinterpret_cast<uint4*>(sA + sw128_offset(row, kbyte, kTileM)) = bf16x8_from_bits(nb & 0xFFu);
+    *reinterpret_cast<uint4*>(sA + sw128_offset(row, kbyte + 16, kTileM)) = bf16x8_from_bits(nb >> 8);
+  };
+  if (warp_active) {
+#pragma unroll
+    for (int k = 0; k < kMaxSlots; ++k)
+      if (k < myc) write_chunk(c0 + k, (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+
+  const uint32_t idesc = idesc_bf16(kTileM, mma_n);
+  const uint32_t sA_addr = smem_u32(sA), sJ_addr = smem_u32(sJ);
+  auto issue_fields = [&]() {
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
+      mma_bf16(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
+               sw128_desc(sJ_addr + kb * (NPAD * 128) + ko), idesc, ks > 0 ? 1u : 0u);
+    }
+    mma_commit(bar_mma);
+  };
+  if (tid == 0) {
+    if (!mbar_wait_bounded(bar_j, 0)) {
+      atomicOr(L.err, kDevErrTimeout);
+      *sAbort = 1;
+    } else {
+      tc_fence_after();
+      issue_fields();
+    }
+  }
+  __syncthreads();
+  bool aborted = *sAbort != 0;
+  uint32_t phase = 0;
+
+  for (int t = t_begin; t <= t_end && !aborted; ++t) {
+    const bool last = t == t_end;
+    if (!mbar_wait_bounded(bar_mma, phase)) {
+      atomicOr(L.err, kDevErrTimeout);
+      *sAbort = 1;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    const float b = last ? 0.0f : P.sched_b[t];
+    const float eta = last ? 0.0f : P.sched_eta[t];
+    uint32_t nxt[kWordsPerThread];
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
+    float eacc = 0.0f;
+    if (warp_active) {
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k) {
+        if (k < myc) {
+          const int c = c0 + k;
+          uint32_t v[16];
+          tmem_ld16(tmem_warp + c * 16, v);
+          PhiloxOut o0{}, o1{};
+          if (!last) {
+            o0 = philox4x32_10_rk(2u * c, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
+                                  L.round_keys);
+            o1 = philox4x32_10_rk(2u * c + 1u, static_cast<uint32_t>(rg), static_cast<uint32_t>(t),
+                                  q, L.round_keys);
+          }
+          tmem_wait_ld(v);
+          const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+          const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+          uint32_t nb = 0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float hv = sH[c * 16 + e];
+            const float I = __fadd_rn(__uint_as_float(v[e]), hv);
+            const uint32_t s = (ob >> e) & 1u;
+            const float term = __fadd_rn(I, hv);
+            eacc += s ? term : -term;
+            if (!last) {
+              const float x = __fmul_rn(b, I);
+              const float tau = act == 0 ? tanhf(x) : staircase(x, levels);
+              const float a = __fadd_rn(tau, s ? xi : -xi);
+              const uint32_t word = rw[e >> 1];
+              const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+              const float delta = __fadd_rn(a, __fmul_rn(eta, sZ[key]));
+              nb |= (delta >= 0.0f ? 1u : 0u) << e;
+            }
+          }
+          const int valid = n - c * 16;
+          if (valid < 16) nb &= (1u << valid) - 1u;
+          nxt[k >> 1] |= nb << ((k & 1) * 16);
+          if (!last) write_chunk(c, nb);
+        }
+      }
+    }
+    sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    aborted = *sAbort != 0;
+    if (aborted) break;
+    if (tid == 0 && !last) {
+      tc_fence_after();
+      issue_fields();
+    }
+    const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    const float E = -0.5f * etot;
+    if (E < best_E) {
+      best_E = E;
+      best_t = t;
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+    }
+    if (has_target && first_hit < 0 && static_cast<double>(E) <= target) first_hit = t;
+    if (last) {
+      if (row_valid) {
+        uint16_t* cur_out = reinterpret_cast<uint16_t*>(P.cur_bits);
+        uint16_t* best_out = reinterpret_cast<uint16_t*>(P.best_bits);
+#pragma unroll
+        for (int k = 0; k < kMaxSlots; ++k)
+          if (k < myc) {
+            const size_t o = static_cast<size_t>(rg) * P.words * 2 + (c0 + k);
+            cur_out[o] = static_cast<uint16_t>(cur[k >> 1] >> ((k & 1) * 16));
+            best_out[o] = static_cast<uint16_t>(best[k >> 1] >> ((k & 1) * 16));
+          }
+        if (half == 0) {
+          P.best_E[rg] = static_cast<double>(best_E);
+          P.best_t[rg] = best_t;
+          P.first_hit[rg] = first_hit;
+          P.final_E[rg] = static_cast<double>(E);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) cur[w] = nxt[w];
+    }
+  }
+  if (aborted && tid == 0) mbar_wait_bounded(bar_mma, phase);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, NPAD);
+}
+
+template <int NPAD>
+cudaError_t launch_float_variant(const Launch& L, int blocks, cudaStream_t st) {
+  const int smem = sweep_float_smem_bytes(NPAD);
+  cudaError_t e = cudaFuncSetAttribute(sweep_float_kernel<NPAD>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  sweep_float_kernel<NPAD><<<blocks, kThreads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int sweep_float_smem_bytes(int npad) {
+  return 1024 + npad * 2 * npad + kTileM * 2 * npad + 4096 * 4 + npad * 4 + 2 * 2 * kTileM * 4 + 64;
+}
+
+cudaError_t launch_sweep_float(const Launch& L, int npad, int blocks, cudaStream_t st) {
+  return npad <= 128 ? launch_float_variant<128>(L, blocks, st)
+                     : launch_float_variant<256>(L, blocks, st);
+}
+
+// J (BF16 bits, row-major n x n) -> BF16 operand image (rows npad, K = npad values, 2 bytes
+// each, K-major with the 128-byte swizzle); zero outside n x n.  One thread per element.
+__global__ void stage_bf16_image_kernel(const uint16_t* __restrict__ J, int n, int npad,
+                                        uint8_t* __restrict__ img) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= static_cast<uint32_t>(npad) * npad) return;
+  const int i = e / npad, j = e % npad;
+  const uint16_t v = (i < n && j < n) ? J[static_cast<size_t>(i) * n + j] : 0;
+  *reinterpret_cast<uint16_t*>(img + sw128_offset(i, 2 * j, npad)) = v;
+}
+
+cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
+                                    cudaStream_t st) {
+  const uint32_t total = static_cast<uint32_t>(npad) * npad;
+  stage_bf16_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, d_img);
+  return cudaGetLastError();
+}
+
+}  // namespace pim

@@ -42,6 +42,12 @@ cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStrea
                             bool diag);
 int sweep_tc_smem_bytes(int npad, int stride_words_max);
 
+// Real-valued couplings (BF16 operands, FP32 decision), n <= 256.
+cudaError_t launch_sweep_float(const Launch& L, int npad, int blocks, cudaStream_t st);
+int sweep_float_smem_bytes(int npad);
+cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
+                                    cudaStream_t st);
+
 // Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs.
 cudaError_t launch_sweep_big(const BigLaunch& L, int blocks, cudaStream_t st);
 int sweep_big_tile_n();

@@ -31,6 +31,15 @@ struct Problem {
   uint32_t q;              // instance counter word of the noise stream
   int has_target;
   long long target;        // first-hit when energy <= target (integer couplings)
+  // Real-valued couplings (BF16 operand image in jimg):
+  const float* hf;         // float bias or nullptr
+  const float* sched_b;    // b_t = fl32(beta_t c), [steps]
+  const float* sched_eta;  // eta_t, [steps]
+  const float* zlev;       // 4096 noise levels
+  float xi;
+  int act;                 // 0 tanh, 1 L-level staircase
+  int lut_levels;
+  double target_f;         // first-hit when energy <= target_f (real couplings)
 };
 
 // One unit of work of the fused sweep kernel: (problem index, first replica).

@@ -20,6 +20,8 @@
 
 #define PIM_API extern "C" __attribute__((visibility("default")))
 
+extern "C" void pim_destroy(pim_instance* inst);
+
 using namespace pim;
 
 namespace {
@@ -59,14 +61,23 @@ struct Schedule {
   int stride_words = 0;  // per-step stride, multiple of 4 words (16 bytes)
   uint32_t* d_thr = nullptr;
   uint32_t* d_thr_diag = nullptr;  // by D = I + 256 s (only when imax <= 255)
+  // Real-valued couplings: the decision is evaluated on the device from these.
+  float* d_bt = nullptr;   // b_t = fl32(beta_t c)
+  float* d_eta = nullptr;  // eta_t
+  float* d_z = nullptr;    // 4096 noise levels
+  float xi = 0.0f;
+  int act = 0, lut = 0;
   int device = 0;
   ~Schedule() {
-    if (d_thr || d_thr_diag) {
+    if (d_thr || d_thr_diag || d_bt) {
       int prev = 0;
       cudaGetDevice(&prev);
       cudaSetDevice(device);
       cudaFree(d_thr);
       cudaFree(d_thr_diag);
+      cudaFree(d_bt);
+      cudaFree(d_eta);
+      cudaFree(d_z);
       cudaSetDevice(prev);
     }
   }
@@ -108,6 +119,8 @@ struct pim_instance {
   int imax = 0;  // exact max_i sum_j |J_ij| + |h_i|
   bool has_h = false;
   bool diag = false;  // image carries 256 on the diagonal (h = 0, imax <= 255)
+  bool real = false;  // real-valued couplings: BF16 operand image, float bias
+  float* d_hf = nullptr;
   int8_t* d_J8 = nullptr;
   uint8_t* d_img = nullptr;
   float* d_jf = nullptr;
@@ -281,6 +294,115 @@ PIM_API int pim_activation_levels(float b_t, int imax, int act_kind, int lut_lev
   return PIM_OK;
 }
 
+namespace {
+
+// Round a double to the nearest BF16 value (ties to even) and return its bit pattern.
+uint16_t bf16_bits_rne(double v) {
+  if (v == 0.0) return std::signbit(v) ? 0x8000u : 0u;
+  int e = 0;
+  const double m = std::frexp(v, &e);           // v = m 2^e, 0.5 <= |m| < 1
+  const double q = std::nearbyint(m * 256.0);   // 8 significant bits, ties to even
+  const float f = static_cast<float>(std::ldexp(q, e - 8));  // exact in float
+  uint32_t bits;
+  std::memcpy(&bits, &f, sizeof bits);
+  return static_cast<uint16_t>(bits >> 16);
+}
+
+// Real-valued couplings: J rounded to BF16 for the tensor-core operand, bias as float.
+int create_real(pim_instance** out, int n, int j_type, const void* J, const void* h, double c) {
+  if (n > kMaxNTensor)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_create: real-valued couplings need n <= %d", kMaxNTensor);
+  auto at = [&](const void* a, size_t k) -> double {
+    return j_type == PIM_J_FP32 ? static_cast<double>(static_cast<const float*>(a)[k])
+                                : static_cast<const double*>(a)[k];
+  };
+  std::vector<uint16_t> jb(static_cast<size_t>(n) * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double v = at(J, static_cast<size_t>(i) * n + j);
+      if (!std::isfinite(v) || std::fabs(v) > 1e30)
+        return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] not finite", i, j);
+      if (i == j && v != 0.0)
+        return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] != 0 (diagonal must be zero)", i, i);
+      if (v != at(J, static_cast<size_t>(j) * n + i))
+        return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", i, j);
+      jb[static_cast<size_t>(i) * n + j] = bf16_bits_rne(v);
+    }
+  std::vector<float> hf(n, 0.0f);
+  bool has_h = false;
+  if (h)
+    for (int i = 0; i < n; ++i) {
+      const double v = at(h, i);
+      if (!std::isfinite(v)) return fail(PIM_ERR_INVALID, "pim_create: h[%d] not finite", i);
+      hf[i] = static_cast<float>(v);
+      has_h |= hf[i] != 0.0f;
+    }
+  auto* p = new (std::nothrow) pim_instance();
+  if (!p) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");
+  cudaGetDevice(&p->device);
+  p->real = true;
+  p->n = n;
+  p->npad = n <= 128 ? 128 : 256;
+  p->words = ((n + 63) / 64) * 2;
+  p->c = c;
+  p->has_h = has_h;
+  auto bail = [&](cudaError_t e, const char* what) {
+    const int rc = cuda_fail(e, what);
+    pim_destroy(p);
+    return rc;
+  };
+  cudaError_t e;
+  uint16_t* d_tmp = nullptr;
+  const size_t nn = static_cast<size_t>(n) * n;
+  if ((e = cudaMalloc(&d_tmp, nn * 2)) != cudaSuccess) return bail(e, "cudaMalloc J");
+  if ((e = cudaMemcpy(d_tmp, jb.data(), nn * 2, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(d_tmp);
+    return bail(e, "upload J");
+  }
+  if ((e = cudaMalloc(&p->d_img, static_cast<size_t>(p->npad) * p->npad * 2)) != cudaSuccess) {
+    cudaFree(d_tmp);
+    return bail(e, "cudaMalloc J image");
+  }
+  e = launch_stage_bf16_image(d_tmp, n, p->npad, p->d_img, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_tmp);
+  if (e != cudaSuccess) return bail(e, "stage BF16 J image");
+  if (has_h) {
+    if ((e = cudaMalloc(&p->d_hf, n * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc h");
+    if ((e = cudaMemcpy(p->d_hf, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "upload h");
+  }
+  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  *out = p;
+  return PIM_OK;
+}
+
+int build_real_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
+                        const float* eta, float xi, int noise, int act, int lut, double c,
+                        int device) {
+  auto s = std::make_shared<Schedule>();
+  s->steps = steps;
+  s->device = device;
+  s->xi = xi;
+  s->act = act;
+  s->lut = lut;
+  std::vector<float> bt(steps);
+  for (int t = 0; t < steps; ++t) bt[t] = scaled_beta(beta[t], c);
+  std::vector<float> z(kNoiseLevels);
+  noise_levels(noise == PIM_NOISE_GAUSS ? 0 : 1, z.data());
+  CK(cudaMalloc(&s->d_bt, steps * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_eta, steps * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_z, kNoiseLevels * 4), "cudaMalloc schedule");
+  CK(cudaMemcpy(s->d_bt, bt.data(), steps * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_eta, eta, steps * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_z, z.data(), kNoiseLevels * 4, cudaMemcpyHostToDevice), "upload schedule");
+  out = s;
+  return PIM_OK;
+}
+
+}  // namespace
+
 PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, const void* h,
                        double scale_c) {
   if (!out) return fail(PIM_ERR_INVALID, "pim_create: out is NULL");
@@ -289,8 +411,7 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if (!J) return fail(PIM_ERR_INVALID, "pim_create: J is NULL");
   if (!(scale_c > 0.0) || !std::isfinite(scale_c))
     return fail(PIM_ERR_INVALID, "pim_create: scale_c must be finite and > 0");
-  if (j_type == PIM_J_FP32 || j_type == PIM_J_FP64)
-    return fail(PIM_ERR_UNSUPPORTED, "pim_create: real-valued couplings are not supported yet");
+  if (j_type == PIM_J_FP32 || j_type == PIM_J_FP64) return create_real(out, n, j_type, J, h, scale_c);
   if (j_type != PIM_J_INT8) return fail(PIM_ERR_INVALID, "pim_create: unknown j_type %d", j_type);
   const int8_t* J8 = static_cast<const int8_t*>(J);
   const int32_t* h32 = static_cast<const int32_t*>(h);
@@ -369,7 +490,7 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
   for (int t = 0; t < steps; ++t)
     if (!std::isfinite(beta[t]) || beta[t] < 0.0f || !std::isfinite(eta[t]) || eta[t] < 0.0f)
       return fail(PIM_ERR_INVALID, "pim_set_schedule: beta/eta[%d] must be finite and >= 0", t);
-  const int imax = table_imax(inst);
+  const int imax = inst->real ? -1 : table_imax(inst);  // -1 marks a real-valued schedule
   const std::string key = schedule_key(steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
                                        inst->c, imax, inst->device);
   std::shared_ptr<Schedule> s;
@@ -379,8 +500,10 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
     if (it != g_sched_cache.end()) s = it->second.lock();
   }
   if (!s) {
-    const int rc = build_schedule(s, steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
-                                  inst->c, imax, inst->device);
+    const int rc = inst->real ? build_real_schedule(s, steps, beta, eta, xi, noise_kind, act_kind,
+                                                    lut_levels, inst->c, inst->device)
+                              : build_schedule(s, steps, beta, eta, xi, noise_kind, act_kind,
+                                               lut_levels, inst->c, imax, inst->device);
     if (rc != PIM_OK) return rc;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched_cache[key] = s;
@@ -456,7 +579,9 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
                   static_cast<long long>(t_begin) + sweeps, p->sched->steps);
     if (cont && (!p->has_results || p->R != replicas[k]))
       return fail(PIM_ERR_STATE, "anneal: CONTINUE needs a previous run with the same replicas");
-    if (!ref && p->n <= kMaxNTensor && p->sched->imax > kMaxImaxTensor)
+    if (ref && p->real)
+      return fail(PIM_ERR_UNSUPPORTED, "anneal: the plain path takes integer couplings only");
+    if (!ref && !p->real && p->n <= kMaxNTensor && p->sched->imax > kMaxImaxTensor)
       return fail(PIM_ERR_UNSUPPORTED, "anneal: field range %d too large for the fused kernel",
                   p->sched->imax);
     for (int j = 0; j < k; ++j)
@@ -498,15 +623,25 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.stride_words = p->sched->stride_words;
     P.R = replicas[k];
     P.q = ids ? ids[k] : static_cast<uint32_t>(k);
+    P.hf = p->d_hf;
+    P.sched_b = p->sched->d_bt;
+    P.sched_eta = p->sched->d_eta;
+    P.zlev = p->sched->d_z;
+    P.xi = p->sched->xi;
+    P.act = p->sched->act;
+    P.lut_levels = p->sched->lut;
     const double tg = targets ? targets[k] : NAN;
     P.has_target = std::isnan(tg) ? 0 : 1;
     P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
+    P.target_f = std::isnan(tg) ? 0.0 : tg;
   }
-  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias).
-  std::vector<WorkItem> work[4];
+  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias | real-valued).
+  constexpr int kGroups = 6;
+  std::vector<WorkItem> work[kGroups];
   for (int k = 0; k < count; ++k) {
     if (insts[k]->n > kMaxNTensor) continue;  // large-N kernel, launched per instance below
-    const int g = (insts[k]->npad <= 128 ? 0 : 1) + (insts[k]->diag ? 0 : 2);
+    const int g = (insts[k]->npad <= 128 ? 0 : 1) +
+                  (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
     for (int rb = 0; rb < replicas[k]; rb += 128) work[g].push_back({k, rb});
   }
   size_t nwork_total = 0;
@@ -520,10 +655,10 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf(total);
   std::memcpy(h_buf.data(), probs.data(), probs_bytes);
-  const WorkItem* d_work[4];
+  const WorkItem* d_work[kGroups];
   {
     size_t off = probs_bytes;
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < kGroups; ++g) {
       if (!work[g].empty())
         std::memcpy(h_buf.data() + off, work[g].data(), work[g].size() * sizeof(WorkItem));
       d_work[g] = reinterpret_cast<const WorkItem*>(d_buf + off);
@@ -557,7 +692,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     CK(cudaFreeAsync(d_I, st), "cudaFreeAsync");
   } else {
     CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < kGroups; ++g) {
       if (work[g].empty()) continue;
       Launch L{};
       L.probs = d_probs;
@@ -571,7 +706,10 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.cont = cont ? 1 : 0;
       L.stride_words_max = stride_max;
       L.err = d_err;
-      CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
+      if (g >= 4)
+        CK(launch_sweep_float(L, (g & 1) ? 256 : 128, L.nwork, st), "real-valued sweep kernel");
+      else
+        CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
     }
     for (int k = 0; k < count; ++k) {
       if (insts[k]->n <= kMaxNTensor) continue;
@@ -721,6 +859,7 @@ PIM_API void pim_destroy(pim_instance* inst) {
   cudaFree(inst->d_img);
   cudaFree(inst->d_jf);
   cudaFree(inst->d_h);
+  cudaFree(inst->d_hf);
   inst->sched.reset();
   delete inst;
 }
@@ -729,6 +868,7 @@ PIM_API int pim_thresholds(pim_instance* inst, uint32_t* out, size_t cap_words, 
                            int* imax, int* stride_words) {
   if (!inst) return fail(PIM_ERR_INVALID, "pim_thresholds: instance is NULL");
   if (!inst->sched) return fail(PIM_ERR_STATE, "pim_thresholds: no schedule");
+  if (inst->real) return fail(PIM_ERR_STATE, "pim_thresholds: real-valued couplings have no tables");
   const Schedule& s = *inst->sched;
   if (steps) *steps = s.steps;
   if (imax) *imax = s.imax;

@@ -104,15 +104,20 @@ def pim_last_error() -> str:
 
 
 def pim_create(J: np.ndarray, h: np.ndarray | None = None, scale_c: float = 1.0) -> int:
-    """Stage an integer instance; returns the opaque handle (an int)."""
-    J = np.ascontiguousarray(J, dtype=np.int8)
+    """Stage an instance; integer J -> PIM_J_INT8 (int32 h), float J -> PIM_J_FP64 (float64
+    h).  Returns the opaque handle (an int)."""
+    J = np.asarray(J)
     n = J.shape[0]
     if J.shape != (n, n):
         raise ValueError("J must be square")
-    hh = None if h is None else np.ascontiguousarray(h, dtype=np.int32)
+    if np.issubdtype(J.dtype, np.floating):
+        jt, J = PIM_J_FP64, np.ascontiguousarray(J, dtype=np.float64)
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    else:
+        jt, J = PIM_J_INT8, np.ascontiguousarray(J, dtype=np.int8)
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.int32)
     out = C.c_void_p()
-    _check(lib().pim_create(C.byref(out), n, PIM_J_INT8, _ptr(J), _ptr(hh), float(scale_c)),
-           "pim_create")
+    _check(lib().pim_create(C.byref(out), n, jt, _ptr(J), _ptr(hh), float(scale_c)), "pim_create")
     return out.value
 
 

@@ -1,0 +1,108 @@
+"""GPU checks of the real-valued coupling path (BF16 operands, FP32 accumulation and decision)
+against the float64 oracle on the same BF16-rounded couplings.
+
+Bit-exactness is not expected here: the device accumulates the fields in FP32 and evaluates
+tanh in FP32, the oracle in float64.  The checks are (i) the energies the kernel reports
+for its own states agree with the float64 energies of those states, which bounds the field
+error, and (ii) one sweep from identical states makes identical decisions except where the
+oracle's decision margin |delta| is within the field / tanh error bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pimi
+from workloads import Instance, eta_power, linear_beta, maxcut_gauss, random_spins
+
+from gpu_helpers import collect, pim
+
+pytestmark = pytest.mark.gpu
+
+FIELD_REL_TOL = 1e-2   # relative field error target for BF16 couplings (stated bound)
+
+
+def _gauss(n, seed, with_h=False):
+    base = maxcut_gauss(n, seed)
+    J = pimi.round_bf16(base.J)
+    h = pimi.round_bf16(np.random.default_rng(seed).standard_normal(n)) if with_h else \
+        np.zeros(n)
+    return Instance("maxcut_gauss", n, J, h, base.c, seed)
+
+
+def _run(inst, beta, eta, xi, R, seed, init=None, sweeps=None, target=None):
+    P = pim()
+    hd = P.pim_create(inst.J, inst.h if np.any(inst.h) else None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, xi)
+        P.pim_anneal(hd, R, len(beta) if sweeps is None else sweeps, seed, init_spins=init,
+                     target=target)
+        e = P.pim_energies(hd)
+        out = dict(best_E=e["best_E"], final_E=e["final_E"], best_t=e["best_t"],
+                   first_hit=e["first_hit"], best_state=P.pim_best_state(hd, inst.n),
+                   final_state=P.pim_final_state(hd, inst.n))
+    finally:
+        P.pim_destroy(hd)
+    return out
+
+
+@pytest.mark.parametrize("n,with_h", [(64, True), (100, False), (200, True), (256, False)])
+def test_real_energies_match_float64(n, with_h):
+    """Energies reported by the kernel for its best and final states agree with float64
+    energies of those states (BF16 couplings, FP32 accumulation)."""
+    inst = _gauss(n, 3, with_h)
+    T = 150
+    beta = linear_beta(T)
+    got = _run(inst, beta, eta_power(beta), 0.7, 160, 9)
+    for which in ("best", "final"):
+        E64 = oracle.energy(inst.J, inst.h, got[f"{which}_state"])
+        scale = 0.5 * np.abs(inst.J).sum() + np.abs(inst.h).sum()
+        err = np.abs(got[f"{which}_E"] - E64) / scale
+        assert err.max() < 1e-5, (which, err.max())
+    assert np.all(got["best_E"] <= got["final_E"] + 1e-3)
+
+
+def test_real_one_sweep_decisions_match_oracle():
+    """From identical host-given states, one sweep gives the oracle's decisions wherever the
+    oracle's margin |delta| exceeds the error bound of FP32 fields and tanh."""
+    inst = _gauss(200, 5, True)
+    R = 256
+    T = 4
+    beta = np.full(T, 2.0, np.float32)
+    eta = np.full(T, 0.4, np.float32)
+    xi = 0.5
+    init = random_spins(200, R, seed=6)
+    got = _run(inst, beta, eta, xi, R, 13, init=init, sweeps=1)
+    # oracle: fields in float64 from the same BF16 couplings, then Eq. 4 in float32
+    I = oracle.field(inst.J, inst.h, init)
+    b = np.float32(np.float64(beta[0]) * inst.c)
+    tau = oracle.activation(b, I)
+    d = oracle.noise_draw16(13, 0, np.arange(R)[:, None], 0, np.arange(200)[None, :])
+    z = pimi.gaussian_quantiles()[d >> 4]
+    delta = pimi.delta(tau, init, xi, eta[0], z)
+    want = np.where(delta >= 0, 1, -1)
+    bound = 1e-4
+    differ = got["final_state"] != want
+    assert np.all(np.abs(delta[differ]) < bound), np.abs(delta[differ]).max(initial=0)
+    assert differ.mean() < 1e-3
+    # field error of the kernel's energy of the initial state vs float64
+    E0 = oracle.energy(inst.J, inst.h, init)
+    assert np.all(np.abs(got["best_E"] - np.minimum(E0, oracle.energy(inst.J, inst.h,
+                                                                       got["final_state"])))
+                  <= FIELD_REL_TOL * (0.5 * np.abs(inst.J).sum()))
+
+
+def test_real_rejects_plain_path_and_large_n():
+    P = pim()
+    inst = _gauss(40, 1)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, linear_beta(4), eta_power(linear_beta(4)), 0.5)
+        with pytest.raises(P.PimError) as e:
+            P.pim_anneal(hd, 8, 2, 0, flags=P.PIM_PATH_FP32REF)
+        assert e.value.code == P.PIM_ERR_UNSUPPORTED
+    finally:
+        P.pim_destroy(hd)
+    big = _gauss(300, 1)
+    with pytest.raises(P.PimError) as e:
+        P.pim_create(big.J, None, big.c)
+    assert e.value.code == P.PIM_ERR_UNSUPPORTED

@@ -327,3 +327,15 @@ def test_n_trials_closed_forms():
     assert math.isclose(oracle.n_trials(0.5), math.log2(1000), rel_tol=1e-12)
     assert oracle.n_trials(1.0) == 1.0
     assert math.isclose(oracle.tts99(2.0, 0.9), 2.0 * 2.0, rel_tol=1e-12)
+
+
+def test_round_bf16_examples():
+    """bfloat16 keeps 8 significant bits: 1 + 2^-8 is a tie and rounds to even (1.0),
+    1 + 3 * 2^-8 rounds up to 1 + 2^-6, and representable values are unchanged."""
+    x = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -3.140625, 0.0, 2.0 ** -130, 1.0 + 2 ** -7])
+    want = np.array([1.0, 1.0 + 2.0 ** -6, -3.140625, 0.0, 2.0 ** -130, 1.0 + 2 ** -7])
+    assert np.array_equal(pimi.round_bf16(x), want)
+    r = pimi.round_bf16(np.random.default_rng(0).standard_normal(1000))
+    assert np.array_equal(pimi.round_bf16(r), r)
+    f32 = r.astype(np.float32).view(np.uint32)
+    assert np.all(f32 & 0xFFFF == 0)
