@@ -211,9 +211,16 @@ def _max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _instance_ids(rank: int, count: int):
+    """Instance ids (Philox counter words) of one rank: disjoint across ranks, so the
+    ranks run independent problems with no exchange (weak scaling)."""
+    return list(range(rank * count, (rank + 1) * count))
 
 
 def _barrier(world: int):
@@ -268,8 +275,8 @@ def run_ours(args, w: Workload):
     pkg_build.build()
     n_inst, sweeps, R, N = w.count, w.sweeps, w.replicas, w.n
     beta, eta = _schedule(sweeps)
-    insts = [_instance(w, rank * n_inst + k) for k in range(n_inst)]
-    ids = np.arange(rank * n_inst, (rank + 1) * n_inst, dtype=np.uint32)
+    ids = np.asarray(_instance_ids(rank, n_inst), dtype=np.uint32)
+    insts = [_instance(w, int(q)) for q in ids]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

@@ -208,6 +208,19 @@ void pim_destroy(pim_instance* inst);
 const char* pim_last_error(void);
 
 /*
+ * pim_set_fault_injection -- testing hook for the failure handling of the fused kernels
+ * (no counterpart in the paper).  Applies to launches made after the call, process-wide.
+ *   mode           0 = off; 1 = the sweep kernels skip their first field computation (no MMA
+ *                  issued, no operand loaded), so their first bounded wait cannot complete.
+ *   wait_limit_ns  limit of every device-side wait of later launches (0 = 2 s).
+ * With mode 1 the kernel gives up after the limit, stops every thread at the next barrier,
+ * releases its tensor memory and returns; the next synchronising call on the instance
+ * reports PIM_ERR_TIMEOUT and the CUDA context stays usable.
+ * Errors: PIM_ERR_INVALID (unknown mode).
+ */
+int pim_set_fault_injection(int mode, uint64_t wait_limit_ns);
+
+/*
  * Inspection entry points (host only; no GPU needed).
  * pim_noise_levels -- the 4096 float32 noise levels z(m) the decision tables use:
  *   Gaussian: z(m) = fl32(Phi^-1((m+0.5)/4096)) for m < 2048 and z(4095-m) = -z(m);

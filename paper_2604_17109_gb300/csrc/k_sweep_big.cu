@@ -32,7 +32,6 @@ constexpr int kABytes = 128 * 128;  // one K-block of the spin tile (128 rows x 
 constexpr int kBBytes = kNT * 128;  // one K-block of the coupling rows (64 rows x 128 B)
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
-constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
   uint32_t v;
@@ -51,7 +50,9 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 // Grid-wide barrier with a time bound.  bar[0] = arrivals, bar[1] = generation,
 // bar[2] = abort flag.  Returns false (on all threads of the CTA) when the barrier gave up
 // or another CTA aborted.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err, int* sflag) {
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err, int* sflag,
+                             uint64_t limit_ns) {
+  const uint64_t limit = limit_ns ? limit_ns : 2000000000ull;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -68,7 +69,7 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err, 
           ok = 0;
           break;
         }
-        if (global_ns() - t0 > kWaitNs) {
+        if (global_ns() - t0 > limit) {
           atomicOr(err, kDevErrTimeout);
           atomicExch(&bar[2], 1u);
           ok = 0;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
   };
   write_image(L.s_img[0], cur & vmask);
   fence_proxy_async_global();
-  if (!grid_barrier(L.bar, nblocks, L.err, sFlag)) goto teardown;
+  if (!grid_barrier(L.bar, nblocks, L.err, sFlag, L.wait_ns)) goto teardown;
 
   {
     uint32_t loads = 0, mmas = 0, done_phase = 0;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * kNT * 128;
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = loads % kStages, use = loads / kStages;
-        if (use > 0 && !mbar_wait_bounded(bar_empty0 + 8 * s, (use - 1) & 1)) return false;
+        if (use > 0 && !mbar_wait_bounded(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
         mbar_expect_tx(bar_full0 + 8 * s, kABytes + kBBytes);
         bulk_g2s(smem_u32(sA + s * kABytes), a_src + static_cast<size_t>(kb) * rpad * 128, kABytes,
                  bar_full0 + 8 * s);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     auto multiply = [&]() -> bool {
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = mmas % kStages, use = mmas / kStages;
-        if (!mbar_wait_bounded(bar_full0 + 8 * s, use & 1)) return false;
+        if (!mbar_wait_bounded(bar_full0 + 8 * s, use & 1, L.wait_ns)) return false;
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
@@ -220,7 +221,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       const bool last = t == t_end;
       if (tid == 0) {
         fence_proxy_async_global();
-        if (!produce(L.s_img[cur_img])) {
+        // Injected fault: nothing is loaded in the first sweep, so the MMA thread's first
+        // wait cannot complete.
+        if (!(L.inject == 1 && t == t_begin) && !produce(L.s_img[cur_img])) {
           atomicOr(L.err, kDevErrTimeout);
           atomicExch(&L.bar[2], 1u);
         }
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
             reinterpret_cast<uint4*>(sTab)[k] = __ldg(src + k);
         }
         asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-        const bool ok = mbar_wait_bounded(bar_done, done_phase);
+        const bool ok = mbar_wait_bounded(bar_done, done_phase, L.wait_ns);
         if (!ok) {
           atomicOr(L.err, kDevErrTimeout);
           atomicExch(&L.bar[2], 1u);
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         atomicAdd(&L.energy[((t - t_begin) % 3) * rpad + rl], tot);
       }
       fence_proxy_async_global();
-      if (!grid_barrier(L.bar, nblocks, L.err, sFlag)) goto teardown;
+      if (!grid_barrier(L.bar, nblocks, L.err, sFlag, L.wait_ns)) goto teardown;
       if (epi) {
         // L2 read: the accumulator was written by other SMs during this sweep.
         const float etot = __ldcg(&L.energy[((t - t_begin) % 3) * rpad + rl]);

@@ -177,10 +177,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
     mma_commit(bar_mma);
   };
   if (tid == 0) {
-    if (!mbar_wait_bounded(bar_j, 0)) {
+    if (!mbar_wait_bounded(bar_j, 0, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
-    } else {
+    } else if (L.inject != 1) {  // injected fault: the first wait below cannot complete
       tc_fence_after();
       issue_fields();
     }
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
 
   for (int t = t_begin; t <= t_end && !aborted; ++t) {
     const bool last = t == t_end;
-    if (!mbar_wait_bounded(bar_mma, phase)) {
+    if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
     }
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
       for (int w = 0; w < kWordsPerThread; ++w) cur[w] = nxt[w];
     }
   }
-  if (aborted && tid == 0) mbar_wait_bounded(bar_mma, phase);
+  if (aborted && tid == 0) mbar_wait_bounded(bar_mma, phase, L.wait_ns);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, NPAD);

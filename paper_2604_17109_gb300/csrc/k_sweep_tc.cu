@@ -231,10 +231,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   };
 
   if (tid == 0) {
-    if (!mbar_wait_bounded(bar_j, 0)) {
+    if (!mbar_wait_bounded(bar_j, 0, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
-    } else {
+    } else if (L.inject != 1) {  // injected fault: the first wait below cannot complete
       tc_fence_after();
       issue_fields();
     }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
 
   // ---- sweep loop ----------------------------------------------------------------------
   for (int t = t_begin; t < t_end && !aborted; ++t) {
-    if (!mbar_wait_bounded(bar_mma, phase)) {
+    if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
     }
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
 
   // ---- energy of the final state s(t_end) ---------------------------------------------
   if (!aborted) {
-    if (!mbar_wait_bounded(bar_mma, phase)) {
+    if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
     }
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   } else if (tid == 0) {
     // An earlier wait gave up: give the in-flight MMA a bounded chance to land before the
     // tensor memory is released.
-    mbar_wait_bounded(bar_mma, phase);
+    mbar_wait_bounded(bar_mma, phase, L.wait_ns);
   }
 
   tc_fence_before();

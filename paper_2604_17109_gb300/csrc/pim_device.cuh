@@ -71,6 +71,8 @@ struct Launch {
   int cont;                // 1: keep previous best / first-hit records
   int stride_words_max;    // largest table stride among the problems (smem sizing)
   int* err;                // device error word
+  uint64_t wait_ns;        // limit of every device-side wait (0 = 2 s)
+  int inject;              // fault injection for tests: 1 = skip the first field MMA
 };
 
 // Launch of the large-N kernel: one instance, all sweeps, cooperative grid of
@@ -88,6 +90,8 @@ struct BigLaunch {
   int cont;
   uint32_t round_keys[20];
   int* err;
+  uint64_t wait_ns;        // limit of every device-side wait (0 = 2 s)
+  int inject;              // fault injection for tests: 1 = load nothing in the first sweep
 };
 
 }  // namespace pim

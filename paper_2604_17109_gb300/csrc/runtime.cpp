@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -82,6 +83,10 @@ struct Schedule {
     }
   }
 };
+
+// Fault injection for tests (pim_set_fault_injection).
+std::atomic<int> g_inject{0};
+std::atomic<uint64_t> g_wait_ns{0};
 
 std::mutex g_sched_mu;
 std::map<std::string, std::weak_ptr<Schedule>> g_sched_cache;
@@ -551,6 +556,8 @@ int launch_big(const Problem& P, int npad, int t_begin, int sweeps, uint64_t see
     L.cont = cont ? 1 : 0;
     philox_round_keys(seed, L.round_keys);
     L.err = d_err;
+    L.wait_ns = g_wait_ns.load();
+    L.inject = g_inject.load();
     CK(launch_sweep_big(L, tiles * ncb, st), "large-N sweep kernel");
     CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
   }
@@ -706,6 +713,8 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.cont = cont ? 1 : 0;
       L.stride_words_max = stride_max;
       L.err = d_err;
+      L.wait_ns = g_wait_ns.load();
+      L.inject = g_inject.load();
       if (g >= 4)
         CK(launch_sweep_float(L, (g & 1) ? 256 : 128, L.nwork, st), "real-valued sweep kernel");
       else
@@ -758,6 +767,13 @@ PIM_API int pim_sync(pim_instance* inst) {
 }
 
 PIM_API int pim_replicas(const pim_instance* inst) { return inst ? inst->R : 0; }
+
+PIM_API int pim_set_fault_injection(int mode, uint64_t wait_limit_ns) {
+  if (mode < 0 || mode > 1) return fail(PIM_ERR_INVALID, "pim_set_fault_injection: mode %d", mode);
+  g_inject.store(mode);
+  g_wait_ns.store(wait_limit_ns);
+  return PIM_OK;
+}
 
 PIM_API int pim_kernel_ms(pim_instance* inst, float* ms) {
   if (!inst || !ms) return fail(PIM_ERR_INVALID, "pim_kernel_ms: NULL argument");

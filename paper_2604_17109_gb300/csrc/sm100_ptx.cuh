@@ -36,12 +36,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Wait for the phase with the given parity; gives up after ~2 s and returns false.
-static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for the phase with the given parity; gives up after `limit_ns` (0 = 2 s) and
+// returns false.
+static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                      uint64_t limit_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t limit = limit_ns ? limit_ns : 2000000000ull;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit) return false;
   }
   return true;
 }

@@ -39,6 +39,7 @@ SIGNATURES = {
     "pim_final_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "pim_replicas": (C.c_int, [C.c_void_p]),
     "pim_kernel_ms": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "pim_set_fault_injection": (C.c_int, [C.c_int, C.c_uint64]),
     "pim_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_uint64)]),
     "pim_poll": (C.c_int, [C.c_uint64]),
     "pim_destroy": (None, [C.c_void_p]),
@@ -161,6 +162,10 @@ def pim_sync(inst: int) -> None:
 
 def pim_replicas(inst: int) -> int:
     return lib().pim_replicas(inst)
+
+
+def pim_set_fault_injection(mode: int, wait_limit_ns: int = 0) -> None:
+    _check(lib().pim_set_fault_injection(int(mode), int(wait_limit_ns)), "pim_set_fault_injection")
 
 
 def pim_kernel_ms(inst: int) -> float:
