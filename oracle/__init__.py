@@ -22,5 +22,6 @@ from .pimi import (  # noqa: F401
     anneal_sequential,
     n_trials,
     tts99,
+    neighbour_triggered_flip_rate,
 )
 from .brute import all_energies, ground_state, boltzmann  # noqa: F401

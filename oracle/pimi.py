@@ -214,7 +214,8 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
            sweeps: int | None = None, seed: int = 0, q: int = 0, t_begin: int = 0,
            init: np.ndarray | None = None, target: float | None = None,
            noise: str = "gauss", act: str = "tanh", lut_levels: int = 4,
-           replica_ids=None, record: bool = False, prev: dict | None = None) -> dict:
+           replica_ids=None, record: bool = False, record_states: bool = False,
+           prev: dict | None = None) -> dict:
     """Run fully parallel PIMI sweeps t = t_begin .. t_begin+sweeps-1.
 
     Each sweep: fields I(t) = J s(t) + h (Eq. 2); energy H(s(t)) (Eq. 1) with best and
@@ -251,6 +252,7 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
         best_state = s.copy()
 
     traj = []
+    states = [s.copy()] if record_states else None
 
     def bookkeep(E, t):
         nonlocal best_E
@@ -274,6 +276,8 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
         d = noise_draw16(seed, q, replica_ids[:, None], t, ivec[None, :])
         z = z_table[d >> 4]
         s = decide(tau, s, xi, eta[t], z)                   # Eq. 4, synchronous
+        if record_states:
+            states.append(s.copy())
     E = energy(J, h, s)
     bookkeep(E, t_begin + sweeps)
     out = dict(best_E=best_E if not integer else best_E.astype(np.int64),
@@ -282,7 +286,22 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
                best_state=best_state, final_state=s)
     if record:
         out["energies"] = np.stack(traj)
+    if record_states:
+        out["states"] = np.stack(states)
     return out
+
+
+def neighbour_triggered_flip_rate(J, states) -> np.ndarray:
+    """P_NT(t) of the supplementary section on coupled oscillations: over all spins i and
+    replicas, the fraction of the events "some coupled neighbour j (J_ij != 0) flips at step
+    t" in which spin i flips at the same step.  states: (T+1, R, n) -> P_NT: (T,)."""
+    adj = (np.asarray(J) != 0).astype(np.int64)
+    np.fill_diagonal(adj, 0)
+    flips = (states[1:] != states[:-1]).astype(np.int64)          # (T, R, n)
+    nb_flip = (flips @ adj.T) > 0                                  # neighbour flipped
+    both = (flips > 0) & nb_flip
+    den = nb_flip.sum(axis=(1, 2)).astype(np.float64)
+    return np.where(den > 0, both.sum(axis=(1, 2)) / np.maximum(den, 1), 0.0)
 
 
 def anneal_sequential(J, h, c: float, beta, eta, *, replicas: int, steps: int, seed: int = 0,
