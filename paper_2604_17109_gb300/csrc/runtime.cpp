@@ -106,6 +106,49 @@ int* device_error_word(int dev) {
   return p;
 }
 
+// Per device: a non-blocking stream for staging and freeing, and a memory pool that keeps
+// freed blocks (instance buffers come and go with every request).
+struct DeviceCtx {
+  cudaStream_t staging = nullptr;
+  cudaMemPool_t pool = nullptr;
+};
+std::mutex g_ctx_mu;
+std::map<int, DeviceCtx> g_ctx;
+
+DeviceCtx* device_ctx(int dev) {
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  DeviceCtx& c = g_ctx[dev];
+  if (!c.staging) {
+    if (cudaStreamCreateWithFlags(&c.staging, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&c.pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return &c;
+}
+
+// Stream-ordered allocation from the library's pool.
+cudaError_t pool_alloc(void** p, size_t bytes, int dev, cudaStream_t st) {
+  DeviceCtx* c = device_ctx(dev);
+  if (!c) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+}
+
+// Free `p` on the staging stream once `after` (if any) has completed.
+void pool_free_after(void* p, int dev, cudaEvent_t after) {
+  if (!p) return;
+  DeviceCtx* c = device_ctx(dev);
+  if (!c) return;
+  if (after) cudaStreamWaitEvent(c->staging, after, 0);
+  cudaFreeAsync(p, c->staging);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
 // CUDA events around one sweep-kernel launch, shared by the instances of that launch.
 struct LaunchTimer {
   cudaEvent_t start = nullptr, stop = nullptr;
@@ -126,6 +169,9 @@ struct pim_instance {
   bool diag = false;  // image carries 256 on the diagonal (h = 0, imax <= 255)
   bool real = false;  // real-valued couplings: BF16 operand image, float bias
   float* d_hf = nullptr;
+  char* d_slab = nullptr;   // J8 | image | bias (one pool block)
+  char* d_res = nullptr;    // results (one pool block)
+  cudaEvent_t ready = nullptr;  // staging of the inputs done
   int8_t* d_J8 = nullptr;
   uint8_t* d_img = nullptr;
   float* d_jf = nullptr;
@@ -148,29 +194,30 @@ struct pim_instance {
 namespace {
 
 void free_results(pim_instance* p) {
-  cudaFree(p->d_bestE);
-  cudaFree(p->d_finalE);
-  cudaFree(p->d_bestT);
-  cudaFree(p->d_first);
-  cudaFree(p->d_best_bits);
-  cudaFree(p->d_cur_bits);
+  pool_free_after(p->d_res, p->device, p->done);
+  p->d_res = nullptr;
   p->d_bestE = p->d_finalE = nullptr;
   p->d_bestT = p->d_first = nullptr;
   p->d_best_bits = p->d_cur_bits = nullptr;
   p->R_cap = 0;
 }
 
-int ensure_results(pim_instance* p, int R) {
+// Results of R replicas in one block, stream-ordered on the anneal's stream:
+// best_E | final_E (f64) | best_t | first_hit (i32) | best bits | current bits.
+int ensure_results(pim_instance* p, int R, cudaStream_t st) {
   if (R <= p->R_cap) return PIM_OK;
-  if (p->done) CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
   free_results(p);
   const size_t bits = static_cast<size_t>(R) * p->words * sizeof(uint32_t);
-  CK(cudaMalloc(&p->d_bestE, R * sizeof(double)), "cudaMalloc results");
-  CK(cudaMalloc(&p->d_finalE, R * sizeof(double)), "cudaMalloc results");
-  CK(cudaMalloc(&p->d_bestT, R * sizeof(int32_t)), "cudaMalloc results");
-  CK(cudaMalloc(&p->d_first, R * sizeof(int32_t)), "cudaMalloc results");
-  CK(cudaMalloc(&p->d_best_bits, bits), "cudaMalloc results");
-  CK(cudaMalloc(&p->d_cur_bits, bits), "cudaMalloc results");
+  const size_t scal = align256(static_cast<size_t>(R) * 24);
+  void* d = nullptr;
+  CK(pool_alloc(&d, scal + 2 * align256(bits), p->device, st), "allocating results");
+  p->d_res = static_cast<char*>(d);
+  p->d_bestE = reinterpret_cast<double*>(p->d_res);
+  p->d_finalE = p->d_bestE + R;
+  p->d_bestT = reinterpret_cast<int32_t*>(p->d_finalE + R);
+  p->d_first = p->d_bestT + R;
+  p->d_best_bits = reinterpret_cast<uint32_t*>(p->d_res + scal);
+  p->d_cur_bits = reinterpret_cast<uint32_t*>(p->d_res + scal + align256(bits));
   p->R_cap = R;
   return PIM_OK;
 }
@@ -357,28 +404,31 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
     return rc;
   };
   cudaError_t e;
-  uint16_t* d_tmp = nullptr;
+  DeviceCtx* ctx = device_ctx(p->device);
+  if (!ctx) return bail(cudaErrorMemoryAllocation, "device context");
   const size_t nn = static_cast<size_t>(n) * n;
-  if ((e = cudaMalloc(&d_tmp, nn * 2)) != cudaSuccess) return bail(e, "cudaMalloc J");
-  if ((e = cudaMemcpy(d_tmp, jb.data(), nn * 2, cudaMemcpyHostToDevice)) != cudaSuccess) {
-    cudaFree(d_tmp);
+  const size_t o_img = align256(nn * 2), o_h = o_img + align256(static_cast<size_t>(p->npad) * p->npad * 2);
+  void* slab = nullptr;
+  if ((e = pool_alloc(&slab, o_h + align256(n * sizeof(float)), p->device, ctx->staging)) != cudaSuccess)
+    return bail(e, "allocating J");
+  p->d_slab = static_cast<char*>(slab);
+  uint16_t* d_bf = reinterpret_cast<uint16_t*>(p->d_slab);
+  p->d_img = reinterpret_cast<uint8_t*>(p->d_slab + o_img);
+  if ((e = cudaMemcpyAsync(d_bf, jb.data(), nn * 2, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
     return bail(e, "upload J");
-  }
-  if ((e = cudaMalloc(&p->d_img, static_cast<size_t>(p->npad) * p->npad * 2)) != cudaSuccess) {
-    cudaFree(d_tmp);
-    return bail(e, "cudaMalloc J image");
-  }
-  e = launch_stage_bf16_image(d_tmp, n, p->npad, p->d_img, nullptr);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(d_tmp);
-  if (e != cudaSuccess) return bail(e, "stage BF16 J image");
+  if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging)) != cudaSuccess)
+    return bail(e, "stage BF16 J image");
   if (has_h) {
-    if ((e = cudaMalloc(&p->d_hf, n * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc h");
-    if ((e = cudaMemcpy(p->d_hf, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    p->d_hf = reinterpret_cast<float*>(p->d_slab + o_h);
+    if ((e = cudaMemcpyAsync(p->d_hf, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->staging)) != cudaSuccess)
       return bail(e, "upload h");
   }
   if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
+  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
   *out = p;
   return PIM_OK;
 }
@@ -453,29 +503,37 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     pim_destroy(p);
     return rc;
   };
+  // One pool block J8 | FP8 image | bias, filled and staged on the library's staging
+  // stream; anneals wait for the `ready` event instead of the host waiting here.
   cudaError_t e;
+  DeviceCtx* ctx = device_ctx(p->device);
+  if (!ctx) return bail(cudaErrorMemoryAllocation, "device context");
   const size_t nn = static_cast<size_t>(n) * n;
-  if ((e = cudaMalloc(&p->d_J8, nn)) != cudaSuccess) return bail(e, "cudaMalloc J");
-  if ((e = cudaMemcpy(p->d_J8, J8, nn, cudaMemcpyHostToDevice)) != cudaSuccess)
+  const size_t img = static_cast<size_t>(p->npad) * p->npad;
+  const size_t o_img = align256(nn), o_h = o_img + align256(img);
+  void* slab = nullptr;
+  if ((e = pool_alloc(&slab, o_h + align256(n * sizeof(int32_t)), p->device, ctx->staging)) != cudaSuccess)
+    return bail(e, "allocating J");
+  p->d_slab = static_cast<char*>(slab);
+  p->d_J8 = reinterpret_cast<int8_t*>(p->d_slab);
+  p->d_img = reinterpret_cast<uint8_t*>(p->d_slab + o_img);
+  if ((e = cudaMemcpyAsync(p->d_J8, J8, nn, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
     return bail(e, "upload J");
   if (p->has_h) {
-    if ((e = cudaMalloc(&p->d_h, n * sizeof(int32_t))) != cudaSuccess) return bail(e, "cudaMalloc h");
-    if ((e = cudaMemcpy(p->d_h, h32, n * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+    p->d_h = reinterpret_cast<int32_t*>(p->d_slab + o_h);
+    if ((e = cudaMemcpyAsync(p->d_h, h32, n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             ctx->staging)) != cudaSuccess)
       return bail(e, "upload h");
   }
-  {
-    p->diag = n <= kMaxNTensor && !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
-    const size_t img = static_cast<size_t>(p->npad) * p->npad;
-    if ((e = cudaMalloc(&p->d_img, img)) != cudaSuccess) return bail(e, "cudaMalloc J image");
-    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, nullptr)) !=
-        cudaSuccess)
-      return bail(e, "stage J image");
-  }
-  if ((e = cudaMalloc(&p->d_jf, nn * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc Jf");
-  if ((e = launch_stage_f32(p->d_J8, n, p->d_jf, nullptr)) != cudaSuccess) return bail(e, "stage Jf");
+  p->diag = n <= kMaxNTensor && !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
+  if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging)) !=
+      cudaSuccess)
+    return bail(e, "stage J image");
   if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "staging");
+  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "cudaEventCreate");
+  if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
   *out = p;
   return PIM_OK;
 }
@@ -602,7 +660,16 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   }
   if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
   for (int k = 0; k < count; ++k) {
-    int rc = ensure_results(insts[k], replicas[k]);
+    pim_instance* p = insts[k];
+    CK(cudaStreamWaitEvent(st, p->ready, 0), "cudaStreamWaitEvent");  // inputs staged
+    if (ref && !p->d_jf) {  // float32 couplings of the plain path, built on first use
+      void* d = nullptr;
+      CK(pool_alloc(&d, static_cast<size_t>(p->n) * p->n * sizeof(float), p->device, st),
+         "allocating float32 J");
+      p->d_jf = static_cast<float*>(d);
+      CK(launch_stage_f32(p->d_J8, p->n, p->d_jf, st), "stage float32 J");
+    }
+    int rc = ensure_results(p, replicas[k], st);
     if (rc != PIM_OK) return rc;
   }
   int* d_err = device_error_word(dev);
@@ -789,11 +856,14 @@ PIM_API int pim_energies(pim_instance* inst, double* best_E, int32_t* best_t,
   if (!inst->has_results) return fail(PIM_ERR_STATE, "pim_energies: no anneal has run");
   int rc = sync_instance(inst);
   if (rc != PIM_OK) return rc;
-  const size_t R = inst->R;
-  if (best_E) CK(cudaMemcpy(best_E, inst->d_bestE, R * 8, cudaMemcpyDeviceToHost), "copy best_E");
-  if (best_t) CK(cudaMemcpy(best_t, inst->d_bestT, R * 4, cudaMemcpyDeviceToHost), "copy best_t");
-  if (first_hit_t) CK(cudaMemcpy(first_hit_t, inst->d_first, R * 4, cudaMemcpyDeviceToHost), "copy first_hit");
-  if (final_E) CK(cudaMemcpy(final_E, inst->d_finalE, R * 8, cudaMemcpyDeviceToHost), "copy final_E");
+  // The four per-replica arrays are contiguous on the device: one copy.
+  const size_t R = inst->R, cap = inst->R_cap;
+  std::vector<char> h(cap * 24);
+  CK(cudaMemcpy(h.data(), inst->d_res, cap * 24, cudaMemcpyDeviceToHost), "copy energies");
+  if (best_E) std::memcpy(best_E, h.data(), R * 8);
+  if (final_E) std::memcpy(final_E, h.data() + cap * 8, R * 8);
+  if (best_t) std::memcpy(best_t, h.data() + cap * 16, R * 4);
+  if (first_hit_t) std::memcpy(first_hit_t, h.data() + cap * 20, R * 4);
   return PIM_OK;
 }
 
@@ -805,11 +875,23 @@ int copy_state(pim_instance* inst, const uint32_t* d_bits, int8_t* out) {
   if (rc != PIM_OK) return rc;
   std::vector<uint32_t> bits(static_cast<size_t>(inst->R) * inst->words);
   CK(cudaMemcpy(bits.data(), d_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "copy state bits");
-  for (int r = 0; r < inst->R; ++r)
-    for (int i = 0; i < inst->n; ++i) {
-      const uint32_t w = bits[static_cast<size_t>(r) * inst->words + (i >> 5)];
-      out[static_cast<size_t>(r) * inst->n + i] = ((w >> (i & 31)) & 1u) ? 1 : -1;
+  // Byte -> eight int8 spins (+1 where the bit is set, -1 elsewhere), 8 spins per lookup.
+  static const std::vector<uint64_t> expand = [] {
+    std::vector<uint64_t> tab(256);
+    for (int b = 0; b < 256; ++b) {
+      uint64_t v = 0;
+      for (int k = 0; k < 8; ++k) v |= static_cast<uint64_t>(((b >> k) & 1) ? 0x01 : 0xFF) << (8 * k);
+      tab[b] = v;
     }
+    return tab;
+  }();
+  const int n = inst->n, full = n / 8;
+  for (int r = 0; r < inst->R; ++r) {
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(&bits[static_cast<size_t>(r) * inst->words]);
+    int8_t* dst = out + static_cast<size_t>(r) * n;
+    for (int b = 0; b < full; ++b) std::memcpy(dst + 8 * b, &expand[src[b]], 8);
+    for (int i = 8 * full; i < n; ++i) dst[i] = ((src[i >> 3] >> (i & 7)) & 1) ? 1 : -1;
+  }
   return PIM_OK;
 }
 }  // namespace
@@ -862,20 +944,17 @@ PIM_API int pim_poll(uint64_t ticket) {
 
 PIM_API void pim_destroy(pim_instance* inst) {
   if (!inst) return;
-  if (inst->done) {
-    cudaEventSynchronize(inst->done);
-    cudaEventDestroy(inst->done);
-  }
+  if (inst->done) cudaEventSynchronize(inst->done);
   {
     std::lock_guard<std::mutex> lk(g_ticket_mu);
     if (inst->ticket) g_tickets.erase(inst->ticket);
   }
+  // Blocks go back to the pool on the staging stream once the last anneal has finished.
   free_results(inst);
-  cudaFree(inst->d_J8);
-  cudaFree(inst->d_img);
-  cudaFree(inst->d_jf);
-  cudaFree(inst->d_h);
-  cudaFree(inst->d_hf);
+  pool_free_after(inst->d_slab, inst->device, inst->done);
+  pool_free_after(inst->d_jf, inst->device, inst->done);
+  if (inst->done) cudaEventDestroy(inst->done);
+  if (inst->ready) cudaEventDestroy(inst->ready);
   inst->sched.reset();
   delete inst;
 }
