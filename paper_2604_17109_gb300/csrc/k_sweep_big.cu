@@ -1,21 +1,28 @@
 // Large-N PIMI sweep kernel (N > 256): persistent, cooperative, one CTA per (128-replica
-// tile, 64-spin column block), all sweeps in one launch.
+// tile, NT-spin column block), all sweeps in one launch.  Two operand kinds:
+//   integer couplings  FP8 E4M3 images (tcgen05 kind::f8f6f4), exact integer fields and the
+//                      exact threshold-table decision;
+//   real couplings     BF16 images (kind::f16), FP32 fields, Eq. 4 evaluated in FP32.
+// NT (64 or 128 spins) is chosen per instance by the host from the replica and spin counts.
 //
 // Per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
-//   fields   D[r, i] = sum_j S[r, j] J[i, j] for the CTA's 128 replicas and 64 spins: the
-//            K dimension (all N spins) streams through a 7-stage shared-memory ring filled
-//            by cp.async.bulk (spins of the tile from the global spin image, rows of J from
-//            the FP8 coupling image), consumed by tcgen05.mma kind::f8f6f4 into TMEM.
+//   fields   D[r, i] = sum_j S[r, j] J[i, j] for the CTA's 128 replicas and NT spins: the
+//            K dimension (all N spins) streams through a shared-memory ring filled by
+//            cp.async.bulk (spins of the tile from the global spin image, rows of J from the
+//            coupling image), consumed by tcgen05.mma into TMEM.
 //   decision 16 epilogue warps (4 TMEM lane quadrants x 4 column groups); each thread owns
-//            one replica and 16 spins for the whole anneal, keeps their old / new / best
-//            bits in registers, draws the Philox block, looks the threshold up by field
-//            I = D + h in the step's threshold table (staged into shared memory while the
-//            MMAs run, or read through L1 when it is larger), writes the new spins as FP8
-//            bytes into the other spin image, and adds its share of sum_i s_i (I_i + h_i)
-//            to the replica's energy accumulator (global atomics, three rotating buffers).
+//            one replica and NT/4 spins for the whole anneal, keeps their old / new / best
+//            bits in registers, draws the Philox blocks and decides: integer couplings by
+//            the step's threshold table at field I = D + h (staged into shared memory while
+//            the MMAs run, or read through L1 when it is larger), real couplings by
+//            tanh(b_t I) + xi s + eta_t z >= 0.  It writes the new spins into the other spin
+//            image and adds its share of sum_i s_i (I_i + h_i) to the replica's energy
+//            accumulator (global atomics, three rotating buffers; int32 for integer
+//            couplings, so the energy stays exact).
 //   exchange a bounded grid barrier; every CTA then reads the replica energies of s(t),
 //            updates best / first hit (redundantly, identically in all CTAs) and copies its
-//            own 16 old spins into the best state when the energy improved.
+//            own old spins into the best state when the energy improved.
+#include <cfloat>
 #include <climits>
 
 #include "kernels.h"
@@ -25,13 +32,28 @@
 namespace pim {
 namespace {
 
-constexpr int kNT = 64;           // spins (output columns) per CTA
-constexpr int kStages = 7;        // K-block ring depth
-constexpr int kTabWords = 8192;   // threshold table of one step staged in shared memory
-constexpr int kABytes = 128 * 128;  // one K-block of the spin tile (128 rows x 128 B)
-constexpr int kBBytes = kNT * 128;  // one K-block of the coupling rows (64 rows x 128 B)
+#include <type_traits>
+
+constexpr int kTabWords = 8192;     // threshold table of one step staged in shared memory
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr int kSmemBudget = 227 * 1024;
+
+// Shared-memory plan of one kernel variant: NT output spins per CTA, FP8 or BF16 operands.
+template <int NT, bool REAL>
+struct BigCfg {
+  static constexpr int kEB = REAL ? 2 : 1;       // operand element bytes
+  static constexpr int kSPT = NT / 4;            // spins per epilogue thread
+  static constexpr int kChunks = kSPT / 16;      // 16-spin chunks per thread
+  static constexpr int kABytes = 128 * 128;      // one K-block of the spin tile (128 rows x 128 B)
+  static constexpr int kBBytes = NT * 128;       // one K-block of the coupling rows
+  static constexpr int kAux = REAL ? 4096 * 4 : kTabWords * 4;  // noise levels | step table
+  static constexpr int kFixed = 1024 + kAux + 4 * 128 * 4 + NT * 4 + 256;
+  static constexpr int kFit = (kSmemBudget - kFixed) / (kABytes + kBBytes);
+  static constexpr int kStages = kFit < 8 ? kFit : 8;  // K-block ring depth
+  static constexpr int kSmem = kFixed + kStages * (kABytes + kBBytes);
+  static_assert(kStages >= 3, "ring too shallow");
+};
 
 __device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
   uint32_t v;
@@ -84,16 +106,22 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err, 
   return *sflag != 0;
 }
 
+template <int NT, bool REAL>
 __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_constant__ BigLaunch L) {
+  using C = BigCfg<NT, REAL>;
+  using EAcc = std::conditional_t<REAL, float, int>;  // energy partial sums
+  constexpr int kStages = C::kStages, kABytes = C::kABytes, kBBytes = C::kBBytes;
+  constexpr int kSPT = C::kSPT, kChunks = C::kChunks;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint8_t* sA = smem;                           // kStages x kABytes
-  uint8_t* sB = sA + kStages * kABytes;         // kStages x kBBytes
-  uint32_t* sTab = reinterpret_cast<uint32_t*>(sB + kStages * kBBytes);  // [kTabWords]
-  float* sRed = reinterpret_cast<float*>(sTab + kTabWords);  // [4 groups][128 rows]
-  int* sH = reinterpret_cast<int*>(sRed + 4 * 128);                // [kNT]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + kNT);          // full[S], empty[S], done
+  uint8_t* sA = smem;                               // kStages x kABytes
+  uint8_t* sB = sA + kStages * kABytes;             // kStages x kBBytes
+  uint32_t* sTab = reinterpret_cast<uint32_t*>(sB + kStages * kBBytes);  // [kTabWords] (integer)
+  float* sZ = reinterpret_cast<float*>(sTab);       // [4096] noise levels (real)
+  EAcc* sRed = reinterpret_cast<EAcc*>(sB + kStages * kBBytes + C::kAux);  // [4 groups][128 rows]
+  uint32_t* sH = reinterpret_cast<uint32_t*>(sRed + 4 * 128);  // [NT] bias: int32 or float bits
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + NT);       // full[S], empty[S], done
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
   int* sFlag = reinterpret_cast<int*>(sTmem + 1);
 
@@ -103,27 +131,28 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
   const int cb = blockIdx.x % ncb, rt = blockIdx.x / ncb;
   const unsigned int nblocks = gridDim.x;
   const int n = P.n, npad = P.npad, R = P.R, rpad = L.rpad;
-  const int kblocks = npad / 128;
+  const int kblocks = npad * C::kEB / 128;
   const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
   const bool epi = warp >= 2;
   const int ew = warp - 2;             // epilogue warp 0..15
   const int quad = warp & 3;           // TMEM lane quadrant of this warp
-  const int grp = epi ? ew >> 2 : 0;   // column group 0..3 (16 spins each)
+  const int grp = epi ? ew >> 2 : 0;   // column group 0..3 (kSPT spins each)
   const int row = quad * 32 + lane;    // replica row inside the tile
   const int rl = rt * 128 + row;       // replica row inside this launch's images
   const int r = L.rbase + rl;          // replica index
-  const int col0 = cb * kNT + grp * 16;  // first spin of this thread's 16
+  const int col0 = cb * NT + grp * kSPT;  // first spin of this thread's kSPT
   const bool row_valid = epi && r < R;
   const bool warp_active = epi && (L.rbase + rt * 128 + quad * 32) < R && col0 < n;
-  const int valid = n - col0;            // spins of the 16 that exist
-  const uint32_t vmask = valid >= 16 ? 0xFFFFu : (valid > 0 ? (1u << valid) - 1u : 0u);
+  const int valid = n - col0;            // spins of the kSPT that exist
+  const uint32_t full_mask = kSPT == 32 ? 0xFFFFFFFFu : ((1u << (kSPT & 31)) - 1u);
+  const uint32_t vmask = valid >= kSPT ? full_mask : (valid > 0 ? (1u << valid) - 1u : 0u);
 
   const uint32_t bar_full0 = smem_u32(&bars[0]);
   const uint32_t bar_empty0 = smem_u32(&bars[kStages]);
   const uint32_t bar_done = smem_u32(&bars[2 * kStages]);
 
   if (warp == 1) {
-    tmem_alloc(smem_u32(sTmem), kNT);
+    tmem_alloc(smem_u32(sTmem), NT);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -134,42 +163,63 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     mbar_init(bar_done, 1);
     fence_mbar_init();
   }
-  for (int k = tid; k < kNT; k += kThreads) {
-    const int i = cb * kNT + k;
-    sH[k] = (P.h != nullptr && i < n) ? P.h[i] : 0;
+  for (int k = tid; k < NT; k += kThreads) {
+    const int i = cb * NT + k;
+    if constexpr (REAL)
+      sH[k] = __float_as_uint((P.hf != nullptr && i < n) ? P.hf[i] : 0.0f);
+    else
+      sH[k] = static_cast<uint32_t>((P.h != nullptr && i < n) ? P.h[i] : 0);
   }
+  if constexpr (REAL)
+    for (int k = tid; k < 4096; k += kThreads) sZ[k] = P.zlev[k];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
 
-  // ---- per-thread state: this replica's 16 spins ------------------------------------
+  // ---- per-thread state: this replica's kSPT spins ------------------------------------
   uint32_t cur = 0, best = 0;
-  int best_E = INT_MAX, best_t = -1, first_hit = -1;
+  EAcc best_E;
+  if constexpr (REAL)
+    best_E = FLT_MAX;
+  else
+    best_E = INT_MAX;
+  int best_t = -1, first_hit = -1;
   const int half_words = P.words * 2;  // 16-bit chunks per row in the caller's bit arrays
   const int chunk = col0 >> 4;
-  if (row_valid && chunk < half_words) {
-    cur = reinterpret_cast<const uint16_t*>(P.cur_bits)[static_cast<size_t>(r) * half_words + chunk];
+  const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
+  const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
+  if (row_valid) {
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c)
+      if (chunk + c < half_words) {
+        const size_t o = static_cast<size_t>(r) * half_words + chunk + c;
+        cur |= static_cast<uint32_t>(cur_in[o]) << (16 * c);
+        if (L.cont) best |= static_cast<uint32_t>(best_in[o]) << (16 * c);
+      }
     if (L.cont) {
-      best = reinterpret_cast<const uint16_t*>(P.best_bits)[static_cast<size_t>(r) * half_words + chunk];
-      best_E = static_cast<int>(P.best_E[r]);
+      best_E = static_cast<EAcc>(P.best_E[r]);
       best_t = P.best_t[r];
       first_hit = P.first_hit[r];
     }
   }
   if (!L.cont) best = cur;
   const bool has_target = P.has_target != 0;
-  const long long target = P.target;
 
-  // Initial spin image s(t_begin) for this CTA's block (rows of the tile, its 64 spins).
+  // Spin image s(t) for this CTA's block (rows of the tile, its NT spins): FP8 or BF16 +-1.
   auto write_image = [&](uint8_t* img, uint32_t bits) {
     if (!epi || col0 >= npad) return;
-    const uint4 bytes = make_uint4(
-        ((((bits >> 0) & 0xFu) * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u,
-        ((((bits >> 4) & 0xFu) * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u,
-        ((((bits >> 8) & 0xFu) * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u,
-        ((((bits >> 12) & 0xFu) * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u);
-    *reinterpret_cast<uint4*>(img + sw128_offset(rl, col0, rpad)) = bytes;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+      const uint32_t b16 = (bits >> (16 * c)) & 0xFFFFu;
+      const int k = col0 + 16 * c;
+      if constexpr (REAL) {
+        *reinterpret_cast<uint4*>(img + sw128_offset(rl, 2 * k, rpad)) = bf16x8_from_bits(b16 & 0xFFu);
+        *reinterpret_cast<uint4*>(img + sw128_offset(rl, 2 * k + 16, rpad)) = bf16x8_from_bits(b16 >> 8);
+      } else {
+        *reinterpret_cast<uint4*>(img + sw128_offset(rl, k, rpad)) = fp8x16_from_bits(b16);
+      }
+    }
   };
   write_image(L.s_img[0], cur & vmask);
   fence_proxy_async_global();
@@ -177,14 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
 
   {
     uint32_t loads = 0, mmas = 0, done_phase = 0;
-    const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(kNT >> 3) << 17) |
-                           (static_cast<uint32_t>(128 >> 4) << 24);
+    const uint32_t idesc = REAL ? idesc_bf16(128, NT) : idesc_e4m3(128, NT);
     // Producer (thread 0): stream the K blocks of image `img` (spins of the tile) and of the
     // coupling rows of the column block into the ring.  A stage is refilled once the MMAs
     // that read it have completed (its empty barrier).
     auto produce = [&](const uint8_t* img) -> bool {
       const uint8_t* a_src = img + static_cast<size_t>(rt) * 128 * 128;
-      const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * kNT * 128;
+      const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * NT * 128;
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = loads % kStages, use = loads / kStages;
         if (use > 0 && !mbar_wait_bounded(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
@@ -198,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       return true;
     };
     // MMA issuer (thread 32): D = S_tile x J_block^T, K block by K block as stages land; it
-    // never waits for an MMA to finish, only for data.
+    // never waits for an MMA to finish, only for data.  Each MMA consumes 32 bytes of K
+    // (32 FP8 or 16 BF16 values).
     auto multiply = [&]() -> bool {
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = mmas % kStages, use = mmas / kStages;
@@ -206,9 +256,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-          mma_e4m3(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
-                   (kb > 0 || ks > 0) ? 1u : 0u);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+          if constexpr (REAL)
+            mma_bf16(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
+          else
+            mma_e4m3(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
+        }
         mma_commit(bar_empty0 + 8 * s);
         ++mmas;
       }
@@ -233,11 +287,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
           atomicExch(&L.bar[2], 1u);
         }
       }
+      EAcc* energy = reinterpret_cast<EAcc*>(L.energy);
       // Zero the energy buffer that sweep t+1 will accumulate into (see header).
-      if (cb == 0 && epi && grp == 0) __stcg(&L.energy[((t - t_begin + 1) % 3) * rpad + rl], 0.0f);
-      float eacc = 0.0f;
+      if (cb == 0 && epi && grp == 0) __stcg(&energy[((t - t_begin + 1) % 3) * rpad + rl], EAcc(0));
+      EAcc eacc = 0;
       uint32_t nxt = 0;
-      const bool tab_in_smem = P.stride_words <= kTabWords;
+      const bool tab_in_smem = !REAL && P.stride_words <= kTabWords;
       if (epi) {
         // Stage this step's thresholds while the MMAs run (the previous step's reads ended
         // before the last grid barrier), then sync the 16 epilogue warps.
@@ -255,32 +310,59 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         }
         tc_fence_after();
         if (warp_active) {
-          uint32_t v[16];
-          tmem_ld16(tmem + (static_cast<uint32_t>(quad * 32) << 16) + grp * 16, v);
-          PhiloxOut o0{}, o1{};
-          if (!last) {
-            o0 = philox4x32_10_rk(static_cast<uint32_t>(col0 >> 3), static_cast<uint32_t>(r),
-                                  static_cast<uint32_t>(t), P.q, L.round_keys);
-            o1 = philox4x32_10_rk(static_cast<uint32_t>((col0 >> 3) + 1), static_cast<uint32_t>(r),
-                                  static_cast<uint32_t>(t), P.q, L.round_keys);
-          }
-          tmem_wait_ld(v);
-          const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-          const uint32_t* tab =
-              tab_in_smem ? sTab : P.thr + static_cast<size_t>(last ? t_begin : t) * P.stride_words;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int hv = sH[grp * 16 + e];
-            const int I = __float2int_rn(__uint_as_float(v[e])) + hv;
-            const uint32_t s = (cur >> e) & 1u;
-            const int term = I + hv;
-            eacc += static_cast<float>(s ? term : -term);
+          const uint32_t* tab = nullptr;
+          float b = 0.0f, eta = 0.0f;
+          if constexpr (REAL) {
             if (!last) {
-              const uint32_t w = tab[I + P.imax];
-              const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
+              b = P.sched_b[t];
+              eta = P.sched_eta[t];
+            }
+          } else {
+            tab = tab_in_smem ? sTab : P.thr + static_cast<size_t>(last ? t_begin : t) * P.stride_words;
+          }
+#pragma unroll
+          for (int c = 0; c < kChunks; ++c) {
+            uint32_t v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(quad * 32) << 16) + grp * kSPT + 16 * c, v);
+            PhiloxOut o0{}, o1{};
+            if (!last) {
+              const uint32_t ctr = static_cast<uint32_t>((col0 + 16 * c) >> 3);
+              o0 = philox4x32_10_rk(ctr, static_cast<uint32_t>(r), static_cast<uint32_t>(t), P.q,
+                                    L.round_keys);
+              o1 = philox4x32_10_rk(ctr + 1u, static_cast<uint32_t>(r), static_cast<uint32_t>(t),
+                                    P.q, L.round_keys);
+            }
+            tmem_wait_ld(v);
+            const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int bit = 16 * c + e;
+              const uint32_t s = (cur >> bit) & 1u;
               const uint32_t word = rw[e >> 1];
               const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
-              nxt |= (key >= th ? 1u : 0u) << e;
+              if constexpr (REAL) {
+                const float hv = __uint_as_float(sH[grp * kSPT + bit]);
+                const float I = __fadd_rn(__uint_as_float(v[e]), hv);
+                const float term = __fadd_rn(I, hv);
+                eacc += s ? term : -term;
+                if (!last) {
+                  const float x = __fmul_rn(b, I);
+                  const float tau = P.act == 0 ? tanhf(x) : staircase(x, P.lut_levels);
+                  const float a = __fadd_rn(tau, s ? P.xi : -P.xi);
+                  const float delta = __fadd_rn(a, __fmul_rn(eta, sZ[key]));
+                  nxt |= (delta >= 0.0f ? 1u : 0u) << bit;
+                }
+              } else {
+                const int hv = static_cast<int>(sH[grp * kSPT + bit]);
+                const int I = __float2int_rn(__uint_as_float(v[e])) + hv;
+                const int term = I + hv;
+                eacc += s ? term : -term;
+                if (!last) {
+                  const uint32_t w = tab[I + P.imax];
+                  const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
+                  nxt |= (key >= th ? 1u : 0u) << bit;
+                }
+              }
             }
           }
           nxt &= vmask;
@@ -292,27 +374,38 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       tc_fence_before();
       __syncthreads();
       if (epi && grp == 0) {
-        const float tot = sRed[row] + sRed[128 + row] + sRed[256 + row] + sRed[384 + row];
-        atomicAdd(&L.energy[((t - t_begin) % 3) * rpad + rl], tot);
+        const EAcc tot = sRed[row] + sRed[128 + row] + sRed[256 + row] + sRed[384 + row];
+        atomicAdd(&energy[((t - t_begin) % 3) * rpad + rl], tot);
       }
       fence_proxy_async_global();
       if (!grid_barrier(L.bar, nblocks, L.err, sFlag, L.wait_ns)) goto teardown;
       if (epi) {
         // L2 read: the accumulator was written by other SMs during this sweep.
-        const float etot = __ldcg(&L.energy[((t - t_begin) % 3) * rpad + rl]);
-        const int E = -(static_cast<int>(etot) / 2);
+        const EAcc etot = __ldcg(&energy[((t - t_begin) % 3) * rpad + rl]);
+        EAcc E;
+        bool hit;
+        if constexpr (REAL) {
+          E = -0.5f * etot;
+          hit = static_cast<double>(E) <= P.target_f;
+        } else {
+          E = -(etot / 2);  // s^T J s is even for symmetric integer J with zero diagonal
+          hit = static_cast<long long>(E) <= P.target;
+        }
         if (E < best_E) {
           best_E = E;
           best_t = t;
           best = cur;
         }
-        if (has_target && first_hit < 0 && E <= target) first_hit = t;
+        if (has_target && first_hit < 0 && hit) first_hit = t;
         if (last) {
-          if (row_valid && chunk < half_words) {
-            reinterpret_cast<uint16_t*>(P.cur_bits)[static_cast<size_t>(r) * half_words + chunk] =
-                static_cast<uint16_t>(cur);
-            reinterpret_cast<uint16_t*>(P.best_bits)[static_cast<size_t>(r) * half_words + chunk] =
-                static_cast<uint16_t>(best);
+          if (row_valid) {
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c)
+              if (chunk + c < half_words) {
+                const size_t o = static_cast<size_t>(r) * half_words + chunk + c;
+                reinterpret_cast<uint16_t*>(P.cur_bits)[o] = static_cast<uint16_t>(cur >> (16 * c));
+                reinterpret_cast<uint16_t*>(P.best_bits)[o] = static_cast<uint16_t>(best >> (16 * c));
+              }
             if (cb == 0 && grp == 0) {
               P.best_E[r] = static_cast<double>(best_E);
               P.best_t[r] = best_t;
@@ -331,45 +424,56 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
 teardown:
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, kNT);
+  if (warp == 1) tmem_dealloc(tmem, NT);
+}
+
+// Kernel, dynamic shared memory and co-resident CTAs of the (NT, REAL) variant.
+template <int NT, bool REAL>
+cudaError_t variant_setup(const void** fn, int* smem, int* max_blocks) {
+  *fn = reinterpret_cast<const void*>(sweep_big_kernel<NT, REAL>);
+  *smem = BigCfg<NT, REAL>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(sweep_big_kernel<NT, REAL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_big_kernel<NT, REAL>, kThreads,
+                                                    *smem);
+  if (e != cudaSuccess) return e;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *max_blocks = per_sm * sms;
+  return cudaSuccess;
+}
+
+cudaError_t variant(int nt, bool real, const void** fn, int* smem, int* max_blocks) {
+  if (nt == 64) return real ? variant_setup<64, true>(fn, smem, max_blocks)
+                            : variant_setup<64, false>(fn, smem, max_blocks);
+  if (nt == 128) return real ? variant_setup<128, true>(fn, smem, max_blocks)
+                             : variant_setup<128, false>(fn, smem, max_blocks);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-int sweep_big_smem_bytes() {
-  return 1024 + kStages * (kABytes + kBBytes) + kTabWords * 4 + 4 * 128 * 4 + kNT * 4 +
-         (2 * kStages + 1) * 8 + 16;
+int sweep_big_stages(int nt, bool real) {
+  if (nt == 64) return real ? BigCfg<64, true>::kStages : BigCfg<64, false>::kStages;
+  return real ? BigCfg<128, true>::kStages : BigCfg<128, false>::kStages;
 }
 
-int sweep_big_tile_n() { return kNT; }
-
-int sweep_big_max_blocks() {
-  const int smem = sweep_big_smem_bytes();
-  if (cudaFuncSetAttribute(sweep_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-      cudaSuccess)
-    return 0;
-  int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_big_kernel, kThreads, smem) !=
-      cudaSuccess)
-    return 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return per_sm * sms;
+int sweep_big_max_blocks(int nt, bool real) {
+  const void* fn = nullptr;
+  int smem = 0, blocks = 0;
+  return variant(nt, real, &fn, &smem, &blocks) == cudaSuccess ? blocks : 0;
 }
 
-cudaError_t launch_sweep_big(const BigLaunch& L, int blocks, cudaStream_t st) {
-  const int smem = sweep_big_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(sweep_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t launch_sweep_big(const BigLaunch& L, int nt, bool real, int blocks, cudaStream_t st) {
+  const void* fn = nullptr;
+  int smem = 0, cap = 0;
+  cudaError_t e = variant(nt, real, &fn, &smem, &cap);
   if (e != cudaSuccess) return e;
-  int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_big_kernel, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (blocks > per_sm * sms) return cudaErrorCooperativeLaunchTooLarge;
+  if (blocks > cap) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {const_cast<BigLaunch*>(&L)};
-  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(sweep_big_kernel), dim3(blocks),
-                                  dim3(kThreads), args, smem, st);
+  e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kThreads), args, smem, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -48,10 +48,11 @@ int sweep_float_smem_bytes(int npad);
 cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
                                     cudaStream_t st);
 
-// Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs.
-cudaError_t launch_sweep_big(const BigLaunch& L, int blocks, cudaStream_t st);
-int sweep_big_tile_n();
-int sweep_big_max_blocks();  // co-resident CTAs on the current device (0 on error)
+// Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs, each
+// computing nt (64 or 128) output spins; real = BF16 operands and the FP32 decision.
+cudaError_t launch_sweep_big(const BigLaunch& L, int nt, bool real, int blocks, cudaStream_t st);
+int sweep_big_max_blocks(int nt, bool real);  // co-resident CTAs on the current device (0 on error)
+int sweep_big_stages(int nt, bool real);      // depth of the K-block ring
 
 // Plain FP32 comparator path: per sweep one field GEMM and one update kernel.
 cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, int nprob,

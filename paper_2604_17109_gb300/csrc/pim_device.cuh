@@ -76,15 +76,17 @@ struct Launch {
 };
 
 // Launch of the large-N kernel: one instance, all sweeps, cooperative grid of
-// (replica tiles) x (64-spin column blocks).
+// (replica tiles) x (nt-spin column blocks).
 struct BigLaunch {
   Problem P;
   uint8_t* s_img[2];       // FP8 spin images [npad/128][rpad][128 B] (A operand), ping-pong
-  float* energy;           // [3][rpad] rotating per-replica energy accumulators (zeroed)
+  float* energy;           // [3][rpad] rotating per-replica energy accumulators (zeroed);
+                           // int32 for integer couplings, float for real couplings
+  int nt;                  // output spins per CTA (64 or 128)
   unsigned int* bar;       // grid barrier {arrivals, generation, abort} (zeroed)
   int rbase;               // first replica of this launch
   int rpad;                // replica rows of this launch (multiple of 128)
-  int ncb;                 // column blocks = npad / 64
+  int ncb;                 // column blocks = npad / nt
   int t_begin;
   int sweeps;
   int cont;

@@ -362,8 +362,6 @@ uint16_t bf16_bits_rne(double v) {
 
 // Real-valued couplings: J rounded to BF16 for the tensor-core operand, bias as float.
 int create_real(pim_instance** out, int n, int j_type, const void* J, const void* h, double c) {
-  if (n > kMaxNTensor)
-    return fail(PIM_ERR_UNSUPPORTED, "pim_create: real-valued couplings need n <= %d", kMaxNTensor);
   auto at = [&](const void* a, size_t k) -> double {
     return j_type == PIM_J_FP32 ? static_cast<double>(static_cast<const float*>(a)[k])
                                 : static_cast<const double*>(a)[k];
@@ -394,7 +392,7 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
   cudaGetDevice(&p->device);
   p->real = true;
   p->n = n;
-  p->npad = n <= 128 ? 128 : 256;
+  p->npad = n <= 128 ? 128 : (n <= 256 ? 256 : ((n + 127) / 128) * 128);
   p->words = ((n + 63) / 64) * 2;
   p->c = c;
   p->has_h = has_h;
@@ -578,23 +576,64 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
 
 namespace {
 
+// Tile plan of the large-N kernel for one instance.
+struct BigPlan {
+  int nt = 0;                // output spins per CTA (64 or 128)
+  int tiles_per_launch = 0;  // 128-replica tiles per cooperative launch
+  int launches = 0;
+  double us_per_sweep = 0.0;  // model estimate
+};
+
+// Per-sweep time model of the large-N kernel.  Every CTA streams npad * bytes / 128
+// K-blocks of (128 x 128 B spins + nt x 128 B couplings); a K-block costs the larger of its
+// ingest time at the per-SM bulk-copy rate (about 64 GB/s per SM when all SMs stream, as
+// measured for this kernel on GB300) and its MMA time at the per-SM tensor rate (1889 TFLOP/s
+// BF16, twice that for FP8, over 152 SMs); replica tiles that do not fit the co-resident grid
+// run as further launches, each with its own ~3 us grid barrier per sweep.
+constexpr double kIngestBytesPerUs = 64e3;
+constexpr double kBf16FlopsPerUs = 1889e6 / 152;
+
+int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
+  const int eb = real ? 2 : 1;
+  const int kblocks = npad * eb / 128;
+  const int tiles_total = (R + 127) / 128;
+  BigPlan best;
+  for (int nt : {64, 128}) {
+    if (npad % nt) continue;
+    const int ncb = npad / nt;
+    const int cap = sweep_big_max_blocks(nt, real);
+    if (cap < ncb) continue;
+    BigPlan p;
+    p.nt = nt;
+    p.tiles_per_launch = std::min(tiles_total, cap / ncb);
+    p.launches = (tiles_total + p.tiles_per_launch - 1) / p.tiles_per_launch;
+    const double bytes = 128.0 * 128 + nt * 128.0;
+    const double flops = 2.0 * 128 * nt * (128 / eb);
+    const double per_kb = std::max(bytes / kIngestBytesPerUs, flops / (kBf16FlopsPerUs * (real ? 1 : 2)));
+    p.us_per_sweep = p.launches * (kblocks * per_kb + 3.0);
+    if (best.nt == 0 || p.us_per_sweep < best.us_per_sweep) best = p;
+  }
+  if (best.nt == 0)
+    return fail(PIM_ERR_UNSUPPORTED, "anneal: n = %d needs more co-resident CTAs than the device holds", n);
+  *out = best;
+  return PIM_OK;
+}
+
 // Large-N anneal of one instance: the replicas are split into groups of tiles that fit the
 // co-resident grid (each group is an independent cooperative launch); per launch scratch
 // (two spin images, energy accumulators, barrier words) comes from the stream-ordered pool.
-int launch_big(const Problem& P, int npad, int t_begin, int sweeps, uint64_t seed, bool cont,
+int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t seed, bool cont,
                int* d_err, cudaStream_t st) {
-  const int nt = sweep_big_tile_n();
-  const int ncb = npad / nt;
-  const int cap = sweep_big_max_blocks();
-  if (cap < ncb)
-    return fail(PIM_ERR_UNSUPPORTED, "anneal: n = %d needs %d co-resident CTAs, device holds %d",
-                P.n, ncb, cap);
+  BigPlan plan;
+  const int rc = plan_big(P.n, P.npad, P.R, real, &plan);
+  if (rc != PIM_OK) return rc;
+  const int ncb = P.npad / plan.nt;
   const int tiles_total = (P.R + 127) / 128;
-  const int tiles_per_launch = std::min(tiles_total, cap / ncb);
-  for (int tile0 = 0; tile0 < tiles_total; tile0 += tiles_per_launch) {
-    const int tiles = std::min(tiles_per_launch, tiles_total - tile0);
+  const int eb = real ? 2 : 1;
+  for (int tile0 = 0; tile0 < tiles_total; tile0 += plan.tiles_per_launch) {
+    const int tiles = std::min(plan.tiles_per_launch, tiles_total - tile0);
     const int rpad = tiles * 128;
-    const size_t img_bytes = static_cast<size_t>(rpad) * npad;
+    const size_t img_bytes = static_cast<size_t>(rpad) * P.npad * eb;
     const size_t energy_bytes = sizeof(float) * 3 * rpad;
     const size_t bytes = 2 * img_bytes + energy_bytes + 256;
     char* d = nullptr;
@@ -606,6 +645,7 @@ int launch_big(const Problem& P, int npad, int t_begin, int sweeps, uint64_t see
     L.s_img[1] = reinterpret_cast<uint8_t*>(d + img_bytes);
     L.energy = reinterpret_cast<float*>(d + 2 * img_bytes);
     L.bar = reinterpret_cast<unsigned int*>(d + 2 * img_bytes + energy_bytes);
+    L.nt = plan.nt;
     L.rbase = tile0 * 128;
     L.rpad = rpad;
     L.ncb = ncb;
@@ -616,7 +656,7 @@ int launch_big(const Problem& P, int npad, int t_begin, int sweeps, uint64_t see
     L.err = d_err;
     L.wait_ns = g_wait_ns.load();
     L.inject = g_inject.load();
-    CK(launch_sweep_big(L, tiles * ncb, st), "large-N sweep kernel");
+    CK(launch_sweep_big(L, plan.nt, real, tiles * ncb, st), "large-N sweep kernel");
     CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
   }
   return PIM_OK;
@@ -789,7 +829,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     }
     for (int k = 0; k < count; ++k) {
       if (insts[k]->n <= kMaxNTensor) continue;
-      const int rc = launch_big(probs[k], insts[k]->npad, t_begin, sweeps, seed, cont, d_err, st);
+      const int rc = launch_big(probs[k], insts[k]->real, t_begin, sweeps, seed, cont, d_err, st);
       if (rc != PIM_OK) return rc;
     }
     CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");

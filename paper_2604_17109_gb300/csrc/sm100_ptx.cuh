@@ -172,4 +172,40 @@ __device__ __forceinline__ uint4 fp8x16_from_bits(uint32_t nb) {
 }
 
 
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Eight spins (low 8 bits) -> eight BF16 values (+1 = 0x3F80, -1 = 0xBF80), 16 bytes.
+__device__ __forceinline__ uint4 bf16x8_from_bits(uint32_t b) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t lo = (b >> (2 * k)) & 1u, hi = (b >> (2 * k + 1)) & 1u;
+    w[k] = 0x3F803F80u | ((lo ^ 1u) << 15) | ((hi ^ 1u) << 31);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ float staircase(float x, int levels) {
+  if (x < -1.0f) return -1.0f;
+  if (x > 1.0f) return 1.0f;
+  int k = 0;
+  for (int kk = 1; kk < levels; ++kk)
+    if (x >= -1.0f + 2.0f * kk / levels) k = kk;
+  return -1.0f + 2.0f * k / (levels - 1);
+}
+
 }  // namespace pim
