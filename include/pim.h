@@ -51,8 +51,8 @@ typedef enum pim_status {
 /* Element type of the host coupling matrix passed to pim_create. */
 typedef enum pim_j_type {
   PIM_J_INT8 = 0,  /* int8, integer couplings |J_ij| <= 16 (held exactly as FP8 E4M3) */
-  PIM_J_FP32 = 1,  /* float32 real couplings, rounded to BF16 for the tensor cores (n <= 256) */
-  PIM_J_FP64 = 2   /* float64 real couplings, rounded to BF16 for the tensor cores (n <= 256) */
+  PIM_J_FP32 = 1,  /* float32 real couplings, rounded to BF16 for the tensor cores */
+  PIM_J_FP64 = 2   /* float64 real couplings, rounded to BF16 for the tensor cores */
 } pim_j_type;
 
 /* Noise term of the update rule. */
@@ -71,8 +71,13 @@ typedef enum pim_act {
 typedef enum pim_flags {
   PIM_CONTINUE = 1,     /* start from the instance's current state and keep its best /
                            first-hit records (resume); replicas must equal the last run's */
-  PIM_PATH_FP32REF = 2  /* run the plain FP32 two-kernels-per-sweep comparator path instead
+  PIM_PATH_FP32REF = 2, /* run the plain FP32 two-kernels-per-sweep comparator path instead
                            of the fused tensor-core sweep kernel (same decisions) */
+  PIM_PATH_MID = 4,     /* put every integer instance with n <= 1024 on the persistent mid-N
+                           kernel (same decisions; for tests and tuning) */
+  PIM_PATH_BIG = 8      /* put every instance with n > 256 on the large-N cooperative kernel
+                           (same decisions; for tests and tuning).  Without either flag the
+                           library picks the kernel of each instance from its cost model. */
 } pim_flags;
 
 typedef struct pim_instance pim_instance;
@@ -81,8 +86,8 @@ typedef struct pim_instance pim_instance;
  * pim_create -- stage one Ising instance (J, h) on the device.
  * Defines the problem of Eq. 1 / Eq. 2 (Ising Hamiltonian and local field).
  *   out      receives the new handle (set to NULL on failure).
- *   n        number of spins, 1 <= n <= 8192 (integer couplings; the fused kernel serves
- *            n <= 256, the large-N kernel n > 256); real couplings n <= 256.
+ *   n        number of spins, 1 <= n <= 8192; the fused kernels serve n <= 256, the
+ *            large-N kernel n > 256 (integer and real couplings alike).
  *   j_type   element type of J (pim_j_type).
  *   J        host, row-major n x n; must be symmetric with a zero diagonal.
  *   h        host bias, n entries: int32 when j_type == PIM_J_INT8, else the float type
@@ -95,8 +100,8 @@ typedef struct pim_instance pim_instance;
  *            2/sqrt(N) for Max-Cut, 1/sqrt(N) for SK-1): the activation sees beta_t*c*I.
  *            Energies are reported in unscaled units of J and h.
  * Errors: PIM_ERR_INVALID (n out of range, J asymmetric, diagonal non-zero, |J| > 16 for
- *         integer J, non-finite values, scale_c <= 0 or not finite), PIM_ERR_UNSUPPORTED
- *         (real-valued J with n > 256), PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ *         integer J, non-finite values or |J| > 1e30, scale_c <= 0 or not finite; the first
+ *         offending entry in row-major order is named), PIM_ERR_NOMEM, PIM_ERR_CUDA.
  */
 int pim_create(pim_instance** out, int n, int j_type, const void* J, const void* h,
                double scale_c);

@@ -1,0 +1,458 @@
+// Mid-N PIMI sweep kernel (integer couplings, n <= 1024): persistent, one CTA per SM.
+// Serves any integer instance with n <= 1024 (plain or diagonal-encoded FP8 image).  Each
+// CTA takes (instance, 128-replica panel) units from a global counter, in the order the host
+// sorted them (largest first), and runs every sweep of a unit before it takes the next, so
+// instances of any size and replica count share one launch with no inter-CTA
+// synchronisation.
+//
+// Per unit, per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
+//   spins    the panel's spins s(t) stay in shared memory as the A operand of the field GEMM
+//            (128 replicas x npad FP8 +-1, K-major, 128-byte swizzle);
+//   fields   the couplings stream from L2 through a 4-stage cp.async.bulk ring in chunks of
+//            128 output spins; chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one
+//            of four TMEM buffers (tcgen05.mma kind::f8f6f4), so the MMAs of chunk c+1 run
+//            while the epilogue decides chunk c;
+//   decision 8 epilogue warps (4 TMEM lane quadrants x 2 groups of 64 columns): each
+//            thread owns one replica and 64 spins of every chunk, keeps their old / new
+//            bits in registers, draws the Philox blocks and looks the threshold up in the
+//            step's table at I = D + h; after the last chunk it writes the new spins into
+//            the A image (all MMAs of the sweep have completed by then);
+//   energy   E(s(t)) = -1/2 sum_i s_i (I_i + h_i), exact in int32, reduced over the two
+//            column groups in shared memory; best state (written to the output array when
+//            it improves) and first hit per replica.
+#include <climits>
+
+#include "kernels.h"
+#include "philox.cuh"
+#include "sm100_ptx.cuh"
+
+namespace pim {
+namespace {
+
+constexpr int kNT = 128;                    // output spins per chunk (MMA N)
+constexpr int kMaxNpad = 1024;
+constexpr int kMaxChunks = kMaxNpad / kNT;
+constexpr int kStages = 4;                  // coupling ring depth
+constexpr int kBufs = 4;                    // TMEM accumulators of kNT columns
+constexpr int kTabWords = 4096;             // threshold table of one step in shared memory
+constexpr int kEpiWarps = 8;
+constexpr int kGroups = kEpiWarps / 4;      // column groups per chunk
+constexpr int kCols = kNT / kGroups;        // columns of a chunk per epilogue thread
+constexpr int kWordsPT = kCols / 32;        // 32-bit spin words per thread and chunk
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = kEpiThreads + 64;  // + producer warp + MMA warp
+constexpr int kABytes = 128 * kMaxNpad;     // spin image: 128 rows x npad FP8
+constexpr int kStageBytes = kNT * 128;      // one K-block of 128 coupling rows
+constexpr int kBarCount = 2 * kStages + 2 * kBufs + 2;
+
+// 32 spins (bits) -> their 32 FP8 +-1 bytes in one row of the A image.
+__device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint32_t bits) {
+  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col, 128)) = fp8x16_from_bits(bits & 0xFFFFu);
+  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col + 16, 128)) = fp8x16_from_bits(bits >> 16);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_constant__ Launch L) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sRing = sA + kABytes;
+  uint32_t* sTab = reinterpret_cast<uint32_t*>(sRing + kStages * kStageBytes);
+  int* sRed = reinterpret_cast<int*>(sTab + kTabWords);  // [kGroups][128 rows]
+  int* sH = sRed + kGroups * 128;                         // [kMaxNpad]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sH + kMaxNpad);
+  uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + kBarCount);
+  volatile int* sUnit = reinterpret_cast<volatile int*>(sTmem + 1);
+  volatile int* sAbort = sUnit + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool epi = warp >= 2;
+  const int quad = warp & 3;                    // TMEM lane quadrant of this warp
+  const int grp = epi ? (warp - 2) >> 2 : 0;    // group of kCols columns inside a chunk
+  const int row = quad * 32 + lane;             // replica row inside the panel
+  const uint32_t full0 = smem_u32(&bars[0]);
+  const uint32_t empty0 = smem_u32(&bars[kStages]);
+  const uint32_t tfull0 = smem_u32(&bars[2 * kStages]);
+  const uint32_t tempty0 = smem_u32(&bars[2 * kStages + kBufs]);
+  const uint32_t aready = smem_u32(&bars[2 * kStages + 2 * kBufs]);
+  const uint32_t drain = aready + 8;
+
+  if (warp == 1) {
+    tmem_alloc(smem_u32(sTmem), kBufs * kNT);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, kEpiWarps);
+    }
+    mbar_init(aready, 1);
+    mbar_init(drain, 1);
+    fence_mbar_init();
+    *sAbort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  // Role counters, continued across units so every mbarrier phase is tracked exactly.
+  uint32_t loads = 0, mmas = 0, cpass = 0, apass = 0;
+  bool first_unit = true;
+  const uint32_t idesc = idesc_e4m3(128, kNT);
+
+  for (;;) {
+    if (tid == 0) *sUnit = static_cast<int>(atomicAdd(L.next, 1u));
+    __syncthreads();
+    const int u = *sUnit;
+    if (__syncthreads_or(*sAbort != 0) || u >= L.nwork) break;  // also orders the sUnit reads
+
+    const WorkItem wk = L.work[u];
+    const Problem& P = L.probs[wk.prob];
+    const int n = P.n, npad = P.npad, R = P.R;
+    const int nchunks = npad / kNT, kblocks = npad / 128;
+    const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
+
+    if (tid == 0) {
+      // ---- producer: coupling K-blocks (chunk-major) into the ring ---------------------
+      bool ok = true;
+      for (int t = t_begin; t <= t_end && ok; ++t) {
+        if (L.inject == 1 && first_unit && t == t_begin) continue;  // injected fault
+        for (int c = 0; c < nchunks && ok; ++c)
+          for (int kb = 0; kb < kblocks; ++kb) {
+            const uint32_t s = loads % kStages, use = loads / kStages;
+            if ((use > 0 && !mbar_wait_sleep(empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) ||
+                *sAbort != 0) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full0 + 8 * s, kStageBytes);
+            bulk_g2s(smem_u32(sRing + s * kStageBytes),
+                     P.jimg + static_cast<size_t>(kb) * npad * 128 + static_cast<size_t>(c) * kNT * 128,
+                     kStageBytes, full0 + 8 * s);
+            ++loads;
+          }
+      }
+      if (!ok) {
+        atomicOr(L.err, kDevErrTimeout);
+        *sAbort = 1;
+      }
+    } else if (tid == 32) {
+      // ---- MMA issuer: per sweep, wait for s(t) in the A image, then every chunk --------
+      bool ok = true;
+      for (int t = t_begin; t <= t_end && ok; ++t) {
+        if (!mbar_wait_sleep(aready, apass & 1, L.wait_ns)) {
+          ok = false;
+          break;
+        }
+        ++apass;
+        tc_fence_after();
+        for (int c = 0; c < nchunks && ok; ++c) {
+          const uint32_t b = cpass % kBufs, buse = cpass / kBufs;
+          if (buse > 0 && !mbar_wait_sleep(tempty0 + 8 * b, (buse - 1) & 1, L.wait_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int kb = 0; kb < kblocks; ++kb) {
+            const uint32_t s = mmas % kStages, use = mmas / kStages;
+            if (!mbar_wait_sleep(full0 + 8 * s, use & 1, L.wait_ns)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA) + kb * (128 * 128);
+            const uint32_t b0 = smem_u32(sRing + s * kStageBytes);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_e4m3(tmem + b * kNT, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+                       (kb > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * s);
+            ++mmas;
+          }
+          if (!ok) break;
+          mma_commit(tfull0 + 8 * b);
+          ++cpass;
+        }
+      }
+      if (!ok) {
+        atomicOr(L.err, kDevErrTimeout);
+        *sAbort = 1;
+      }
+    } else if (epi) {
+      // ---- epilogue ---------------------------------------------------------------------
+      const int etid = tid - 64;
+      const int rg = wk.rbase + row;
+      const bool row_valid = rg < R;
+      const bool warp_active = wk.rbase + quad * 32 < R;
+      // Spins of this thread's 32-column word w of chunk c that exist (columns >= n stay -1).
+      auto valid_mask = [&](int c, int w) -> uint32_t {
+        const int valid = n - (c * kNT + grp * kCols + 32 * w);
+        return valid >= 32 ? 0xFFFFFFFFu : (valid > 0 ? (1u << valid) - 1u : 0u);
+      };
+      // Bit rows of the caller's arrays as 32-bit words: word c*4 + grp*kWordsPT + w of row
+      // rg holds this thread's spins 32w .. 32w+31 of chunk c.
+      const int words = P.words;
+      uint32_t* cur_io = P.cur_bits + static_cast<size_t>(rg) * words;
+      uint32_t* best_io = P.best_bits + static_cast<size_t>(rg) * words;
+      auto word_of = [&](int c, int w) { return c * (kNT / 32) + grp * kWordsPT + w; };
+      uint32_t cur[kMaxChunks][kWordsPT], nxt[kMaxChunks][kWordsPT];
+      int best_E = INT_MAX, best_t = -1, first_hit = -1;
+#pragma unroll
+      for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+        for (int w = 0; w < kWordsPT; ++w) {
+          cur[c][w] = nxt[c][w] = 0;
+          if (c < nchunks && row_valid && word_of(c, w) < words)
+            cur[c][w] = cur_io[word_of(c, w)] & valid_mask(c, w);
+        }
+      if (L.cont && row_valid) {
+        best_E = static_cast<int>(P.best_E[rg]);
+        best_t = P.best_t[rg];
+        first_hit = P.first_hit[rg];
+      }
+      for (int k = etid; k < npad; k += kEpiThreads) sH[k] = (P.h != nullptr && k < n) ? P.h[k] : 0;
+#pragma unroll
+      for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+        for (int w = 0; w < kWordsPT; ++w)
+          if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, cur[c][w]);
+      fence_proxy_async_smem();
+      bool stop = bar_sync_or(1, kEpiThreads, false);
+      if (etid == 0) mbar_arrive(aready);
+
+      // Problem fields in registers: the loops below store to global memory, which would
+      // otherwise make the compiler reload them from the descriptor.
+      const uint32_t q = P.q;
+      const int imax = P.imax, stride = P.stride_words;
+      const uint32_t* thr = P.thr;
+      const long long target = P.target;
+      const bool tab_smem = stride <= kTabWords;
+      const bool has_target = P.has_target != 0;
+      const int dg = P.diag_img ? 256 : 0;  // diagonal-encoded image: D = I + 256 s
+      const bool fast = P.h == nullptr && !P.diag_img && tab_smem;
+      const uint16_t* sTab16 = reinterpret_cast<const uint16_t*>(sTab);
+      const uint32_t toff = 2u * static_cast<uint32_t>(imax) - 2u * 0x4B400000u;  // mod 2^32
+      for (int t = t_begin; t <= t_end && !stop; ++t) {
+        const bool last = t == t_end;
+        if (tab_smem && !last) {
+          const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t) * stride);
+          for (int k = etid; k < stride / 4; k += kEpiThreads)
+            reinterpret_cast<uint4*>(sTab)[k] = __ldg(src + k);
+        }
+        if (bar_sync_or(1, kEpiThreads, *sAbort != 0)) break;
+        const uint32_t* tab =
+            tab_smem ? sTab : thr + static_cast<size_t>(last ? t_begin : t) * stride;
+        int eacc = 0;
+        bool waitfail = false;
+#pragma unroll 1
+        for (int c = 0; c < nchunks; ++c) {
+          const uint32_t b = cpass % kBufs, buse = cpass / kBufs;
+          ++cpass;
+          if (!mbar_wait_sleep(tfull0 + 8 * b, buse & 1, L.wait_ns)) waitfail = true;
+          tc_fence_after();
+          // All kCols fields of this thread: four TMEM loads in flight while the Philox
+          // blocks of its first 32 spins are drawn, one wait, then the buffer is released.
+          uint32_t v[kCols / 16][16];
+          uint32_t rw[4][4];
+          const uint32_t blk0 = static_cast<uint32_t>((c * kNT + grp * kCols) >> 3);
+          auto draw = [&](int w) {  // Philox blocks of spins 32w .. 32w+31
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              PhiloxOut o{};
+              if (!last)
+                o = philox4x32_10_rk(blk0 + 4 * w + k, static_cast<uint32_t>(rg),
+                                     static_cast<uint32_t>(t), q, L.round_keys);
+              rw[k][0] = o.x0;
+              rw[k][1] = o.x1;
+              rw[k][2] = o.x2;
+              rw[k][3] = o.x3;
+            }
+          };
+          if (warp_active) {
+            const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) + b * kNT + grp * kCols;
+#pragma unroll
+            for (int h2 = 0; h2 < kCols / 16; ++h2) tmem_ld16(ta + 16 * h2, v[h2]);
+            draw(0);
+#pragma unroll
+            for (int h2 = 0; h2 < kCols / 16; ++h2) tmem_wait_ld(v[h2]);
+          }
+          // TMEM buffer b drained by this warp: let the MMA issuer reuse it.
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+          if (warp_active && fast) {
+            // h = 0, plain image, table in shared memory.  With vb = bits(D + 1.5 * 2^23) the
+            // field is I = vb - 0x4B400000, the 16-bit threshold of (s, I) sits at entry
+            // 2 (I + imax) + s of the table, and key < threshold (new spin -1) is the sign of
+            // key - threshold, shifted into `down`.  Energies sum the raw vb and are corrected
+            // once per 32 spins (mod 2^32 arithmetic; the true sums fit in int32).
+#pragma unroll
+            for (int w = 0; w < kWordsPT; ++w) {
+              if (w > 0) draw(w);
+              const uint32_t cw = cur[c][w];
+              uint32_t down = 0, sum_all = 0, sum_up = 0;
+#pragma unroll
+              for (int bit = 0; bit < 32; ++bit) {
+                const int e = 32 * w + bit;
+                const uint32_t vb = __float_as_uint(__fadd_rn(__uint_as_float(v[e >> 4][e & 15]), 12582912.0f));
+                const uint32_t s = (cw >> bit) & 1u;
+                sum_all += vb;
+                sum_up += s * vb;
+                if (!last) {
+                  const uint32_t th = sTab16[2u * vb + s + toff];
+                  const uint32_t word = rw[bit >> 3][(bit & 7) >> 1];
+                  const uint32_t key = (bit & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+                  down = __funnelshift_l(key - th, down, 1);
+                }
+              }
+              const uint32_t up_sum = sum_up - static_cast<uint32_t>(__popc(cw)) * 0x4B400000u;
+              const uint32_t all_sum = sum_all - 32u * 0x4B400000u;
+              eacc += static_cast<int>(2u * up_sum - all_sum);
+              nxt[c][w] = ~__brev(down) & valid_mask(c, w);
+            }
+          } else if (warp_active) {
+#pragma unroll
+            for (int w = 0; w < kWordsPT; ++w) {
+              if (w > 0) draw(w);
+              const uint32_t cw = cur[c][w];
+              uint32_t nb = 0;
+#pragma unroll
+              for (int bit = 0; bit < 32; ++bit) {
+                const int e = 32 * w + bit;  // column of this thread inside the chunk
+                const int col = c * kNT + grp * kCols + e;
+                const uint32_t s = (cw >> bit) & 1u;
+                const int hv = sH[col];
+                const int dgc = col < n ? (s ? dg : -dg) : 0;  // image diagonal inside n only
+                // exact float -> int of the integer-valued field (|D| < 2^22) by the
+                // 1.5 * 2^23 shift, at full FP32/INT rate
+                const int D = __float_as_int(__fadd_rn(__uint_as_float(v[e >> 4][e & 15]), 12582912.0f)) -
+                              0x4B400000;
+                const int I = D + hv - dgc;
+                const int term = I + hv;
+                eacc += s ? term : -term;
+                if (!last) {
+                  const uint32_t wd = tab[I + imax];
+                  const uint32_t th = s ? (wd >> 16) : (wd & 0xFFFFu);
+                  const uint32_t word = rw[bit >> 3][(bit & 7) >> 1];
+                  const uint32_t key = (bit & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+                  nb |= (key >= th ? 1u : 0u) << bit;
+                }
+              }
+              nxt[c][w] = nb & valid_mask(c, w);
+            }
+          }
+        }
+        if (!last && warp_active) {
+          // Every MMA of sweep t has completed (the last chunk's commit was awaited): the A
+          // image can take s(t+1).
+#pragma unroll
+          for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+            for (int w = 0; w < kWordsPT; ++w)
+              if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, nxt[c][w]);
+          fence_proxy_async_smem();
+        }
+        sRed[grp * 128 + row] = eacc;
+        stop = bar_sync_or(1, kEpiThreads, waitfail || *sAbort != 0);
+        if (stop) {
+          if (etid == 0) {
+            atomicOr(L.err, kDevErrTimeout);
+            *sAbort = 1;
+          }
+          break;
+        }
+        if (!last && etid == 0) mbar_arrive(aready);
+        int tot = 0;
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) tot += sRed[g * 128 + row];
+        const int E = -(tot / 2);
+        if (E < best_E) {
+          // the best state lives in the output array: written when it improves
+          best_E = E;
+          best_t = t;
+          if (row_valid) {
+#pragma unroll
+            for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+              for (int w = 0; w < kWordsPT; ++w)
+                if (c < nchunks && word_of(c, w) < words) best_io[word_of(c, w)] = cur[c][w];
+          }
+        }
+        if (has_target && first_hit < 0 && static_cast<long long>(E) <= target) first_hit = t;
+        if (last) {
+          if (row_valid) {
+#pragma unroll
+            for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+              for (int w = 0; w < kWordsPT; ++w)
+                if (c < nchunks && word_of(c, w) < words) cur_io[word_of(c, w)] = cur[c][w];
+            if (grp == 0) {
+              P.best_E[rg] = static_cast<double>(best_E);
+              P.best_t[rg] = best_t;
+              P.first_hit[rg] = first_hit;
+              P.final_E[rg] = static_cast<double>(E);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+            for (int w = 0; w < kWordsPT; ++w) cur[c][w] = nxt[c][w];
+        }
+      }
+    }
+    first_unit = false;
+  }
+
+  // ---- teardown: no copy or MMA of this CTA may still be in flight ------------------------
+  if (tid == 32) {
+    mma_commit(drain);
+    mbar_wait_sleep(drain, 0, L.wait_ns);
+  } else if (tid == 0) {
+    for (uint32_t k = loads > kStages ? loads - kStages : 0; k < loads; ++k)
+      mbar_wait_sleep(full0 + 8 * (k % kStages), (k / kStages) & 1, L.wait_ns);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, kBufs * kNT);
+}
+
+}  // namespace
+
+int sweep_mid_smem_bytes() {
+  return 1024 + kABytes + kStages * kStageBytes + kTabWords * 4 + kGroups * 128 * 4 + kMaxNpad * 4 +
+         kBarCount * 8 + 32;
+}
+
+int sweep_mid_max_npad() { return kMaxNpad; }
+
+int sweep_mid_max_blocks() {
+  const int smem = sweep_mid_smem_bytes();
+  if (cudaFuncSetAttribute(sweep_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_mid_kernel, kThreads, smem) !=
+      cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st) {
+  const int smem = sweep_mid_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(sweep_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(L.next, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  sweep_mid_kernel<<<blocks, kThreads, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace pim

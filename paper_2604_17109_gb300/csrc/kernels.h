@@ -54,6 +54,12 @@ cudaError_t launch_sweep_big(const BigLaunch& L, int nt, bool real, int blocks, 
 int sweep_big_max_blocks(int nt, bool real);  // co-resident CTAs on the current device (0 on error)
 int sweep_big_stages(int nt, bool real);      // depth of the K-block ring
 
+// Persistent mid-N kernel (integer couplings, npad <= 1024): `blocks` CTAs take the units
+// of L.work from the counter L.next (zeroed by the launch).
+cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st);
+int sweep_mid_max_blocks();
+int sweep_mid_max_npad();
+
 // Plain FP32 comparator path: per sweep one field GEMM and one update kernel.
 cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, int nprob,
                               int t_begin, int sweeps, uint32_t key_lo, uint32_t key_hi,

@@ -153,6 +153,7 @@ PIM_API int pim_anneal_noalloc(int n, const int8_t* J, double scale_c, int steps
   P.jimg = d_img;
   P.thr = d_thr;
   P.thr_diag = d_diag;
+  P.diag_img = 1;
   P.best_E = best_E;
   P.final_E = final_E;
   P.best_t = best_t;

@@ -40,6 +40,7 @@ struct Problem {
   int act;                 // 0 tanh, 1 L-level staircase
   int lut_levels;
   double target_f;         // first-hit when energy <= target_f (real couplings)
+  int diag_img;            // 1: the FP8 image carries 256 on the diagonal (D = I + 256 s)
 };
 
 // One unit of work of the fused sweep kernel: (problem index, first replica).
@@ -73,6 +74,7 @@ struct Launch {
   int* err;                // device error word
   uint64_t wait_ns;        // limit of every device-side wait (0 = 2 s)
   int inject;              // fault injection for tests: 1 = skip the first field MMA
+  unsigned int* next;      // persistent kernels: global unit counter (zeroed per launch)
 };
 
 // Launch of the large-N kernel: one instance, all sweeps, cooperative grid of

@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "host_tables.h"
@@ -348,13 +349,65 @@ PIM_API int pim_activation_levels(float b_t, int imax, int act_kind, int lut_lev
 
 namespace {
 
-// Round a double to the nearest BF16 value (ties to even) and return its bit pattern.
+// Runs fn(begin, end) over [0, count) in contiguous parts on up to 16 host threads, at
+// least `grain` items per thread.
+template <class F>
+void parallel_for(int count, F fn, int grain = 64) {
+  const int hw = static_cast<int>(std::thread::hardware_concurrency());
+  const int nth = std::max(1, std::min({hw, 16, count / grain}));
+  if (nth == 1) {
+    fn(0, count);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int per = (count + nth - 1) / nth;
+  for (int k = 0; k < nth; ++k) {
+    const int b = k * per, e = std::min(count, b + per);
+    if (b < e) th.emplace_back(fn, b, e);
+  }
+  for (auto& t : th) t.join();
+}
+
+// First (row-major order) position (i, j), i < j, where a[i*n+j] != a[j*n+i], or (-1, -1).
+// Compares 64 x 64 tiles against their transposes so both reads stay cache-friendly.
+template <class T>
+std::pair<int, int> first_asymmetry(const T* a, int n) {
+  constexpr int kB = 64;
+  const int nb = (n + kB - 1) / kB;
+  std::vector<long long> first(nb, -1);
+  std::atomic<int> next{0};  // block rows have triangular work: hand them out one by one
+  parallel_for(nb, [&](int, int) {
+    for (int bi = next++; bi < nb; bi = next++) {
+      long long hit = -1;
+      const int i1 = std::min(n, (bi + 1) * kB);
+      for (int bj = bi; bj < nb; ++bj) {
+        const int j0 = bj * kB, j1 = std::min(n, (bj + 1) * kB);
+        for (int i = bi * kB; i < i1; ++i)
+          for (int j = std::max(i + 1, j0); j < j1; ++j)
+            if (!(a[static_cast<size_t>(i) * n + j] == a[static_cast<size_t>(j) * n + i])) {
+              const long long pos = static_cast<long long>(i) * n + j;
+              if (hit < 0 || pos < hit) hit = pos;
+            }
+      }
+      first[bi] = hit;
+    }
+  }, 1);
+  for (long long h : first)
+    if (h >= 0) return {static_cast<int>(h / n), static_cast<int>(h % n)};
+  return {-1, -1};
+}
+
+// Round a double to the nearest BF16 value (8 significant bits, ties to even) and return
+// its bit pattern: round the 52-bit double significand at bit 45 (a carry moves into the
+// exponent), then narrow to float, which is exact for finite values in float range.
 uint16_t bf16_bits_rne(double v) {
-  if (v == 0.0) return std::signbit(v) ? 0x8000u : 0u;
-  int e = 0;
-  const double m = std::frexp(v, &e);           // v = m 2^e, 0.5 <= |m| < 1
-  const double q = std::nearbyint(m * 256.0);   // 8 significant bits, ties to even
-  const float f = static_cast<float>(std::ldexp(q, e - 8));  // exact in float
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof b);
+  b += ((1ull << 44) - 1) + ((b >> 45) & 1);
+  b &= ~((1ull << 45) - 1);
+  double r;
+  std::memcpy(&r, &b, sizeof r);
+  const float f = static_cast<float>(r);
   uint32_t bits;
   std::memcpy(&bits, &f, sizeof bits);
   return static_cast<uint16_t>(bits >> 16);
@@ -366,18 +419,63 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
     return j_type == PIM_J_FP32 ? static_cast<double>(static_cast<const float*>(a)[k])
                                 : static_cast<const double*>(a)[k];
   };
-  std::vector<uint16_t> jb(static_cast<size_t>(n) * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      const double v = at(J, static_cast<size_t>(i) * n + j);
-      if (!std::isfinite(v) || std::fabs(v) > 1e30)
-        return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] not finite", i, j);
-      if (i == j && v != 0.0)
-        return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] != 0 (diagonal must be zero)", i, i);
-      if (v != at(J, static_cast<size_t>(j) * n + i))
-        return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", i, j);
-      jb[static_cast<size_t>(i) * n + j] = bf16_bits_rne(v);
+  // One pass over 64 x 64 tile pairs (T, T^transpose), block rows shared out among host
+  // threads: finiteness, zero diagonal, symmetry, and both tiles rounded to BF16.  Each
+  // input element is read once; the first error in row-major order (of the upper triangle
+  // for asymmetry) is reported.
+  constexpr int kB = 64;
+  const int nb = (n + kB - 1) / kB;
+  std::unique_ptr<uint16_t[]> jb(new (std::nothrow) uint16_t[static_cast<size_t>(n) * n]);
+  if (!jb) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");
+  std::vector<long long> err_pos(nb, -1);
+  std::vector<int> err_kind(nb, 0);  // 1 not finite, 2 diagonal, 3 asymmetric
+  std::atomic<int> next{0};
+  parallel_for(nb, [&](int, int) {
+    for (int bi = next++; bi < nb; bi = next++) {
+      long long pos = -1;
+      int kind = 0;
+      auto note = [&](int i, int j, int k) {
+        const long long q = static_cast<long long>(i) * n + j;
+        if (pos < 0 || q < pos || (q == pos && k < kind)) {
+          pos = q;
+          kind = k;
+        }
+      };
+      const int i0 = bi * kB, i1 = std::min(n, i0 + kB);
+      for (int bj = bi; bj < nb; ++bj) {
+        const int j0 = bj * kB, j1 = std::min(n, j0 + kB);
+        for (int i = i0; i < i1; ++i)
+          for (int j = std::max(j0, bi == bj ? i : j0); j < j1; ++j) {
+            const double v = at(J, static_cast<size_t>(i) * n + j);
+            const double w = at(J, static_cast<size_t>(j) * n + i);
+            const bool fv = std::isfinite(v) && std::fabs(v) <= 1e30;
+            const bool fw = std::isfinite(w) && std::fabs(w) <= 1e30;
+            if (!fv) note(i, j, 1);
+            if (!fw) note(j, i, 1);
+            if (i == j && fv && v != 0.0) note(i, i, 2);
+            if (fv && fw && v != w) note(i, j, 3);
+            jb[static_cast<size_t>(i) * n + j] = bf16_bits_rne(fv ? v : 0.0);
+            jb[static_cast<size_t>(j) * n + i] = bf16_bits_rne(fw ? w : 0.0);
+          }
+      }
+      err_pos[bi] = pos;
+      err_kind[bi] = kind;
     }
+  }, 1);
+  long long pos = -1;
+  int kind = 0;
+  for (int b = 0; b < nb; ++b)
+    if (err_pos[b] >= 0 && (pos < 0 || err_pos[b] < pos || (err_pos[b] == pos && err_kind[b] < kind))) {
+      pos = err_pos[b];
+      kind = err_kind[b];
+    }
+  if (pos >= 0) {
+    const int i = static_cast<int>(pos / n), j = static_cast<int>(pos % n);
+    if (kind == 1) return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] not finite", i, j);
+    if (kind == 2)
+      return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] != 0 (diagonal must be zero)", i, i);
+    return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", i, j);
+  }
   std::vector<float> hf(n, 0.0f);
   bool has_h = false;
   if (h)
@@ -412,7 +510,7 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
   p->d_slab = static_cast<char*>(slab);
   uint16_t* d_bf = reinterpret_cast<uint16_t*>(p->d_slab);
   p->d_img = reinterpret_cast<uint8_t*>(p->d_slab + o_img);
-  if ((e = cudaMemcpyAsync(d_bf, jb.data(), nn * 2, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(d_bf, jb.get(), nn * 2, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
     return bail(e, "upload J");
   if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging)) != cudaSuccess)
     return bail(e, "stage BF16 J image");
@@ -468,21 +566,38 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if (j_type != PIM_J_INT8) return fail(PIM_ERR_INVALID, "pim_create: unknown j_type %d", j_type);
   const int8_t* J8 = static_cast<const int8_t*>(J);
   const int32_t* h32 = static_cast<const int32_t*>(h);
+  // Row pass (parallel): zero diagonal, |J_ij| <= 16 (exact in E4M3 with exact products),
+  // row sums of |J| + |h| (the field bound); then the symmetry check.
+  std::vector<long long> rowsum(n, 0);
+  std::vector<int> bad(n, -1);
+  parallel_for(n, [&](int i0, int i1) {
+    for (int i = i0; i < i1; ++i) {
+      const int8_t* row = J8 + static_cast<size_t>(i) * n;
+      long long s = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
+      for (int j = 0; j < n; ++j) {
+        const int v = row[j];
+        if ((i == j && v != 0) || v < -16 || v > 16) {
+          bad[i] = j;
+          break;
+        }
+        s += v < 0 ? -v : v;
+      }
+      rowsum[i] = s;
+    }
+  });
   long long imax = 0;
   for (int i = 0; i < n; ++i) {
-    if (J8[static_cast<size_t>(i) * n + i] != 0)
+    if (bad[i] == i)
       return fail(PIM_ERR_INVALID, "pim_create: J[%d][%d] != 0 (diagonal must be zero)", i, i);
-    long long row = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
-    for (int j = 0; j < n; ++j) {
-      const int v = J8[static_cast<size_t>(i) * n + j];
-      if (v != J8[static_cast<size_t>(j) * n + i])
-        return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", i, j);
-      if (v < -16 || v > 16)
-        return fail(PIM_ERR_INVALID, "pim_create: |J[%d][%d]| = %d > 16", i, j, v < 0 ? -v : v);
-      row += v < 0 ? -v : v;
+    if (bad[i] >= 0) {
+      const int v = J8[static_cast<size_t>(i) * n + bad[i]];
+      return fail(PIM_ERR_INVALID, "pim_create: |J[%d][%d]| = %d > 16", i, bad[i], v < 0 ? -v : v);
     }
-    if (row > imax) imax = row;
+    imax = std::max(imax, rowsum[i]);
   }
+  const auto asym = first_asymmetry(J8, n);
+  if (asym.first >= 0)
+    return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", asym.first, asym.second);
   if (imax > (1 << 20)) return fail(PIM_ERR_INVALID, "pim_create: field range too large");
   auto* p = new (std::nothrow) pim_instance();
   if (!p) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");
@@ -662,12 +777,90 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
   return PIM_OK;
 }
 
+// Kernel of each instance of a batch: kFused (n <= 256, one CTA per 128-replica panel with
+// J resident in shared memory), kMid (integer n <= 1024, persistent, J streamed from L2) or
+// kBig (n > 256, cooperative grid per instance).  Integer instances with 256 < n <= 1024
+// can run on kMid or kBig; the choice minimises a time model of the batch:
+//   kMid   a unit (instance, 128-replica panel) takes about (chunks + 1) x max(epilogue of
+//          a 128 x 128 chunk, ingest of the chunk's 128 x npad couplings) per sweep; the
+//          persistent grid finishes after max(longest unit, total / SMs);
+//   kBig   plan_big's per-sweep estimate, launches run one after another.
+// Starting from every eligible instance on kMid, the largest instances move to kBig while
+// that lowers the modelled time (a lone large instance fills more SMs on kBig).
+enum Route { kFused = 0, kMid = 1, kBig = 2 };
+constexpr double kEpiUsPerChunk = 2.0;  // 128 x 128 decisions at ~8.5e9 spin updates/s/SM
+
+double mid_unit_us(int npad) {
+  const int chunks = npad / 128;
+  const double ingest = 128.0 * npad / kIngestBytesPerUs;
+  return (chunks + 1) * std::max(kEpiUsPerChunk, ingest);
+}
+
+int route_batch(pim_instance* const* insts, const int* replicas, int count, int flags,
+                std::vector<int>& route) {
+  route.assign(count, kFused);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int mid_blocks = std::max(1, std::min(sms, sweep_mid_max_blocks()));
+  std::vector<int> eligible;
+  for (int k = 0; k < count; ++k) {
+    const pim_instance* p = insts[k];
+    if (p->real) {
+      route[k] = p->n <= kMaxNTensor ? kFused : kBig;
+    } else if (p->n <= kMaxNTensor) {
+      route[k] = (flags & PIM_PATH_MID) ? kMid : kFused;
+    } else if (p->npad > sweep_mid_max_npad() || (flags & PIM_PATH_BIG)) {
+      route[k] = kBig;
+    } else {
+      route[k] = kMid;
+      if (!(flags & PIM_PATH_MID)) eligible.push_back(k);
+    }
+  }
+  if (eligible.empty()) return PIM_OK;
+  // time model (per sweep) of the kMid launch and of the instances moved to kBig
+  double mid_total = 0.0, mid_max = 0.0;
+  for (int k = 0; k < count; ++k)
+    if (route[k] == kMid) {
+      const double u = mid_unit_us(insts[k]->npad);
+      mid_total += u * ((replicas[k] + 127) / 128);
+      mid_max = std::max(mid_max, u);
+    }
+  std::sort(eligible.begin(), eligible.end(), [&](int a, int b) {
+    return static_cast<long long>(insts[a]->npad) * replicas[a] >
+           static_cast<long long>(insts[b]->npad) * replicas[b];
+  });
+  double big_total = 0.0;
+  for (size_t e = 0; e < eligible.size(); ++e) {
+    const int k = eligible[e];
+    BigPlan plan;
+    if (plan_big(insts[k]->n, insts[k]->npad, replicas[k], false, &plan) != PIM_OK) continue;
+    const double u = mid_unit_us(insts[k]->npad);
+    const double rest_total = mid_total - u * ((replicas[k] + 127) / 128);
+    double rest_max = 0.0;
+    for (size_t f2 = e + 1; f2 < eligible.size(); ++f2)
+      rest_max = std::max(rest_max, mid_unit_us(insts[eligible[f2]]->npad));
+    for (int j = 0; j < count; ++j)
+      if (route[j] == kMid && insts[j]->n <= kMaxNTensor)
+        rest_max = std::max(rest_max, mid_unit_us(insts[j]->npad));
+    const double before = big_total + std::max(mid_max, mid_total / mid_blocks);
+    const double after = big_total + plan.us_per_sweep + std::max(rest_max, rest_total / mid_blocks);
+    if (after >= before) break;
+    route[k] = kBig;
+    big_total += plan.us_per_sweep;
+    mid_total = rest_total;
+    mid_max = rest_max;
+  }
+  return PIM_OK;
+}
+
 int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
                 int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
                 const int8_t* init_spins, int flags, cudaStream_t st) {
   if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
   if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
-  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF)) return fail(PIM_ERR_INVALID, "anneal: unknown flags");
+  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG))
+    return fail(PIM_ERR_INVALID, "anneal: unknown flags");
   const bool cont = (flags & PIM_CONTINUE) != 0;
   const bool ref = (flags & PIM_PATH_FP32REF) != 0;
   int dev = 0;
@@ -686,7 +879,8 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       return fail(PIM_ERR_STATE, "anneal: CONTINUE needs a previous run with the same replicas");
     if (ref && p->real)
       return fail(PIM_ERR_UNSUPPORTED, "anneal: the plain path takes integer couplings only");
-    if (!ref && !p->real && p->n <= kMaxNTensor && p->sched->imax > kMaxImaxTensor)
+    if (!ref && !p->real && p->n <= kMaxNTensor && !(flags & PIM_PATH_MID) &&
+        p->sched->imax > kMaxImaxTensor)
       return fail(PIM_ERR_UNSUPPORTED, "anneal: field range %d too large for the fused kernel",
                   p->sched->imax);
     for (int j = 0; j < k; ++j)
@@ -724,6 +918,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.h = p->d_h;
     P.thr = p->sched->d_thr;
     P.thr_diag = p->sched->d_thr_diag;
+    P.diag_img = p->diag ? 1 : 0;
     P.best_E = p->d_bestE;
     P.final_E = p->d_finalE;
     P.best_t = p->d_bestT;
@@ -749,22 +944,35 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
     P.target_f = std::isnan(tg) ? 0.0 : tg;
   }
-  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias | real-valued).
-  constexpr int kGroups = 6;
+  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias | real-valued) on the
+  // fused kernels, then one persistent mid-N launch; large-N instances launch one by one.
+  std::vector<int> route;
+  if (!ref) {
+    const int rc = route_batch(insts, replicas, count, flags, route);
+    if (rc != PIM_OK) return rc;
+  }
+  constexpr int kGroups = 7, kMidGroup = 6;
   std::vector<WorkItem> work[kGroups];
-  for (int k = 0; k < count; ++k) {
-    if (insts[k]->n > kMaxNTensor) continue;  // large-N kernel, launched per instance below
-    const int g = (insts[k]->npad <= 128 ? 0 : 1) +
-                  (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
+  for (int k = 0; k < count && !ref; ++k) {
+    if (route[k] == kBig) continue;
+    const int g = route[k] == kMid ? kMidGroup
+                                   : (insts[k]->npad <= 128 ? 0 : 1) +
+                                         (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
     for (int rb = 0; rb < replicas[k]; rb += 128) work[g].push_back({k, rb});
   }
+  // persistent launch: largest units first so the last wave is short
+  std::stable_sort(work[kMidGroup].begin(), work[kMidGroup].end(),
+                   [&](const WorkItem& a, const WorkItem& b) {
+                     return insts[a.prob]->npad > insts[b.prob]->npad;
+                   });
   size_t nwork_total = 0;
   for (auto& w : work) nwork_total += w.size();
 
   const size_t probs_bytes = probs.size() * sizeof(Problem);
   const size_t work_bytes = nwork_total * sizeof(WorkItem);
   const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
-  const size_t total = probs_bytes + work_bytes + init_bytes + 64;
+  const size_t counters_off = (probs_bytes + work_bytes + init_bytes + 15) & ~static_cast<size_t>(15);
+  const size_t total = counters_off + 64;
   char* d_buf = nullptr;
   CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf(total);
@@ -822,13 +1030,19 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       L.err = d_err;
       L.wait_ns = g_wait_ns.load();
       L.inject = g_inject.load();
-      if (g >= 4)
+      L.next = reinterpret_cast<unsigned int*>(d_buf + counters_off);
+      if (g == kMidGroup) {
+        const int blocks = std::min(L.nwork, sweep_mid_max_blocks());
+        if (blocks < 1) return fail(PIM_ERR_CUDA, "anneal: mid-N kernel cannot be resident");
+        CK(launch_sweep_mid(L, blocks, st), "persistent mid-N sweep kernel");
+      } else if (g >= 4) {
         CK(launch_sweep_float(L, (g & 1) ? 256 : 128, L.nwork, st), "real-valued sweep kernel");
-      else
+      } else {
         CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
+      }
     }
     for (int k = 0; k < count; ++k) {
-      if (insts[k]->n <= kMaxNTensor) continue;
+      if (route[k] != kBig) continue;
       const int rc = launch_big(probs[k], insts[k]->real, t_begin, sweeps, seed, cont, d_err, st);
       if (rc != PIM_OK) return rc;
     }

@@ -30,6 +30,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait that may suspend the thread for up to `hint_ns` nanoseconds while the phase is
+// incomplete (it resumes when the phase completes): a waiting thread does not keep issuing.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -47,6 +61,37 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t par
     if (global_ns() - t0 > limit) return false;
   }
   return true;
+}
+
+// As mbar_wait_bounded, but the polling thread sleeps inside try_wait between checks.
+static __device__ __noinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
+                                                    uint64_t limit_ns = 0) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t limit = limit_ns ? limit_ns : 2000000000ull;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
+    if (global_ns() - t0 > limit) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Named barrier `id` over `nthreads` threads that also ORs a predicate across them: every
+// participating thread gets the same answer.
+__device__ __forceinline__ bool bar_sync_or(int id, int nthreads, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(out)
+      : "r"(pred ? 1u : 0u), "r"(id), "r"(nthreads)
+      : "memory");
+  return out != 0;
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {

@@ -21,7 +21,7 @@ PIM_ERR_STATE, PIM_ERR_TIMEOUT, PIM_ERR_UNSUPPORTED = -4, -5, -6
 PIM_J_INT8, PIM_J_FP32, PIM_J_FP64 = 0, 1, 2
 PIM_NOISE_GAUSS, PIM_NOISE_UNIFORM = 0, 1
 PIM_ACT_TANH, PIM_ACT_LUT = 0, 1
-PIM_CONTINUE, PIM_PATH_FP32REF = 1, 2
+PIM_CONTINUE, PIM_PATH_FP32REF, PIM_PATH_MID, PIM_PATH_BIG = 1, 2, 4, 8
 
 # name -> (restype, argtypes); every symbol declared in include/pim.h
 SIGNATURES = {
@@ -105,13 +105,16 @@ def pim_last_error() -> str:
 
 
 def pim_create(J: np.ndarray, h: np.ndarray | None = None, scale_c: float = 1.0) -> int:
-    """Stage an instance; integer J -> PIM_J_INT8 (int32 h), float J -> PIM_J_FP64 (float64
-    h).  Returns the opaque handle (an int)."""
+    """Stage an instance; integer J -> PIM_J_INT8 (int32 h), float32 J -> PIM_J_FP32 (float32
+    h), other float J -> PIM_J_FP64 (float64 h).  Returns the opaque handle (an int)."""
     J = np.asarray(J)
     n = J.shape[0]
     if J.shape != (n, n):
         raise ValueError("J must be square")
-    if np.issubdtype(J.dtype, np.floating):
+    if J.dtype == np.float32:
+        jt, J = PIM_J_FP32, np.ascontiguousarray(J)
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.float32)
+    elif np.issubdtype(J.dtype, np.floating):
         jt, J = PIM_J_FP64, np.ascontiguousarray(J, dtype=np.float64)
         hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
     else:

@@ -1,6 +1,6 @@
-"""GPU parity: the fused tensor-core sweep kernel and the plain FP32 path, called through
-the C ABI, against the CPU oracle -- bit-exact on integer instances (spins, energies,
-steps)."""
+"""GPU parity: every sweep kernel (fused n <= 256, persistent mid-N, large-N cooperative)
+and the plain FP32 path, called through the C ABI, against the CPU oracle -- bit-exact on
+integer instances (spins, energies, steps)."""
 import math
 
 import numpy as np
@@ -15,7 +15,9 @@ from gpu_helpers import assert_same, collect, oracle_run, pim, run_library
 
 pytestmark = pytest.mark.gpu
 
-PATHS = [0, 2]  # fused tensor-core kernel, plain FP32 path (PIM_PATH_FP32REF)
+# library's choice, plain FP32 path (PIM_PATH_FP32REF), persistent mid-N kernel for every
+# integer n <= 1024 (PIM_PATH_MID), large-N kernel for every n > 256 (PIM_PATH_BIG)
+PATHS = [0, 2, 4, 8]
 
 CASES = [
     # kind, n, replicas, sweeps, seed
@@ -31,6 +33,10 @@ CASES = [
     ("sk2", 150, 140, 30, 8),   # couplings +-2: field range past 255, general-bias kernel
     ("sk", 300, 200, 25, 10),   # large-N kernel: 6 column blocks x 2 replica tiles
     ("maxcut", 520, 129, 15, 11),  # large-N kernel: ragged spins (last block) and replicas
+    ("sk", 700, 257, 6, 14),    # three replica panels, ragged last chunk
+    ("sk", 1000, 100, 8, 12),   # largest mid-N image (npad 1024), ragged
+    ("maxcut", 1024, 130, 6, 13),  # exactly npad 1024
+    ("sk", 1025, 64, 4, 15),    # past the mid-N limit: large-N kernel on every path
 ]
 
 
@@ -55,7 +61,7 @@ def test_matches_oracle(kind, n, R, T, seed, flags):
     assert_same(got, want, label=f"{kind} n={n} path={flags}")
 
 
-@pytest.mark.parametrize("flags", PATHS)
+@pytest.mark.parametrize("flags", [0, 2, 4])
 def test_bias_uniform_noise_lut_and_host_init(flags):
     """Non-zero h, Eq. 3 uniform noise, the 4-level LUT activation and host-given spins."""
     inst = sk_pm1(70, 11)
@@ -73,7 +79,7 @@ def test_bias_uniform_noise_lut_and_host_init(flags):
         assert_same(got, want, label=f"{noise}/{act} path={flags}")
 
 
-@pytest.mark.parametrize("flags", PATHS)
+@pytest.mark.parametrize("flags", [0, 2, 4])
 def test_resume_matches_uninterrupted(flags):
     P = pim()
     inst = maxcut_er(60, 3)
@@ -145,6 +151,60 @@ def test_batch_equals_per_instance_oracle():
         for hd, inst, R, q, tg in zip(handles, insts, reps, ids, targets):
             want = oracle_run(inst, beta, eta, 0.6, replicas=R, seed=77, q=q, target=tg)
             assert_same(collect(hd, inst.n), want, label=f"n={inst.n}")
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+@pytest.mark.parametrize("flags", [0, 4])
+def test_uneven_batch_equals_per_instance_oracle(flags):
+    """Instances of uneven size (n = 20 .. 1100) and replica count (32 .. 300), Max-Cut and
+    SK mixed, in one call: the library's routing (fused / persistent / large-N) or every
+    n <= 1024 on the persistent kernel; each instance is exactly its own oracle run."""
+    P = pim()
+    rng = np.random.default_rng(42)
+    sizes = [20, 1100, 300, 96, 640, 257, 1000, 150, 513, 64]
+    insts = [(sk_pm1 if k % 2 else maxcut_er)(n, 100 + k) for k, n in enumerate(sizes)]
+    reps = [int(x) for x in rng.choice([32, 64, 96, 160, 224, 300], size=len(sizes))]
+    ids = list(range(50, 50 + len(sizes)))
+    T = 12
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.6)
+        targets = [-0.4 * i.n for i in insts]
+        P.pim_anneal_batch(handles, reps, T, seed=5, instance_ids=ids, targets=targets,
+                           flags=flags)
+        for hd, inst, R, q, tg in zip(handles, insts, reps, ids, targets):
+            want = oracle_run(inst, beta, eta, 0.6, replicas=R, seed=5, q=q, target=tg)
+            assert_same(collect(hd, inst.n), want, label=f"n={inst.n} R={R}")
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+def test_persistent_kernel_more_units_than_sms():
+    """More (instance, panel) units than resident CTAs: every CTA of the persistent mid-N
+    kernel takes several units in turn; sampled replicas of every instance are bit-exact."""
+    P = pim()
+    insts = [sk_pm1(300 + 7 * k, 200 + k) for k in range(40)]
+    R, T = 512, 6
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, R, T, seed=9, flags=P.PIM_PATH_MID)
+        rows = [0, 200, 511]
+        for q in range(0, 40, 3):
+            got = collect(handles[q], insts[q].n)
+            want = oracle_run(insts[q], beta, eta, 0.5, replica_ids=rows, seed=9, q=q)
+            assert_same(got, want, rows=rows, label=f"q={q}")
+            J, h = insts[q].J, insts[q].h
+            assert np.array_equal(oracle.energy(J, h, got["final_state"]), got["final_E"])
     finally:
         for hd in handles:
             P.pim_destroy(hd)
