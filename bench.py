@@ -38,7 +38,8 @@ METRIC = "spin-updates/s"
 @dataclasses.dataclass
 class Workload:
     key: str
-    kind: str      # "sk", "maxcut" (unweighted, integer) or "maxcut_gauss" (real, BF16)
+    kind: str      # "sk", "maxcut" (unweighted, integer), "maxcut_gauss" (real, BF16) or
+                   # "uneven" (Max-Cut / SK mix of uneven n and replica count)
     n: int
     count: int     # instances per GPU
     replicas: int
@@ -55,6 +56,8 @@ WORKLOADS = {
     "sk4096": Workload("sk4096", "sk", 4096, 1, 256, 10000, 0.5),
     "maxcut100": Workload("maxcut100", "maxcut", 100, 1, 64, 1000, 0.7),
     "maxcut8192": Workload("maxcut8192", "maxcut_gauss", 8192, 1, 256, 10000, 0.7),
+    # n ~ U[64, 1024], replicas ~ U{32, .., 512}; n and replicas here are the maxima
+    "uneven4096": Workload("uneven4096", "uneven", 1024, 4096, 512, 1000, 0.5),
 }
 
 # Fused small-N kernel: algorithmic work per spin update, in lane issue slots of the
@@ -84,7 +87,21 @@ def _instance(w: Workload, seed: int):
 
 def _couplings(w: Workload) -> str:
     return {"sk": "SK +-1, h=0", "maxcut": "ER(0.5) Max-Cut, J=-A",
-            "maxcut_gauss": "ER(0.5) Max-Cut with N(0,1) weights, J=-W rounded to BF16"}[w.kind]
+            "maxcut_gauss": "ER(0.5) Max-Cut with N(0,1) weights, J=-W rounded to BF16",
+            "uneven": "even k: ER(0.5) Max-Cut J=-A (xi 0.7); odd k: SK +-1 (xi 0.5); "
+                      "n ~ U[64,1024], replicas ~ U{32..512 step 32}"}[w.kind]
+
+
+def _batch_inputs(w: Workload, rank: int):
+    """(instances, replicas, instance ids, xi per instance) of this rank's share."""
+    if w.kind == "uneven":
+        from workloads import uneven_batch
+        insts, reps = uneven_batch(w.count, seed=rank)
+        ids = [rank * w.count + k for k in range(w.count)]
+        xis = [0.7 if k % 2 == 0 else 0.5 for k in range(w.count)]
+        return insts, reps, ids, xis
+    ids = _instance_ids(rank, w.count)
+    return [_instance(w, int(q)) for q in ids], [w.replicas] * w.count, ids, [w.xi] * w.count
 
 
 def _peaks():
@@ -165,13 +182,17 @@ def _oracle_sample(w: Workload, budget_s: float, max_instances: int, replicas: i
     beta, eta = _schedule(w.sweeps)
     done, elapsed = 0, 0.0
     k = 0
+    if w.kind == "uneven":
+        from workloads import uneven_instance, uneven_sizes
+        sizes = uneven_sizes(w.count, seed=0)[0]
     while k < max_instances:
-        inst = _instance(w, k)  # instance generation is not oracle work: outside the clock
+        # instance generation is not oracle work: outside the clock
+        inst = uneven_instance(k, sizes[k]) if w.kind == "uneven" else _instance(w, k)
         t0 = time.perf_counter()
         oracle.anneal(inst.J, inst.h, inst.c, beta, eta, w.xi, replicas=replicas, seed=0, q=k,
                       sweeps=sweeps)
         elapsed += time.perf_counter() - t0
-        done += w.n * replicas * sweeps
+        done += inst.n * replicas * sweeps
         k += 1
         if elapsed > budget_s:
             break
@@ -282,27 +303,33 @@ def run_ours(args, w: Workload):
     from paper_2604_17109_gb300 import pim
 
     pkg_build.build()
-    n_inst, sweeps, R, N = w.count, w.sweeps, w.replicas, w.n
+    sweeps = w.sweeps
     beta, eta = _schedule(sweeps)
-    ids = np.asarray(_instance_ids(rank, n_inst), dtype=np.uint32)
-    insts = [_instance(w, int(q)) for q in ids]
+    insts, reps, ids, xis = _batch_inputs(w, rank)
+    ids = np.asarray(ids, dtype=np.uint32)
+    n_inst = len(insts)
+    real = w.kind == "maxcut_gauss"
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    # ---- device-resident inputs: staged once, reused by every timed step -------------
+    # ---- device-resident inputs: staged once; the batch plan (kernel routing, device
+    # descriptors, result buffers) is built once and every step replays its CUDA graph ----
     handles = [pim.pim_create(i.J, None, i.c) for i in insts]
-    for hd in handles:
-        pim.pim_set_schedule(hd, beta, eta, w.xi)
-    updates_per_step = N * R * sweeps * n_inst
+    for hd, xi in zip(handles, xis):
+        pim.pim_set_schedule(hd, beta, eta, xi)
+    batch = pim.pim_batch_create(handles, reps, instance_ids=ids)
+    updates_per_step = sum(i.n * r for i, r in zip(insts, reps)) * sweeps
+    flops_per_step = sum(2.0 * i.n * i.n * r for i, r in zip(insts, reps)) * sweeps
 
     def step():
-        pim.pim_anneal_batch(handles, R, sweeps, seed=0, instance_ids=ids, stream=stream)
+        pim.pim_batch_run(batch, sweeps, seed=0, stream=stream)
 
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
         step()
     torch.cuda.synchronize()
+    info = pim.pim_batch_info(batch)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -327,25 +354,26 @@ def run_ours(args, w: Workload):
     ms_per_step = total_ms / args.steps
     value = updates_per_step * world / (ms_per_step * 1e-3)
     k_ms = statistics.mean(kernel_ms)
+    pim.pim_batch_destroy(batch)
 
     # ---- end to end through the public API from host buffers ---------------------------
-    e2e_steps = max(1, min(3, args.steps))
-    real = w.kind == "maxcut_gauss"
+    # per step: stage every instance from host memory (J upload), set its schedule, one
+    # batched anneal, read every replica's best energy and best state back, release.
+    e2e_steps = 1 if n_inst > 1000 else max(1, min(3, args.steps))
     h2d = sum(i.n * i.n * (2 if real else 1) for i in insts)  # BF16 or int8 couplings copied
-    words = ((N + 63) // 64) * 2
-    d2h = n_inst * (R * (8 + 4 + 4 + 8) + R * words * 4)
+    d2h = sum(r * (8 + 4 + 4 + 8) + r * (((i.n + 63) // 64) * 2) * 4 for i, r in zip(insts, reps))
     out_E = [None] * n_inst
     torch.cuda.synchronize()
     _barrier(world)
     e0 = time.perf_counter()
     for _ in range(e2e_steps):
         hs = [pim.pim_create(i.J, None, i.c) for i in insts]
-        for hd in hs:
-            pim.pim_set_schedule(hd, beta, eta, w.xi)
-        pim.pim_anneal_batch(hs, R, sweeps, seed=0, instance_ids=ids, stream=stream)
-        for q, hd in enumerate(hs):
+        for hd, xi in zip(hs, xis):
+            pim.pim_set_schedule(hd, beta, eta, xi)
+        pim.pim_anneal_batch(hs, reps, sweeps, seed=0, instance_ids=ids, stream=stream)
+        for q, (hd, inst) in enumerate(zip(hs, insts)):
             out_E[q] = pim.pim_energies(hd)["best_E"]
-            pim.pim_best_state(hd, N)
+            pim.pim_best_state(hd, inst.n)
         for hd in hs:
             pim.pim_destroy(hd)
     e2e_s = _max_over_ranks(time.perf_counter() - e0, world) / e2e_steps
@@ -356,16 +384,17 @@ def run_ours(args, w: Workload):
     # by any replica (the relaxed criterion of the supplementary CCTS section, with the
     # putative ground state of this run in place of the unavailable reference energy).
     tts = None
-    if N <= 256:
-        step()
+    if w.n <= 256 and w.kind != "uneven":
+        R = reps[0]
+        pim.pim_anneal_batch(handles, reps, sweeps, seed=0, instance_ids=ids, stream=stream)
         torch.cuda.synchronize()
         best = [pim.pim_energies(hd)["best_E"] for hd in handles]
         p_bar = float(np.mean([np.mean(b <= 0.999 * b.min()) for b in best]))
         n_plain = min(2, n_inst)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        pim.pim_anneal_batch(handles[:n_plain], R, sweeps, seed=0, instance_ids=ids[:n_plain],
-                             flags=pim.PIM_PATH_FP32REF, stream=stream)
+        pim.pim_anneal_batch(handles[:n_plain], reps[:n_plain], sweeps, seed=0,
+                             instance_ids=ids[:n_plain], flags=pim.PIM_PATH_FP32REF, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         plain_ms_per_instance = ev0.elapsed_time(ev1) / n_plain
@@ -389,15 +418,14 @@ def run_ours(args, w: Workload):
     peaks, peak_kind = _peaks()
     clk = clocks.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    flops = 2.0 * N * N * R * sweeps * n_inst
     tensor_peak = float(peaks["bf16_tflops"]) * (1.0 if real else 2.0)
-    tensor_achieved = flops / (k_ms * 1e-3) / 1e12
+    tensor_achieved = flops_per_step / (k_ms * 1e-3) / 1e12
     tensor = {"bound": "tensor", "achieved": tensor_achieved, "peak": tensor_peak,
               "unit": "TFLOP/s", "frac": tensor_achieved / tensor_peak, "traffic": None,
               "kernel_ms": k_ms,
               "peak_basis": (f"bf16 {peak_kind} burst" if real else
                              f"bf16 {peak_kind} burst x 2 (FP8/BF16 nominal ratio)")}
-    if N <= 256:
+    if w.n <= 256:
         alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
         alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
@@ -405,30 +433,37 @@ def run_ours(args, w: Workload):
                     "kernel": "sweep_tc_kernel<256>", "kernel_ms": k_ms,
                     "ops_per_spin_update": ALU_OPS_PER_SPIN_UPDATE,
                     "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
+    elif w.kind == "uneven":
+        roofline = dict(tensor, kernel="sweep_mid_kernel (+ fused sweep kernels for n <= 256)")
     else:
         roofline = dict(tensor, kernel=f"sweep_big_kernel<{'BF16' if real else 'FP8'}>")
         # couplings stream from L2 / HBM once per replica tile per sweep
-        j_bytes = N * N * (2 if real else 1) * ((R + 127) // 128) * sweeps * n_inst
+        j_bytes = sum(i.n * i.n * (2 if real else 1) * ((r + 127) // 128)
+                      for i, r in zip(insts, reps)) * sweeps
         hbm = j_bytes / (k_ms * 1e-3) / 1e9
         roofline["coupling_stream"] = {"achieved": hbm, "unit": "GB/s",
                                        "frac_of_hbm": hbm / float(peaks["hbm_gbs"])}
+    config = {"workload": w.name, "n": w.n, "instances_per_gpu": n_inst,
+              "replicas": w.replicas if w.kind != "uneven" else "32..512",
+              "sweeps": sweeps, "couplings": _couplings(w),
+              "schedule": f"linear beta 0.1->3, eta=sqrt(beta/5), xi={w.xi if w.kind != 'uneven' else '0.7/0.5'}",
+              "l2": "flushed between timed steps (256 MiB write)",
+              "launch": "batch plan replayed as one CUDA graph" if info["uses_graph"]
+                        else "batch plan, direct launches"}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32" if real else "fp8e4m3/i32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16/f32" if real else "fp8e4m3/i32",
         "data": "synthetic",
-        "config": {"workload": w.name, "n": N, "instances_per_gpu": n_inst, "replicas": R,
-                   "sweeps": sweeps,
-                   "couplings": _couplings(w),
-                   "schedule": f"linear beta 0.1->3, eta=sqrt(beta/5), xi={w.xi}",
-                   "l2": "flushed between timed steps (256 MiB write)"},
+        "config": config,
         "roofline": roofline,
         "tensor_pipe": tensor,
         "tts99": tts,
         "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": info["kernel_launches"] * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,
         "min_best_energy_instance0": float(np.min(out_E[0])),

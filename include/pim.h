@@ -162,6 +162,43 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
                      int sweeps, uint64_t seed, const uint32_t* instance_ids,
                      const double* targets, int flags, void* cuda_stream);
 
+/*
+ * Batch plans -- many instances of uneven n and replica count in one persistent,
+ * CUDA-graph-replayed launch sequence.  This is the device-side counterpart of the
+ * supplementary "Kernel execution" and "Host-side task scheduling" subsections (one kernel
+ * processes instance after instance without idling, fed by a scheduler): here the
+ * instances' (instance, replica panel) units are taken by persistent CTAs from a device
+ * counter, with no host work between instances.
+ *
+ * pim_batch_create builds, once, everything a run of the batch needs: the kernel of each
+ * instance (fused n <= 256, persistent mid-N n <= 1024 integer, large-N cooperative; chosen
+ * by the library's time model unless PIM_PATH_MID / PIM_PATH_BIG force it), the problem
+ * descriptors and unit lists on the device, the result buffers of every instance and the
+ * large-N scratch.
+ *   out           receives the handle (NULL on failure).
+ *   insts, count  instances with schedules; they must outlive the batch and keep their
+ *                 schedule and replica counts while it exists (pim_batch_run checks).
+ *   replicas      count entries >= 1; instance_ids (NULL = 0..count-1) and targets (NULL
+ *                 or NaN = none) as in pim_anneal_batch.
+ *   flags         0, PIM_PATH_MID or PIM_PATH_BIG.
+ * pim_batch_run runs sweeps t_begin .. t_begin+sweeps-1 of every instance, asynchronously on
+ * `cuda_stream`: the first run with given (t_begin, sweeps, seed, run_flags) captures the
+ * batch's launches into a CUDA graph (later changes update the instantiated graph in
+ * place) and every run replays it with one cudaGraphLaunch.  run_flags: 0 or PIM_CONTINUE.
+ * Results are read with the per-instance getters.  A batch whose launches cannot be
+ * captured runs them directly instead (pim_batch_info reports which).
+ * pim_batch_info: kernel launches per run and whether runs replay a graph (1) or not (0).
+ * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (instance changed since creation, CONTINUE without
+ *         a previous run), PIM_ERR_UNSUPPORTED, PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+typedef struct pim_batch pim_batch;
+int pim_batch_create(pim_batch** out, pim_instance* const* insts, int count, const int* replicas,
+                     const uint32_t* instance_ids, const double* targets, int flags);
+int pim_batch_run(pim_batch* batch, int t_begin, int sweeps, uint64_t seed, int run_flags,
+                  void* cuda_stream);
+int pim_batch_info(const pim_batch* batch, int* kernel_launches, int* uses_graph);
+void pim_batch_destroy(pim_batch* batch);
+
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up). */
 int pim_sync(pim_instance* inst);

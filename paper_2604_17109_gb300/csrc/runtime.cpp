@@ -350,11 +350,12 @@ PIM_API int pim_activation_levels(float b_t, int imax, int act_kind, int lut_lev
 namespace {
 
 // Runs fn(begin, end) over [0, count) in contiguous parts on up to 16 host threads, at
-// least `grain` items per thread.
+// least `grain` items per thread; small jobs (`work` < 2M elements) stay on the calling
+// thread, where spawning threads would cost more than it saves.
 template <class F>
-void parallel_for(int count, F fn, int grain = 64) {
+void parallel_for(int count, F fn, int grain = 64, size_t work = SIZE_MAX) {
   const int hw = static_cast<int>(std::thread::hardware_concurrency());
-  const int nth = std::max(1, std::min({hw, 16, count / grain}));
+  const int nth = work < (2u << 20) ? 1 : std::max(1, std::min({hw, 16, count / grain}));
   if (nth == 1) {
     fn(0, count);
     return;
@@ -391,7 +392,7 @@ std::pair<int, int> first_asymmetry(const T* a, int n) {
       }
       first[bi] = hit;
     }
-  }, 1);
+  }, 1, static_cast<size_t>(n) * n);
   for (long long h : first)
     if (h >= 0) return {static_cast<int>(h / n), static_cast<int>(h % n)};
   return {-1, -1};
@@ -461,7 +462,7 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
       err_pos[bi] = pos;
       err_kind[bi] = kind;
     }
-  }, 1);
+  }, 1, static_cast<size_t>(n) * n);
   long long pos = -1;
   int kind = 0;
   for (int b = 0; b < nb; ++b)
@@ -584,7 +585,7 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
       }
       rowsum[i] = s;
     }
-  });
+  }, 64, static_cast<size_t>(n) * n);
   long long imax = 0;
   for (int i = 0; i < n; ++i) {
     if (bad[i] == i)
@@ -738,7 +739,7 @@ int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
 // co-resident grid (each group is an independent cooperative launch); per launch scratch
 // (two spin images, energy accumulators, barrier words) comes from the stream-ordered pool.
 int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t seed, bool cont,
-               int* d_err, cudaStream_t st) {
+               int* d_err, char* scratch, int* launches, cudaStream_t st) {
   BigPlan plan;
   const int rc = plan_big(P.n, P.npad, P.R, real, &plan);
   if (rc != PIM_OK) return rc;
@@ -751,8 +752,9 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
     const size_t img_bytes = static_cast<size_t>(rpad) * P.npad * eb;
     const size_t energy_bytes = sizeof(float) * 3 * rpad;
     const size_t bytes = 2 * img_bytes + energy_bytes + 256;
-    char* d = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st), "cudaMallocAsync large-N scratch");
+    char* d = scratch;
+    if (!scratch)
+      CK(cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st), "cudaMallocAsync large-N scratch");
     CK(cudaMemsetAsync(d + 2 * img_bytes, 0, energy_bytes + 256, st), "clear large-N scratch");
     BigLaunch L{};
     L.P = P;
@@ -772,7 +774,8 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
     L.wait_ns = g_wait_ns.load();
     L.inject = g_inject.load();
     CK(launch_sweep_big(L, plan.nt, real, tiles * ncb, st), "large-N sweep kernel");
-    CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
+    if (!scratch) CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
+    if (launches) ++*launches;
   }
   return PIM_OK;
 }
@@ -854,9 +857,24 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
   return PIM_OK;
 }
 
-int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
-                int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
-                const int8_t* init_spins, int flags, cudaStream_t st) {
+constexpr int kGroups = 7, kMidGroup = 6;
+
+// Launch description of one batch: problem descriptors, the unit lists of each kernel group
+// (fused: npad 128 | 256 x diagonal-encoded | general bias | real-valued; persistent mid-N),
+// the large-N instances, and the layout of the one device buffer that holds them.
+struct BatchPlan {
+  std::vector<Problem> probs;
+  std::vector<int> route;
+  std::vector<WorkItem> work[kGroups];
+  int maxR = 0, max_words = 0, stride_max = 4;
+  size_t work_off[kGroups] = {};
+  size_t init_off = 0, init_bytes = 0, counters_off = 0, total = 0;
+  size_t big_scratch = 0;  // largest scratch one large-N launch of this batch needs
+};
+
+// Argument checks shared by pim_anneal, pim_anneal_batch and pim_batch_run.
+int check_batch(pim_instance* const* insts, int count, const int* replicas, int t_begin,
+                int sweeps, const double* targets, int flags, bool check_steps) {
   if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
   if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
   if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG))
@@ -865,14 +883,13 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   const bool ref = (flags & PIM_PATH_FP32REF) != 0;
   int dev = 0;
   cudaGetDevice(&dev);
-  int maxR = 0, max_words = 0, stride_max = 4, npad_max = 0;
   for (int k = 0; k < count; ++k) {
     pim_instance* p = insts[k];
     if (!p) return fail(PIM_ERR_INVALID, "anneal: instance %d is NULL", k);
     if (p->device != dev) return fail(PIM_ERR_INVALID, "anneal: instance %d lives on device %d", k, p->device);
     if (!p->sched) return fail(PIM_ERR_STATE, "anneal: instance %d has no schedule", k);
     if (replicas[k] < 1) return fail(PIM_ERR_INVALID, "anneal: replicas[%d] = %d < 1", k, replicas[k]);
-    if (static_cast<long long>(t_begin) + sweeps > p->sched->steps)
+    if (check_steps && static_cast<long long>(t_begin) + sweeps > p->sched->steps)
       return fail(PIM_ERR_INVALID, "anneal: t_begin + sweeps = %lld exceeds the %d schedule steps",
                   static_cast<long long>(t_begin) + sweeps, p->sched->steps);
     if (cont && (!p->has_results || p->R != replicas[k]))
@@ -887,32 +904,19 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       if (insts[j] == p) return fail(PIM_ERR_INVALID, "anneal: instance listed twice");
     if (targets && std::isnan(targets[k]) == false && !std::isfinite(targets[k]))
       return fail(PIM_ERR_INVALID, "anneal: target %d not finite", k);
-    maxR = std::max(maxR, replicas[k]);
-    max_words = std::max(max_words, p->words);
-    stride_max = std::max(stride_max, p->sched->stride_words);
-    npad_max = std::max(npad_max, p->npad);
   }
-  if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
-  for (int k = 0; k < count; ++k) {
-    pim_instance* p = insts[k];
-    CK(cudaStreamWaitEvent(st, p->ready, 0), "cudaStreamWaitEvent");  // inputs staged
-    if (ref && !p->d_jf) {  // float32 couplings of the plain path, built on first use
-      void* d = nullptr;
-      CK(pool_alloc(&d, static_cast<size_t>(p->n) * p->n * sizeof(float), p->device, st),
-         "allocating float32 J");
-      p->d_jf = static_cast<float*>(d);
-      CK(launch_stage_f32(p->d_J8, p->n, p->d_jf, st), "stage float32 J");
-    }
-    int rc = ensure_results(p, replicas[k], st);
-    if (rc != PIM_OK) return rc;
-  }
-  int* d_err = device_error_word(dev);
-  if (!d_err) return fail(PIM_ERR_NOMEM, "anneal: error word allocation failed");
+  return PIM_OK;
+}
 
-  std::vector<Problem> probs(count);
+// Host side of a batch: descriptors (instances must have their result buffers), routing,
+// unit lists and the device buffer layout.
+int build_plan(pim_instance* const* insts, int count, const int* replicas, const uint32_t* ids,
+               const double* targets, int flags, size_t init_bytes, BatchPlan& B) {
+  const bool ref = (flags & PIM_PATH_FP32REF) != 0;
+  B.probs.assign(count, Problem{});
   for (int k = 0; k < count; ++k) {
     pim_instance* p = insts[k];
-    Problem& P = probs[k];
+    Problem& P = B.probs[k];
     P.jimg = p->d_img;
     P.jf = p->d_jf;
     P.h = p->d_h;
@@ -943,94 +947,116 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     P.has_target = std::isnan(tg) ? 0 : 1;
     P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
     P.target_f = std::isnan(tg) ? 0.0 : tg;
+    B.maxR = std::max(B.maxR, replicas[k]);
+    B.max_words = std::max(B.max_words, p->words);
+    B.stride_max = std::max(B.stride_max, p->sched->stride_words);
   }
-  // Launch groups: (npad 128 | 256) x (diagonal-encoded | general bias | real-valued) on the
-  // fused kernels, then one persistent mid-N launch; large-N instances launch one by one.
-  std::vector<int> route;
+  B.route.assign(count, kFused);
   if (!ref) {
-    const int rc = route_batch(insts, replicas, count, flags, route);
+    const int rc = route_batch(insts, replicas, count, flags, B.route);
     if (rc != PIM_OK) return rc;
   }
-  constexpr int kGroups = 7, kMidGroup = 6;
-  std::vector<WorkItem> work[kGroups];
+  for (auto& w : B.work) w.clear();
   for (int k = 0; k < count && !ref; ++k) {
-    if (route[k] == kBig) continue;
-    const int g = route[k] == kMid ? kMidGroup
-                                   : (insts[k]->npad <= 128 ? 0 : 1) +
-                                         (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
-    for (int rb = 0; rb < replicas[k]; rb += 128) work[g].push_back({k, rb});
+    if (B.route[k] == kBig) {
+      BigPlan plan;
+      const int rc = plan_big(insts[k]->n, insts[k]->npad, replicas[k], insts[k]->real, &plan);
+      if (rc != PIM_OK) return rc;
+      const size_t rpad = static_cast<size_t>(plan.tiles_per_launch) * 128;
+      B.big_scratch = std::max(B.big_scratch, 2 * rpad * insts[k]->npad * (insts[k]->real ? 2 : 1) +
+                                                  sizeof(float) * 3 * rpad + 256);
+      continue;
+    }
+    const int g = B.route[k] == kMid ? kMidGroup
+                                     : (insts[k]->npad <= 128 ? 0 : 1) +
+                                           (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
+    for (int rb = 0; rb < replicas[k]; rb += 128) B.work[g].push_back({k, rb});
   }
   // persistent launch: largest units first so the last wave is short
-  std::stable_sort(work[kMidGroup].begin(), work[kMidGroup].end(),
+  std::stable_sort(B.work[kMidGroup].begin(), B.work[kMidGroup].end(),
                    [&](const WorkItem& a, const WorkItem& b) {
                      return insts[a.prob]->npad > insts[b.prob]->npad;
                    });
-  size_t nwork_total = 0;
-  for (auto& w : work) nwork_total += w.size();
-
-  const size_t probs_bytes = probs.size() * sizeof(Problem);
-  const size_t work_bytes = nwork_total * sizeof(WorkItem);
-  const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
-  const size_t counters_off = (probs_bytes + work_bytes + init_bytes + 15) & ~static_cast<size_t>(15);
-  const size_t total = counters_off + 64;
-  char* d_buf = nullptr;
-  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
-  std::vector<char> h_buf(total);
-  std::memcpy(h_buf.data(), probs.data(), probs_bytes);
-  const WorkItem* d_work[kGroups];
-  {
-    size_t off = probs_bytes;
-    for (int g = 0; g < kGroups; ++g) {
-      if (!work[g].empty())
-        std::memcpy(h_buf.data() + off, work[g].data(), work[g].size() * sizeof(WorkItem));
-      d_work[g] = reinterpret_cast<const WorkItem*>(d_buf + off);
-      off += work[g].size() * sizeof(WorkItem);
-    }
+  size_t off = align256(B.probs.size() * sizeof(Problem));
+  for (int g = 0; g < kGroups; ++g) {
+    B.work_off[g] = off;
+    off += B.work[g].size() * sizeof(WorkItem);
   }
-  if (init_bytes) std::memcpy(h_buf.data() + probs_bytes + work_bytes, init_spins, init_bytes);
+  B.init_off = align256(off);
+  B.init_bytes = init_bytes;
+  B.counters_off = align256(B.init_off + init_bytes);
+  B.total = B.counters_off + 256;
+  return PIM_OK;
+}
+
+void pack_plan(const BatchPlan& B, const int8_t* init_spins, std::vector<char>& h) {
+  h.assign(B.total, 0);
+  std::memcpy(h.data(), B.probs.data(), B.probs.size() * sizeof(Problem));
+  for (int g = 0; g < kGroups; ++g)
+    if (!B.work[g].empty())
+      std::memcpy(h.data() + B.work_off[g], B.work[g].data(), B.work[g].size() * sizeof(WorkItem));
+  if (B.init_bytes) std::memcpy(h.data() + B.init_off, init_spins, B.init_bytes);
+}
+
+// Event record that also works inside stream capture: there it becomes an event-record
+// node of the graph, so the host can time and wait on replays.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
+// Every device operation of one run of a batch, in stream order: initial spins (unless
+// continuing), the timer start, the kernel groups, the large-N launches, the timer stop.
+// `big_scratch` (may be null) is a preallocated scratch of B.big_scratch bytes.
+int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instance* const* insts,
+                 int count, int t_begin, int sweeps, uint64_t seed, bool cont, bool ref,
+                 LaunchTimer* timer, int* d_err, int* launches, cudaStream_t st) {
   const Problem* d_probs = reinterpret_cast<const Problem*>(d_buf);
-  const int8_t* d_init = init_bytes ? reinterpret_cast<const int8_t*>(d_buf + probs_bytes + work_bytes) : nullptr;
-  CK(cudaMemcpyAsync(d_buf, h_buf.data(), total, cudaMemcpyHostToDevice, st), "upload launch buffer");
-  if (!cont)
-    CK(launch_init_bits(d_probs, count, maxR, max_words, d_init, static_cast<uint32_t>(seed),
+  const int8_t* d_init = B.init_bytes ? reinterpret_cast<const int8_t*>(d_buf + B.init_off) : nullptr;
+  int nl = 0;
+  if (!cont) {
+    CK(launch_init_bits(d_probs, count, B.maxR, B.max_words, d_init, static_cast<uint32_t>(seed),
                         static_cast<uint32_t>(seed >> 32), st),
        "init kernel");
-  auto timer = std::make_shared<LaunchTimer>();
-  CK(cudaEventCreate(&timer->start), "cudaEventCreate");
-  CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
+    ++nl;
+  }
   if (ref) {
     float *d_S = nullptr, *d_I = nullptr;
     size_t maxRn = 0;
     for (int k = 0; k < count; ++k)
-      maxRn = std::max(maxRn, static_cast<size_t>(replicas[k]) * insts[k]->n);
+      maxRn = std::max(maxRn, static_cast<size_t>(B.probs[k].R) * insts[k]->n);
     CK(cudaMallocAsync(reinterpret_cast<void**>(&d_S), maxRn * 4, st), "cudaMallocAsync S");
     CK(cudaMallocAsync(reinterpret_cast<void**>(&d_I), maxRn * 4, st), "cudaMallocAsync I");
-    CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
-    CK(launch_ref_anneal(probs.data(), d_probs, count, t_begin, sweeps, static_cast<uint32_t>(seed),
+    CK(record_event(timer->start, st), "cudaEventRecord");
+    CK(launch_ref_anneal(B.probs.data(), d_probs, count, t_begin, sweeps, static_cast<uint32_t>(seed),
                          static_cast<uint32_t>(seed >> 32), cont ? 1 : 0, d_S, d_I, d_err, st),
        "plain path");
-    CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
+    CK(record_event(timer->stop, st), "cudaEventRecord");
     CK(cudaFreeAsync(d_S, st), "cudaFreeAsync");
     CK(cudaFreeAsync(d_I, st), "cudaFreeAsync");
+    nl += 2 * (sweeps + 1) * count;
   } else {
-    CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
+    CK(record_event(timer->start, st), "cudaEventRecord");
     for (int g = 0; g < kGroups; ++g) {
-      if (work[g].empty()) continue;
+      if (B.work[g].empty()) continue;
       Launch L{};
       L.probs = d_probs;
-      L.work = d_work[g];
-      L.nwork = static_cast<int>(work[g].size());
+      L.work = reinterpret_cast<const WorkItem*>(d_buf + B.work_off[g]);
+      L.nwork = static_cast<int>(B.work[g].size());
       L.t_begin = t_begin;
       L.sweeps = sweeps;
       L.key_lo = static_cast<uint32_t>(seed);
       L.key_hi = static_cast<uint32_t>(seed >> 32);
       philox_round_keys(seed, L.round_keys);
       L.cont = cont ? 1 : 0;
-      L.stride_words_max = stride_max;
+      L.stride_words_max = B.stride_max;
       L.err = d_err;
       L.wait_ns = g_wait_ns.load();
       L.inject = g_inject.load();
-      L.next = reinterpret_cast<unsigned int*>(d_buf + counters_off);
+      L.next = reinterpret_cast<unsigned int*>(d_buf + B.counters_off);
       if (g == kMidGroup) {
         const int blocks = std::min(L.nwork, sweep_mid_max_blocks());
         if (blocks < 1) return fail(PIM_ERR_CUDA, "anneal: mid-N kernel cannot be resident");
@@ -1040,15 +1066,44 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
       } else {
         CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
       }
+      ++nl;
     }
     for (int k = 0; k < count; ++k) {
-      if (route[k] != kBig) continue;
-      const int rc = launch_big(probs[k], insts[k]->real, t_begin, sweeps, seed, cont, d_err, st);
+      if (B.route[k] != kBig) continue;
+      int n_big = 0;
+      const int rc = launch_big(B.probs[k], insts[k]->real, t_begin, sweeps, seed, cont, d_err,
+                                big_scratch, &n_big, st);
       if (rc != PIM_OK) return rc;
+      nl += n_big;
     }
-    CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
+    CK(record_event(timer->stop, st), "cudaEventRecord");
   }
-  CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
+  if (launches) *launches = nl;
+  return PIM_OK;
+}
+
+// Prerequisites of a run on stream st: staged inputs, float32 couplings for the plain path,
+// result buffers for the replica counts.
+int prepare_instances(pim_instance* const* insts, int count, const int* replicas, bool ref,
+                      cudaStream_t st) {
+  for (int k = 0; k < count; ++k) {
+    pim_instance* p = insts[k];
+    CK(cudaStreamWaitEvent(st, p->ready, 0), "cudaStreamWaitEvent");  // inputs staged
+    if (ref && !p->d_jf) {  // float32 couplings of the plain path, built on first use
+      void* d = nullptr;
+      CK(pool_alloc(&d, static_cast<size_t>(p->n) * p->n * sizeof(float), p->device, st),
+         "allocating float32 J");
+      p->d_jf = static_cast<float*>(d);
+      CK(launch_stage_f32(p->d_J8, p->n, p->d_jf, st), "stage float32 J");
+    }
+    const int rc = ensure_results(p, replicas[k], st);
+    if (rc != PIM_OK) return rc;
+  }
+  return PIM_OK;
+}
+
+int finish_run(pim_instance* const* insts, int count, const int* replicas,
+               const std::shared_ptr<LaunchTimer>& timer, cudaStream_t st) {
   for (int k = 0; k < count; ++k) {
     insts[k]->R = replicas[k];
     insts[k]->has_results = true;
@@ -1056,6 +1111,37 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
     CK(cudaEventRecord(insts[k]->done, st), "cudaEventRecord");
   }
   return PIM_OK;
+}
+
+int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
+                int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
+                const int8_t* init_spins, int flags, cudaStream_t st) {
+  int rc = check_batch(insts, count, replicas, t_begin, sweeps, targets, flags, true);
+  if (rc != PIM_OK) return rc;
+  if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
+  const bool cont = (flags & PIM_CONTINUE) != 0;
+  const bool ref = (flags & PIM_PATH_FP32REF) != 0;
+  if ((rc = prepare_instances(insts, count, replicas, ref, st)) != PIM_OK) return rc;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int* d_err = device_error_word(dev);
+  if (!d_err) return fail(PIM_ERR_NOMEM, "anneal: error word allocation failed");
+  BatchPlan B;
+  const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
+  if ((rc = build_plan(insts, count, replicas, ids, targets, flags, init_bytes, B)) != PIM_OK) return rc;
+  char* d_buf = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
+  std::vector<char> h_buf;
+  pack_plan(B, init_spins, h_buf);
+  CK(cudaMemcpyAsync(d_buf, h_buf.data(), B.total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  auto timer = std::make_shared<LaunchTimer>();
+  CK(cudaEventCreate(&timer->start), "cudaEventCreate");
+  CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
+  rc = enqueue_plan(B, d_buf, nullptr, insts, count, t_begin, sweeps, seed, cont, ref, timer.get(),
+                    d_err, nullptr, st);
+  if (rc != PIM_OK) return rc;
+  CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
+  return finish_run(insts, count, replicas, timer, st);
 }
 
 }  // namespace
@@ -1080,6 +1166,188 @@ PIM_API int pim_anneal_batch(pim_instance* const* insts, int count, const int* r
                              const double* targets, int flags, void* cuda_stream) {
   return anneal_impl(insts, count, replicas, t_begin, sweeps, seed, instance_ids, targets, nullptr,
                      flags, static_cast<cudaStream_t>(cuda_stream));
+}
+
+// ----------------------------------------------------------------------------------------
+// Batch plans: routing, descriptors and scratch built once; every run replays one CUDA graph
+// of the batch's launches (re-captured and updated in place when the run parameters change).
+struct pim_batch {
+  int device = 0;
+  std::vector<pim_instance*> insts;
+  std::vector<int> replicas;
+  std::vector<uint32_t> ids;
+  std::vector<double> targets;
+  int flags = 0;
+  BatchPlan plan;
+  std::vector<std::shared_ptr<Schedule>> scheds;  // schedules the descriptors point into
+  std::vector<char*> res;                         // result blocks the descriptors point into
+  char* d_buf = nullptr;
+  char* d_big = nullptr;
+  cudaStream_t cap = nullptr;  // private capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  std::string key;  // run parameters of the instantiated graph
+  int launches = 0;
+  std::shared_ptr<LaunchTimer> timer;
+};
+
+namespace {
+
+void batch_release(pim_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) {
+    cudaStreamSynchronize(b->cap);
+    cudaStreamDestroy(b->cap);
+  }
+  // cudaFree waits for the device, so no replay still reads these buffers
+  if (b->d_buf) cudaFree(b->d_buf);
+  if (b->d_big) cudaFree(b->d_big);
+  delete b;
+}
+
+}  // namespace
+
+PIM_API int pim_batch_create(pim_batch** out, pim_instance* const* insts, int count,
+                             const int* replicas, const uint32_t* instance_ids,
+                             const double* targets, int flags) {
+  if (!out) return fail(PIM_ERR_INVALID, "pim_batch_create: out is NULL");
+  *out = nullptr;
+  if (flags & (PIM_CONTINUE | PIM_PATH_FP32REF))
+    return fail(PIM_ERR_INVALID, "pim_batch_create: flags take only PIM_PATH_MID / PIM_PATH_BIG");
+  int rc = check_batch(insts, count, replicas, 0, 0, targets, flags, false);
+  if (rc != PIM_OK) return rc;
+  auto* b = new (std::nothrow) pim_batch();
+  if (!b) return fail(PIM_ERR_NOMEM, "pim_batch_create: host allocation failed");
+  cudaGetDevice(&b->device);
+  b->insts.assign(insts, insts + count);
+  b->replicas.assign(replicas, replicas + count);
+  b->flags = flags;
+  for (int k = 0; k < count; ++k) {
+    b->ids.push_back(instance_ids ? instance_ids[k] : static_cast<uint32_t>(k));
+    b->targets.push_back(targets ? targets[k] : NAN);
+  }
+  auto bail = [&](int code) {
+    batch_release(b);
+    return code;
+  };
+  auto bail_cuda = [&](cudaError_t e, const char* what) {
+    const int code = cuda_fail(e, what);
+    batch_release(b);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail_cuda(e, "cudaStreamCreate");
+  if ((rc = prepare_instances(b->insts.data(), count, b->replicas.data(), false, b->cap)) != PIM_OK)
+    return bail(rc);
+  if ((rc = build_plan(b->insts.data(), count, b->replicas.data(), b->ids.data(), b->targets.data(),
+                       flags, 0, b->plan)) != PIM_OK)
+    return bail(rc);
+  for (int k = 0; k < count; ++k) {
+    b->scheds.push_back(insts[k]->sched);
+    b->res.push_back(insts[k]->d_res);
+  }
+  if ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_buf), b->plan.total)) != cudaSuccess)
+    return bail_cuda(e, "allocating batch descriptors");
+  if (b->plan.big_scratch &&
+      (e = cudaMalloc(reinterpret_cast<void**>(&b->d_big), b->plan.big_scratch)) != cudaSuccess)
+    return bail_cuda(e, "allocating large-N scratch");
+  std::vector<char> h;
+  pack_plan(b->plan, nullptr, h);
+  if ((e = cudaMemcpyAsync(b->d_buf, h.data(), b->plan.total, cudaMemcpyHostToDevice, b->cap)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(b->cap)) != cudaSuccess)
+    return bail_cuda(e, "uploading batch descriptors");
+  b->timer = std::make_shared<LaunchTimer>();
+  if ((e = cudaEventCreate(&b->timer->start)) != cudaSuccess ||
+      (e = cudaEventCreate(&b->timer->stop)) != cudaSuccess)
+    return bail_cuda(e, "cudaEventCreate");
+  *out = b;
+  return PIM_OK;
+}
+
+PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, int run_flags,
+                          void* cuda_stream) {
+  if (!b) return fail(PIM_ERR_INVALID, "pim_batch_run: batch is NULL");
+  if (run_flags & ~PIM_CONTINUE) return fail(PIM_ERR_INVALID, "pim_batch_run: run flags take only PIM_CONTINUE");
+  const int count = static_cast<int>(b->insts.size());
+  int rc = check_batch(b->insts.data(), count, b->replicas.data(), t_begin, sweeps, b->targets.data(),
+                       b->flags | run_flags, true);
+  if (rc != PIM_OK) return rc;
+  for (int k = 0; k < count; ++k)
+    if (b->insts[k]->sched != b->scheds[k] || b->insts[k]->d_res != b->res[k])
+      return fail(PIM_ERR_STATE, "pim_batch_run: instance %d changed schedule or result buffers "
+                  "since the batch was created", k);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != b->device) return fail(PIM_ERR_INVALID, "pim_batch_run: batch lives on device %d", b->device);
+  int* d_err = device_error_word(dev);
+  if (!d_err) return fail(PIM_ERR_NOMEM, "anneal: error word allocation failed");
+  const bool cont = (run_flags & PIM_CONTINUE) != 0;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  for (int k = 0; k < count; ++k) CK(cudaStreamWaitEvent(st, b->insts[k]->ready, 0), "cudaStreamWaitEvent");
+  // run parameters that the captured launches bake in
+  std::string key;
+  const uint64_t wait_ns = g_wait_ns.load();
+  const int inject = g_inject.load();
+  auto put = [&](const void* v, size_t bytes) { key.append(static_cast<const char*>(v), bytes); };
+  put(&t_begin, sizeof t_begin);
+  put(&sweeps, sizeof sweeps);
+  put(&seed, sizeof seed);
+  put(&cont, sizeof cont);
+  put(&wait_ns, sizeof wait_ns);
+  put(&inject, sizeof inject);
+  if (b->use_graph && (key != b->key || !b->exec)) {
+    cudaGraph_t g = nullptr;
+    int nl = 0;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue_plan(b->plan, b->d_buf, b->d_big, b->insts.data(), count, t_begin, sweeps, seed,
+                        cont, false, b->timer.get(), d_err, &nl, b->cap);
+      e = cudaStreamEndCapture(b->cap, &g);
+    }
+    if (e != cudaSuccess || rc != PIM_OK || !g) {
+      // a launch of this batch cannot be captured: run it without a graph from now on
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      b->use_graph = false;
+    } else {
+      cudaGraphExecUpdateResultInfo info;
+      if (!b->exec || cudaGraphExecUpdate(b->exec, g, &info) != cudaSuccess) {
+        cudaGetLastError();
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        CK(cudaGraphInstantiate(&b->exec, g, 0), "cudaGraphInstantiate");
+      }
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->graph = g;
+      b->key = key;
+      b->launches = nl;
+    }
+  }
+  if (b->use_graph) {
+    CK(cudaGraphLaunch(b->exec, st), "cudaGraphLaunch");
+  } else {
+    rc = enqueue_plan(b->plan, b->d_buf, b->d_big, b->insts.data(), count, t_begin, sweeps, seed, cont,
+                      false, b->timer.get(), d_err, &b->launches, st);
+    if (rc != PIM_OK) return rc;
+  }
+  return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st);
+}
+
+PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_graph) {
+  if (!b) return fail(PIM_ERR_INVALID, "pim_batch_info: batch is NULL");
+  if (kernel_launches) *kernel_launches = b->launches;
+  if (uses_graph) *uses_graph = b->use_graph && b->exec ? 1 : 0;
+  return PIM_OK;
+}
+
+PIM_API void pim_batch_destroy(pim_batch* b) {
+  if (!b) return;
+  for (pim_instance* p : b->insts)
+    if (p && p->done) cudaEventSynchronize(p->done);
+  batch_release(b);
 }
 
 PIM_API int pim_sync(pim_instance* inst) {

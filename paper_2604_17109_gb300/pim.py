@@ -48,6 +48,11 @@ SIGNATURES = {
     "pim_activation_levels": (C.c_int, [C.c_float, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pim_thresholds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_int]),
+    "pim_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
+    "pim_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_batch_destroy": (None, [C.c_void_p]),
     "pim_anneal_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
                                      C.c_void_p, C.c_float, C.c_int, C.c_uint64, C.c_uint32,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -157,6 +162,34 @@ def pim_anneal_batch(insts, replicas, sweeps: int, seed: int, t_begin: int = 0,
     _check(lib().pim_anneal_batch(C.cast(handles, C.c_void_p), count, _ptr(reps), int(t_begin),
                                   int(sweeps), int(seed), _ptr(ids), _ptr(tg), int(flags),
                                   _stream(stream)), "pim_anneal_batch")
+
+
+def pim_batch_create(insts, replicas, instance_ids=None, targets=None, flags: int = 0) -> int:
+    count = len(insts)
+    handles = (C.c_void_p * count)(*insts)
+    reps = np.ascontiguousarray(np.broadcast_to(np.asarray(replicas, np.int32), (count,)))
+    ids = None if instance_ids is None else np.ascontiguousarray(instance_ids, dtype=np.uint32)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64)
+    out = C.c_void_p()
+    _check(lib().pim_batch_create(C.byref(out), C.cast(handles, C.c_void_p), count, _ptr(reps),
+                                  _ptr(ids), _ptr(tg), int(flags)), "pim_batch_create")
+    return out.value
+
+
+def pim_batch_run(batch: int, sweeps: int, seed: int, t_begin: int = 0, run_flags: int = 0,
+                  stream=None) -> None:
+    _check(lib().pim_batch_run(batch, int(t_begin), int(sweeps), int(seed), int(run_flags),
+                               _stream(stream)), "pim_batch_run")
+
+
+def pim_batch_info(batch: int) -> dict:
+    k, g = C.c_int(), C.c_int()
+    _check(lib().pim_batch_info(batch, C.byref(k), C.byref(g)), "pim_batch_info")
+    return {"kernel_launches": k.value, "uses_graph": bool(g.value)}
+
+
+def pim_batch_destroy(batch: int) -> None:
+    lib().pim_batch_destroy(batch)
 
 
 def pim_sync(inst: int) -> None:

@@ -1,0 +1,105 @@
+"""GPU tests of batch plans: an uneven batch routed once onto the fused, persistent mid-N
+and large-N kernels, replayed as a CUDA graph; every run of every instance is bit-exact
+against its own oracle run."""
+import numpy as np
+import pytest
+
+from workloads import eta_power, linear_beta, maxcut_er, sk_pm1
+
+from gpu_helpers import assert_same, collect, oracle_run, pim
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(sizes, reps, seed0=300):
+    insts = [(sk_pm1 if k % 2 else maxcut_er)(n, seed0 + k) for k, n in enumerate(sizes)]
+    return insts, list(reps)
+
+
+def _check_all(P, handles, insts, reps, ids, beta, eta, xi, seed, sweeps=None, targets=None):
+    for k, (hd, inst, R, q) in enumerate(zip(handles, insts, reps, ids)):
+        tg = None if targets is None else targets[k]
+        want = oracle_run(inst, beta, eta, xi, replicas=R, seed=seed, q=q, sweeps=sweeps, target=tg)
+        assert_same(collect(hd, inst.n), want, label=f"n={inst.n} R={R} seed={seed}")
+
+
+def test_batch_plan_graph_replays_match_oracle():
+    """One plan over fused and mid-N instances: runs with two seeds replay a captured graph
+    (updated in place for the new seed); a repeated seed reproduces its results."""
+    P = pim()
+    insts, reps = _batch([40, 300, 150, 700, 256, 1000, 64], [64, 130, 32, 100, 200, 64, 96])
+    ids = list(range(20, 20 + len(insts)))
+    targets = [-0.5 * i.n for i in insts]
+    T = 10
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.6)
+        b = P.pim_batch_create(handles, reps, instance_ids=ids, targets=targets)
+        for seed in (3, 8, 3):
+            P.pim_batch_run(b, T, seed)
+            info = P.pim_batch_info(b)
+            assert info["uses_graph"] and info["kernel_launches"] >= 3
+            assert P.pim_kernel_ms(handles[0]) > 0.0  # timer events are graph nodes
+            _check_all(P, handles, insts, reps, ids, beta, eta, 0.6, seed, targets=targets)
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+def test_batch_plan_resume_and_large_instance():
+    """A plan that also holds a large-N instance (n = 1100): a run split in two with
+    PIM_CONTINUE equals the uninterrupted oracle run."""
+    P = pim()
+    insts, reps = _batch([1100, 90, 520], [64, 40, 130], seed0=400)
+    ids = [5, 6, 7]
+    T = 12
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        b = P.pim_batch_create(handles, reps, instance_ids=ids)
+        P.pim_batch_run(b, 5, 11)
+        P.pim_batch_run(b, 7, 11, t_begin=5, run_flags=P.PIM_CONTINUE)
+        assert P.pim_batch_info(b)["kernel_launches"] >= 2
+        _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, 11)
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)
+
+
+def test_batch_plan_rejects_changed_instance():
+    P = pim()
+    insts, reps = _batch([50, 60], [32, 32])
+    beta = linear_beta(8)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        b = P.pim_batch_create(handles, reps)
+        P.pim_batch_run(b, 8, 1)
+        P.pim_sync(handles[0])
+        P.pim_set_schedule(handles[1], linear_beta(9), eta_power(linear_beta(9)), 0.5)
+        with pytest.raises(P.PimError) as e:
+            P.pim_batch_run(b, 8, 1)
+        assert e.value.code == P.PIM_ERR_STATE
+        with pytest.raises(P.PimError) as e:
+            P.pim_batch_run(b, 9, 1, t_begin=0, run_flags=4)
+        assert e.value.code == P.PIM_ERR_INVALID
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)

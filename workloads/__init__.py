@@ -14,4 +14,7 @@ from .generators import (  # noqa: F401
     random_spins,
     Instance,
     sk_batch,
+    uneven_batch,
+    uneven_sizes,
+    uneven_instance,
 )

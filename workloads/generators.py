@@ -25,6 +25,7 @@ _DOMAIN_MAXCUT = 0x4D43  # "MC"
 _DOMAIN_SK = 0x534B      # "SK"
 _DOMAIN_GAUSS = 0x4747   # "GG"
 _DOMAIN_SPINS = 0x5350   # "SP"
+_DOMAIN_UNEVEN = 0x5542  # "UB"
 
 
 def _rng(domain: int, n: int, seed: int) -> np.random.Generator:
@@ -103,3 +104,26 @@ def random_spins(n: int, replicas: int, seed: int) -> np.ndarray:
     """Initial spins in {-1,+1}, int8, shape (replicas, n)."""
     g = _rng(_DOMAIN_SPINS, n, seed)
     return np.where(g.random((replicas, n)) < 0.5, -1, 1).astype(np.int8)
+
+
+def uneven_sizes(count: int, seed: int = 0, n_min: int = 64, n_max: int = 1024,
+                 r_step: int = 32, r_max: int = 512):
+    """Sizes and replica counts of uneven_batch: n ~ U{n_min .. n_max}, replicas
+    ~ U{r_step, 2 r_step, .., r_max}."""
+    g = _rng(_DOMAIN_UNEVEN, count, seed)
+    sizes = g.integers(n_min, n_max + 1, size=count)
+    reps = r_step * g.integers(1, r_max // r_step + 1, size=count)
+    return [int(n) for n in sizes], [int(r) for r in reps]
+
+
+def uneven_instance(k: int, n: int) -> Instance:
+    """Instance k of an uneven batch: Max-Cut (ER 0.5) for even k, SK-1 for odd k, generator
+    seed k of its family."""
+    return (maxcut_er if k % 2 == 0 else sk_pm1)(n, k)
+
+
+def uneven_batch(count: int, seed: int = 0, **kw):
+    """A batch of `count` instances of uneven size for multi-instance scheduling (see
+    uneven_sizes and uneven_instance).  Returns (instances, replicas)."""
+    sizes, reps = uneven_sizes(count, seed, **kw)
+    return [uneven_instance(k, n) for k, n in enumerate(sizes)], reps
