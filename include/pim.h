@@ -199,6 +199,24 @@ int pim_batch_run(pim_batch* batch, int t_begin, int sweeps, uint64_t seed, int 
 int pim_batch_info(const pim_batch* batch, int* kernel_launches, int* uses_graph);
 void pim_batch_destroy(pim_batch* batch);
 
+/*
+ * pim_anneal_sequential -- conventional PIM with sequential updates (Eq. 3; Box 1, orange
+ * path), the baseline of the fully parallel loop, on integer couplings.
+ *   Sweep k (schedule entry k) updates spins i = 0 .. n-1 one after another, each from the
+ *   field of the current state, with beta_k, eta_k, the instance's xi (xi = 0 gives Eq. 3;
+ *   xi > 0 adds the inertia term of Eq. 4), noise kind and activation, and the draw of
+ *   counter (i>>3, r, k, instance_id): the same numbers the parallel loop draws in sweep k.
+ *   Energies are evaluated on the state at the start of every sweep and on the final
+ *   state; best / first-hit / final records are read with the usual getters.
+ *   replicas, t_begin, sweeps, seed, instance_id, init_spins, target_energy, cuda_stream
+ *   as pim_anneal; flags: 0 or PIM_CONTINUE.  One warp per replica.
+ * Errors: PIM_ERR_INVALID, PIM_ERR_STATE, PIM_ERR_UNSUPPORTED (real couplings, n too large
+ *         for shared memory), PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin, int sweeps,
+                          uint64_t seed, uint32_t instance_id, const int8_t* init_spins,
+                          double target_energy, int flags, void* cuda_stream);
+
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up). */
 int pim_sync(pim_instance* inst);

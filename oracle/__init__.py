@@ -20,6 +20,7 @@ from .pimi import (  # noqa: F401
     energy,
     anneal,
     anneal_sequential,
+    anneal_sequential_sweeps,
     n_trials,
     tts99,
     neighbour_triggered_flip_rate,

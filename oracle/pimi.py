@@ -331,6 +331,69 @@ def anneal_sequential(J, h, c: float, beta, eta, *, replicas: int, steps: int, s
     return s
 
 
+def anneal_sequential_sweeps(J, h, c: float, beta, eta, xi: float = 0.0, *, replicas: int,
+                             sweeps: int | None = None, seed: int = 0, q: int = 0,
+                             t_begin: int = 0, init: np.ndarray | None = None,
+                             target: float | None = None, noise: str = "uniform",
+                             act: str = "tanh", lut_levels: int = 4,
+                             prev: dict | None = None) -> dict:
+    """Conventional PIM with sequential updates (Eq. 3, Box 1 orange path), organised in
+    sweeps like the parallel loop: sweep k (schedule entry k) updates spins i = 0 .. n-1 one
+    after another, each from the field of the current state, with the draw of counter
+    (i>>3, r, k, q), beta_k, eta_k and (for xi > 0) the inertia term of Eq. 4 -- the same
+    numbers the parallel loop draws in sweep k.  Energies are evaluated on the state at the
+    start of every sweep and on the final state, with the bookkeeping of `anneal`; the
+    returned dict has the same keys."""
+    J = np.asarray(J)
+    h = np.asarray(h)
+    n = J.shape[0]
+    beta = np.asarray(beta, dtype=np.float32)
+    eta = np.asarray(eta, dtype=np.float32)
+    if sweeps is None:
+        sweeps = len(beta) - t_begin
+    rids = np.arange(replicas)
+    integer = _is_integer_valued(J) and _is_integer_valued(h)
+    z_table = gaussian_quantiles() if noise == "gauss" else uniform_levels()
+    if prev is not None:
+        s = prev["final_state"].copy()
+        best_E = prev["best_E"].astype(np.float64)
+        best_t = prev["best_t"].copy()
+        first_hit = prev["first_hit"].copy()
+        best_state = prev["best_state"].copy()
+    else:
+        s = (np.asarray(init, dtype=np.int8).copy() if init is not None
+             else init_spin_draw(seed, q, rids, n))
+        best_E = np.full(replicas, np.inf)
+        best_t = np.full(replicas, -1, np.int64)
+        first_hit = np.full(replicas, -1, np.int64)
+        best_state = s.copy()
+
+    def bookkeep(t):
+        nonlocal best_E
+        E = energy(J, h, s)
+        better = E < best_E
+        best_E = np.where(better, E, best_E)
+        best_t[better] = t
+        best_state[better] = s[better]
+        if target is not None:
+            hit = (E <= target) & (first_hit < 0)
+            first_hit[hit] = t
+        return E
+
+    for k in range(t_begin, t_begin + sweeps):
+        bookkeep(k)
+        b_k = np.float32(np.float64(beta[k]) * c)
+        for i in range(n):
+            Ii = field(J[i:i + 1], h[i:i + 1], s)[:, 0]      # Eq. 2 for spin i, current state
+            tau = activation(b_k, Ii, act, lut_levels)
+            d = noise_draw16(seed, q, rids, k, i)
+            s[:, i] = decide(tau, s[:, i], xi, eta[k], z_table[d >> 4])
+    E = bookkeep(t_begin + sweeps)
+    return dict(best_E=best_E.astype(np.int64) if integer else best_E, best_t=best_t,
+                first_hit=first_hit, final_E=E.astype(np.int64) if integer else E,
+                best_state=best_state, final_state=s)
+
+
 # ---------------------------------------------------------------------------------------
 # Trials to solution (supplementary CCTS section).
 # ---------------------------------------------------------------------------------------

@@ -60,6 +60,10 @@ cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st);
 int sweep_mid_max_blocks();
 int sweep_mid_max_npad();
 
+// Sequential (conventional PIM) kernel: one warp per replica, integer couplings.
+cudaError_t launch_sequential(const SeqLaunch& L, cudaStream_t st);
+int sequential_smem_bytes(int n);
+
 // Plain FP32 comparator path: per sweep one field GEMM and one update kernel.
 cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, int nprob,
                               int t_begin, int sweeps, uint32_t key_lo, uint32_t key_hi,

@@ -16,6 +16,7 @@ enum : int {
 struct Problem {
   const uint8_t* jimg;     // FP8 E4M3 couplings, npad x npad, 128B-swizzled K-major image
   const float* jf;         // float32 row-major n x n (plain path)
+  const int8_t* j8;        // int8 row-major n x n (sequential path)
   const int32_t* h;        // int32 bias or nullptr
   const uint32_t* thr;     // decision thresholds [steps][stride_words], entry I + imax
   const uint32_t* thr_diag;  // 16-bit thresholds by D = I + 256 s, [steps][1024], entry D+512
@@ -96,6 +97,16 @@ struct BigLaunch {
   int* err;
   uint64_t wait_ns;        // limit of every device-side wait (0 = 2 s)
   int inject;              // fault injection for tests: 1 = load nothing in the first sweep
+};
+
+// Launch of the sequential (conventional PIM) kernel: one instance, sweeps t_begin ..
+// t_begin+sweeps-1 of n single-spin updates each.
+struct SeqLaunch {
+  Problem P;
+  int t_begin;
+  int sweeps;
+  int cont;
+  uint32_t round_keys[20];
 };
 
 }  // namespace pim

@@ -919,6 +919,7 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
     Problem& P = B.probs[k];
     P.jimg = p->d_img;
     P.jf = p->d_jf;
+    P.j8 = p->d_J8;
     P.h = p->d_h;
     P.thr = p->sched->d_thr;
     P.thr_diag = p->sched->d_thr_diag;
@@ -1348,6 +1349,58 @@ PIM_API void pim_batch_destroy(pim_batch* b) {
   for (pim_instance* p : b->insts)
     if (p && p->done) cudaEventSynchronize(p->done);
   batch_release(b);
+}
+
+PIM_API int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin, int sweeps,
+                                  uint64_t seed, uint32_t instance_id, const int8_t* init_spins,
+                                  double target_energy, int flags, void* cuda_stream) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_anneal_sequential: instance is NULL");
+  if (flags & ~PIM_CONTINUE) return fail(PIM_ERR_INVALID, "pim_anneal_sequential: flags take only PIM_CONTINUE");
+  if (inst->real)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_anneal_sequential: integer couplings only");
+  // (the plain-path flag only skips the fused kernel's field-range check)
+  int rc = check_batch(&inst, 1, &replicas, t_begin, sweeps, &target_energy,
+                       flags | PIM_PATH_FP32REF, true);
+  if (rc != PIM_OK) return rc;
+  const bool cont = (flags & PIM_CONTINUE) != 0;
+  if (cont && init_spins) return fail(PIM_ERR_INVALID, "pim_anneal_sequential: CONTINUE takes no spins");
+  int smem_max = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (sequential_smem_bytes(inst->n) > smem_max)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_anneal_sequential: n = %d too large", inst->n);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if ((rc = prepare_instances(&inst, 1, &replicas, false, st)) != PIM_OK) return rc;
+  BatchPlan B;
+  const uint32_t id = instance_id;
+  const size_t init_bytes = init_spins ? static_cast<size_t>(replicas) * inst->n : 0;
+  if ((rc = build_plan(&inst, 1, &replicas, &id, &target_energy, PIM_PATH_FP32REF, init_bytes, B)) != PIM_OK)
+    return rc;
+  char* d_buf = nullptr;
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
+  std::vector<char> h_buf;
+  pack_plan(B, init_spins, h_buf);
+  CK(cudaMemcpyAsync(d_buf, h_buf.data(), B.total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  if (!cont) {
+    const int8_t* d_init = init_bytes ? reinterpret_cast<const int8_t*>(d_buf + B.init_off) : nullptr;
+    CK(launch_init_bits(reinterpret_cast<const Problem*>(d_buf), 1, replicas, inst->words, d_init,
+                        static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), st),
+       "init kernel");
+  }
+  auto timer = std::make_shared<LaunchTimer>();
+  CK(cudaEventCreate(&timer->start), "cudaEventCreate");
+  CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
+  SeqLaunch L{};
+  L.P = B.probs[0];
+  L.t_begin = t_begin;
+  L.sweeps = sweeps;
+  L.cont = cont ? 1 : 0;
+  philox_round_keys(seed, L.round_keys);
+  CK(cudaEventRecord(timer->start, st), "cudaEventRecord");
+  CK(launch_sequential(L, st), "sequential kernel");
+  CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
+  CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
+  return finish_run(&inst, 1, &replicas, timer, st);
 }
 
 PIM_API int pim_sync(pim_instance* inst) {

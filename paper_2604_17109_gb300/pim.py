@@ -48,6 +48,8 @@ SIGNATURES = {
     "pim_activation_levels": (C.c_int, [C.c_float, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pim_thresholds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                        C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "pim_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int]),
     "pim_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
@@ -162,6 +164,17 @@ def pim_anneal_batch(insts, replicas, sweeps: int, seed: int, t_begin: int = 0,
     _check(lib().pim_anneal_batch(C.cast(handles, C.c_void_p), count, _ptr(reps), int(t_begin),
                                   int(sweeps), int(seed), _ptr(ids), _ptr(tg), int(flags),
                                   _stream(stream)), "pim_anneal_batch")
+
+
+def pim_anneal_sequential(inst: int, replicas: int, sweeps: int, seed: int,
+                          instance_id: int = 0, t_begin: int = 0,
+                          init_spins: np.ndarray | None = None, target=None, flags: int = 0,
+                          stream=None) -> None:
+    init = None if init_spins is None else np.ascontiguousarray(init_spins, dtype=np.int8)
+    tgt = math.nan if target is None else float(target)
+    _check(lib().pim_anneal_sequential(inst, int(replicas), int(t_begin), int(sweeps), int(seed),
+                                       int(instance_id), _ptr(init), tgt, int(flags),
+                                       _stream(stream)), "pim_anneal_sequential")
 
 
 def pim_batch_create(insts, replicas, instance_ids=None, targets=None, flags: int = 0) -> int:

@@ -339,3 +339,55 @@ def test_round_bf16_examples():
     assert np.array_equal(pimi.round_bf16(r), r)
     f32 = r.astype(np.float32).view(np.uint32)
     assert np.all(f32 & 0xFFFF == 0)
+
+
+# ------------------------------------------------ sequential sweeps (conventional PIM, Eq. 3)
+def test_sequential_sweeps_sample_boltzmann_chi2():
+    """Sequential sweeps with xi = 0 and uniform noise are a heat-bath sampler: final
+    states of 4000 chains after 40 sweeps follow exp(-beta H)/Z (chi^2)."""
+    J = np.array([[0, 1, -2, 1], [1, 0, 1, -1], [-2, 1, 0, 2], [1, -1, 2, 0]], np.int8)
+    h = np.array([1, 0, -1, 0], np.int32)
+    beta = 0.4
+    T = 40
+    out = oracle.anneal_sequential_sweeps(J, h, 1.0, np.full(T, beta, np.float32),
+                                          np.ones(T, np.float32), 0.0, replicas=4000, seed=5)
+    s = out["final_state"]
+    idx = ((s > 0).astype(np.int64) << np.arange(4)[None, :]).sum(axis=1)
+    hist = np.bincount(idx, minlength=16)
+    _, p = oracle.boltzmann(J, h, beta)
+    expct = p * len(idx)
+    stat = ((hist - expct) ** 2 / expct).sum()
+    assert chi2.sf(stat, 15) > 1e-3
+
+
+@pytest.mark.parametrize("n,zero_j", [(1, False), (10, True)])
+def test_sequential_equals_parallel_without_interaction(n, zero_j):
+    """With a single spin, or with J = 0, the order of the updates cannot matter: sequential
+    sweeps equal the parallel loop record for record (same draws per sweep)."""
+    rng = np.random.default_rng(n)
+    J = np.zeros((n, n), np.int8)
+    h = rng.integers(-3, 4, n).astype(np.int32)
+    T = 30
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    for xi in (0.0, 0.6):
+        seq = oracle.anneal_sequential_sweeps(J, h, 0.5, beta, eta, xi, replicas=25, seed=7, q=2,
+                                              target=-2.0, noise="gauss")
+        par = oracle.anneal(J, h, 0.5, beta, eta, xi, replicas=25, seed=7, q=2, target=-2.0)
+        for k in ("best_E", "best_t", "first_hit", "final_E", "best_state", "final_state"):
+            assert np.array_equal(seq[k], par[k]), (k, xi)
+
+
+def test_sequential_update_sees_the_new_spin():
+    """Two ferromagnetically coupled spins starting anti-aligned, no noise: the parallel
+    update swaps them (each follows the other's old value), the sequential update aligns
+    them (spin 1 already sees the new spin 0)."""
+    J = np.array([[0, 3], [3, 0]], np.int8)
+    h = np.zeros(2, np.int32)
+    beta = np.full(1, 2.0, np.float32)
+    eta = np.zeros(1, np.float32)
+    init = np.array([[1, -1]], np.int8)
+    seq = oracle.anneal_sequential_sweeps(J, h, 1.0, beta, eta, 0.0, replicas=1, init=init)
+    par = oracle.anneal(J, h, 1.0, beta, eta, 0.0, replicas=1, init=init)
+    assert seq["final_state"].tolist() == [[-1, -1]]
+    assert par["final_state"].tolist() == [[-1, 1]]
