@@ -217,6 +217,81 @@ int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin, int swe
                           uint64_t seed, uint32_t instance_id, const int8_t* init_spins,
                           double target_energy, int flags, void* cuda_stream);
 
+/*
+ * MIMO detection (supplementary sections on MIMO detection and on the Delta-Ising MIMO
+ * formulation).  Complex arrays are interleaved (re, im) doubles; H is row-major nr x nt.
+ *
+ * pim_mimo_formulate -- FP64 host formulation of one uplink detection problem
+ * y = H x + n as the Ising instance of the residual around the hard-sliced MMSE estimate:
+ *   x_mmse = slice((H^H H + mmse_reg I)^-1 H^H y)              (MMSE baseline section)
+ *   real equivalent Hr = [[Re H, -Im H], [Im H, Re H]], yr = [Re y; Im y]
+ *   d = u - x_mmse = T s with T = [I, I] for 4-/16-QAM (corrections {-2, 0, 2}) and
+ *   T = [2I, I, I] for 64-QAM; n = (2 or 3) * 2 nt spins, spin k = block b, component m
+ *   J = -2 zeroDiag(T^T Hr^T Hr T),  h = 2 T^T Hr^T (yr - Hr x_mmse)
+ * so that the library energy -1/2 s^T J s - h^T s equals ||y - H(x_mmse + T s)||^2 up to a
+ * constant (the paper's form -h^T s - s^T J_p s with J = 2 J_p).
+ *   J: caller-allocated n x n, h: n, x_mmse: nt complex (slicing onto the square-QAM
+ *   levels -L+1, .., L-1).  qam in {4, 16, 64}; mmse_reg > 0 (the paper prints
+ *   1 / (Es/N0)).
+ * pim_mimo_reconstruct -- x_hat = slice(x_mmse + T s) for spins s (n int8 +-1), nt complex
+ *   out (reconstruction section).
+ * Errors: PIM_ERR_INVALID (sizes, constellation, non-positive-definite MMSE system).
+ */
+int pim_mimo_formulate(int nt, int nr, int qam, const double* H, const double* y,
+                       double mmse_reg, double* J, double* h, double* x_mmse);
+int pim_mimo_reconstruct(int nt, int qam, const double* x_mmse, const int8_t* spins,
+                         double* x_hat);
+
+/*
+ * MIMO-detection server -- the real-time request loop of the supplementary "Kernel
+ * execution" and "Host-side task scheduling" subsections on one GPU: continuous batching
+ * with memory admission.  A dispatcher thread admits queued requests while one of
+ * `max_inflight` stream slots is free and the device bytes of the admitted requests stay
+ * within `mem_budget`, formulates each (pim_mimo_formulate), stages it as a BF16 instance,
+ * and launches every request admitted at that moment as one batch (at most `max_batch`),
+ * so requests that arrive while others run are admitted as slots and memory free up and
+ * their work overlaps on the device.  A completion thread selects each request's replica
+ * of lowest reported best energy (ties: lowest index), evaluates that state's FP64 energy,
+ * reconstructs x_hat and records the latency (submit -> result available).  Every request uses the server's schedule (beta, eta, xi,
+ * scale_c, Gaussian noise, tanh), `replicas`, `sweeps`, `seed`, and its request_id as the
+ * instance counter word, so its result does not depend on what it was batched with.
+ */
+typedef struct pim_mimo_server_config {
+  int nt, nr, qam;        /* system size and constellation (4, 16, 64) */
+  int replicas, sweeps;   /* trials and PIMI steps per request */
+  const float* beta;      /* [sweeps], copied at creation */
+  const float* eta;       /* [sweeps], copied at creation */
+  float xi;               /* inertia */
+  double scale_c;         /* coupling scale applied to the accumulated field */
+  uint64_t seed;          /* Philox key of every request */
+  int max_batch;          /* requests per launch, >= 1 */
+  int max_inflight;       /* launches in flight (streams), >= 1 */
+  size_t mem_budget;      /* device bytes admitted requests may hold (raised to one request) */
+} pim_mimo_server_config;
+typedef struct pim_mimo_server pim_mimo_server;
+int pim_mimo_server_create(pim_mimo_server** out, const pim_mimo_server_config* cfg);
+/* Copies H (nr x nt complex) and y (nr complex); returns a ticket immediately. */
+int pim_mimo_server_submit(pim_mimo_server* server, const double* H, const double* y,
+                           double mmse_reg, uint32_t request_id, uint64_t* ticket);
+/* PIM_PENDING, PIM_OK or the request's error. */
+int pim_mimo_server_poll(pim_mimo_server* server, uint64_t ticket);
+/* Waits up to timeout_s; on PIM_OK writes x_hat (nt complex), the FP64 energy of the chosen
+   replica and the latency in microseconds, and forgets the ticket; PIM_PENDING on timeout. */
+int pim_mimo_server_result(pim_mimo_server* server, uint64_t ticket, double timeout_s,
+                           double* x_hat, double* best_energy, double* latency_us);
+/* Completed requests, latency percentiles (us), mean requests per launch, peak admitted
+   bytes; returns the first error a batch met (PIM_OK if none). */
+int pim_mimo_server_stats(pim_mimo_server* server, uint64_t* completed, double* p50_us,
+                          double* p99_us, double* mean_batch, size_t* peak_bytes);
+/* Native load driver: submits request k (H_all + k nr nt, y_all + k nr complex) at
+   arrival_us[k] microseconds after the call starts, waits for all, and writes each
+   request's x_hat (nt complex), energy and latency (each output may be NULL). */
+int pim_mimo_server_replay(pim_mimo_server* server, int count, const double* H_all,
+                           const double* y_all, const double* reg_all,
+                           const double* arrival_us, double* x_hat_all,
+                           double* best_energy_all, double* latency_us_all);
+void pim_mimo_server_destroy(pim_mimo_server* server);
+
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up). */
 int pim_sync(pim_instance* inst);

@@ -50,6 +50,21 @@ SIGNATURES = {
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                         C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
+    "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_mimo_reconstruct": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_mimo_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p]),
+    "pim_mimo_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                         C.c_uint32, C.POINTER(C.c_uint64)]),
+    "pim_mimo_server_poll": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "pim_mimo_server_result": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double, C.c_void_p,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pim_mimo_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_size_t)]),
+    "pim_mimo_server_replay": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_mimo_server_destroy": (None, [C.c_void_p]),
     "pim_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int]),
     "pim_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
@@ -175,6 +190,108 @@ def pim_anneal_sequential(inst: int, replicas: int, sweeps: int, seed: int,
     _check(lib().pim_anneal_sequential(inst, int(replicas), int(t_begin), int(sweeps), int(seed),
                                        int(instance_id), _ptr(init), tgt, int(flags),
                                        _stream(stream)), "pim_anneal_sequential")
+
+
+def _complex_ri(a) -> np.ndarray:
+    """complex array -> contiguous interleaved (re, im) float64."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.view(np.float64)
+
+
+def spins_per_component(qam: int) -> int:
+    return {4: 2, 16: 2, 64: 3}[qam]
+
+
+def pim_mimo_formulate(H, y, qam: int, mmse_reg: float):
+    """(J n x n, h n, x_mmse nt complex) of the DI-MIMO instance of (H, y)."""
+    H = np.asarray(H)
+    nr, nt = H.shape
+    n = spins_per_component(qam) * 2 * nt
+    J = np.empty((n, n), np.float64)
+    h = np.empty(n, np.float64)
+    xm = np.empty(2 * nt, np.float64)
+    Hri, yri = _complex_ri(H), _complex_ri(y)
+    _check(lib().pim_mimo_formulate(nt, nr, int(qam), _ptr(Hri), _ptr(yri), float(mmse_reg),
+                                    _ptr(J), _ptr(h), _ptr(xm)), "pim_mimo_formulate")
+    return J, h, xm.view(np.complex128)
+
+
+def pim_mimo_reconstruct(x_mmse, spins, qam: int) -> np.ndarray:
+    xm = _complex_ri(x_mmse)
+    nt = xm.size // 2
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    out = np.empty(2 * nt, np.float64)
+    _check(lib().pim_mimo_reconstruct(nt, int(qam), _ptr(xm), _ptr(s), _ptr(out)),
+           "pim_mimo_reconstruct")
+    return out.view(np.complex128)
+
+
+class MimoServerConfig(C.Structure):
+    _fields_ = [("nt", C.c_int), ("nr", C.c_int), ("qam", C.c_int), ("replicas", C.c_int),
+                ("sweeps", C.c_int), ("beta", C.c_void_p), ("eta", C.c_void_p), ("xi", C.c_float),
+                ("scale_c", C.c_double), ("seed", C.c_uint64), ("max_batch", C.c_int),
+                ("max_inflight", C.c_int), ("mem_budget", C.c_size_t)]
+
+
+def pim_mimo_server_create(nt, nr, qam, replicas, beta, eta, xi, scale_c, seed=0, max_batch=64,
+                           max_inflight=4, mem_budget=1 << 30) -> int:
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    eta = np.ascontiguousarray(eta, dtype=np.float32)
+    cfg = MimoServerConfig(int(nt), int(nr), int(qam), int(replicas), int(beta.size),
+                           beta.ctypes.data, eta.ctypes.data, float(xi), float(scale_c), int(seed),
+                           int(max_batch), int(max_inflight), int(mem_budget))
+    out = C.c_void_p()
+    _check(lib().pim_mimo_server_create(C.byref(out), C.byref(cfg)), "pim_mimo_server_create")
+    return out.value
+
+
+def pim_mimo_server_submit(server: int, H, y, mmse_reg: float, request_id: int) -> int:
+    Hri, yri = _complex_ri(H), _complex_ri(y)
+    t = C.c_uint64()
+    _check(lib().pim_mimo_server_submit(server, _ptr(Hri), _ptr(yri), float(mmse_reg),
+                                        int(request_id), C.byref(t)), "pim_mimo_server_submit")
+    return t.value
+
+
+def pim_mimo_server_poll(server: int, ticket: int) -> int:
+    return _check(lib().pim_mimo_server_poll(server, int(ticket)), "pim_mimo_server_poll")
+
+
+def pim_mimo_server_result(server: int, ticket: int, nt: int, timeout_s: float = 60.0):
+    """(x_hat nt complex, FP64 energy, latency us), or None on timeout."""
+    x = np.empty(2 * nt, np.float64)
+    e, lat = C.c_double(), C.c_double()
+    rc = _check(lib().pim_mimo_server_result(server, int(ticket), float(timeout_s), _ptr(x),
+                                             C.byref(e), C.byref(lat)), "pim_mimo_server_result")
+    if rc == PIM_PENDING:
+        return None
+    return x.view(np.complex128), e.value, lat.value
+
+
+def pim_mimo_server_stats(server: int) -> dict:
+    c, p50, p99, mb, pk = C.c_uint64(), C.c_double(), C.c_double(), C.c_double(), C.c_size_t()
+    rc = lib().pim_mimo_server_stats(server, C.byref(c), C.byref(p50), C.byref(p99), C.byref(mb),
+                                     C.byref(pk))
+    return {"completed": c.value, "p50_us": p50.value, "p99_us": p99.value,
+            "mean_batch": mb.value, "peak_bytes": pk.value, "status": rc}
+
+
+def pim_mimo_server_replay(server: int, H_all, y_all, reg_all, arrival_us, nt: int):
+    """Native load driver; returns (x_hat (count, nt) complex, energies, latencies_us)."""
+    Hri, yri = _complex_ri(H_all), _complex_ri(y_all)
+    reg = np.ascontiguousarray(reg_all, dtype=np.float64)
+    arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+    count = reg.size
+    x = np.empty((count, 2 * nt), np.float64)
+    e = np.empty(count, np.float64)
+    lat = np.empty(count, np.float64)
+    _check(lib().pim_mimo_server_replay(server, count, _ptr(Hri), _ptr(yri), _ptr(reg), _ptr(arr),
+                                        _ptr(x), _ptr(e), _ptr(lat)), "pim_mimo_server_replay")
+    return x.view(np.complex128), e, lat
+
+
+def pim_mimo_server_destroy(server: int) -> None:
+    lib().pim_mimo_server_destroy(server)
 
 
 def pim_batch_create(insts, replicas, instance_ids=None, targets=None, flags: int = 0) -> int:

@@ -18,3 +18,14 @@ from .generators import (  # noqa: F401
     uneven_sizes,
     uneven_instance,
 )
+from .mimo import (  # noqa: F401
+    MimoProblem,
+    mimo_problem,
+    pam_gray,
+    qam_bits_per_symbol,
+    symbols_from_bits,
+    bits_from_symbols,
+    mimo_schedule,
+    mimo_scale,
+    MIMO_XI,
+)
