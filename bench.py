@@ -60,6 +60,8 @@ WORKLOADS = {
     "uneven4096": Workload("uneven4096", "uneven", 1024, 4096, 512, 1000, 0.5),
     # MIMO serving: n = 4 nt spins (16-QAM), count = requests, sweeps per request (16x16: the
     # paper's 64; 64x64: 256, proposed), Poisson arrivals (rate in run_mimo)
+    # fixed-point study: Max-Cut N = 100 (config 1) over 20 instances, float32 vs ap_fixed
+    "fixed100": Workload("fixed100", "fixed", 100, 20, 64, 1000, 0.7),
     "mimo16": Workload("mimo16", "mimo", 64, 2000, 32, 64, 1.0),
     "mimo64": Workload("mimo64", "mimo", 256, 400, 32, 256, 1.0),
 }
@@ -190,6 +192,8 @@ def _oracle_sample(w: Workload, budget_s: float, max_instances: int, replicas: i
     if w.kind == "uneven":
         from workloads import uneven_instance, uneven_sizes
         sizes = uneven_sizes(w.count, seed=0)[0]
+    if w.kind == "fixed":
+        from workloads import maxcut_er
     if w.kind == "mimo":
         from oracle import mimo as om
         from workloads import Instance, MIMO_XI, mimo_problem, mimo_scale, mimo_schedule
@@ -202,7 +206,8 @@ def _oracle_sample(w: Workload, budget_s: float, max_instances: int, replicas: i
     while k < max_instances:
         # instance generation is not oracle work: outside the clock
         inst = (uneven_instance(k, sizes[k]) if w.kind == "uneven"
-                else mimo_inst if w.kind == "mimo" else _instance(w, k))
+                else mimo_inst if w.kind == "mimo"
+                else maxcut_er(w.n, k) if w.kind == "fixed" else _instance(w, k))
         t0 = time.perf_counter()
         oracle.anneal(inst.J, inst.h, inst.c, beta, eta, w.xi, replicas=replicas, seed=0, q=k,
                       sweeps=min(sweeps, len(beta)))
@@ -305,6 +310,80 @@ def run_reference(args, w: Workload):
 
 
 # ------------------------------------------------------------------------- our arm
+def run_fixed(args, w: Workload):
+    """Success probability vs the decision arithmetic (N4): float32, ap_fixed<W, 2> for
+    several W with tanh, and <4, 2> with L-level LUTs, on Max-Cut N = 100 (ER 0.5), 64
+    replicas x 1000 sweeps, 20 instances, the same kernels and draws.  Success of a replica:
+    best energy <= 0.999 x the best energy any configuration found for its instance.
+    value: spin updates/s of the <4, 2> batch."""
+    world, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2604_17109_gb300 import build as pkg_build
+    from paper_2604_17109_gb300 import pim
+    from workloads import maxcut_er
+
+    pkg_build.build()
+    insts = [maxcut_er(w.n, k) for k in range(w.count)]
+    beta, eta = _schedule(w.sweeps)
+    R, T = w.replicas, w.sweeps
+    configs = [("float32", None, "tanh", 0)] + \
+              [(f"fixed<{W},2>", (W, 2), "tanh", 0) for W in (3, 4, 5, 6, 8, 12, 16)] + \
+              [(f"fixed<4,2> lut{L}", (4, 2), "lut", L) for L in (4, 8, 16)]
+    handles = [pim.pim_create(i.J, None, i.c) for i in insts]
+    best = {}
+    timing = {}
+    stream = torch.cuda.Stream()
+    with ClockSampler(local) as clocks:
+        for name, fmt, act, L in configs:
+            for hd in handles:
+                if fmt is None:
+                    pim.pim_set_schedule(hd, beta, eta, w.xi, act=act, lut_levels=max(L, 2))
+                else:
+                    pim.pim_set_schedule_fixed(hd, beta, eta, w.xi, fmt[0], fmt[1], act=act,
+                                               lut_levels=max(L, 2))
+            for _ in range(max(1, args.warmup)):
+                pim.pim_anneal_batch(handles, R, T, seed=0, stream=stream)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pim.pim_anneal_batch(handles, R, T, seed=0, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            timing[name] = statistics.mean(ms)
+            best[name] = np.stack([pim.pim_energies(hd)["best_E"] for hd in handles])
+    for hd in handles:
+        pim.pim_destroy(hd)
+    ref = np.min(np.stack([b.min(axis=1) for b in best.values()]), axis=0)  # per instance
+    study = {name: {"p_success": float(np.mean(b <= 0.999 * ref[:, None])),
+                    "mean_best_energy": float(b.mean()), "ms_per_batch": timing[name]}
+             for name, b in best.items()}
+    if rank != 0:
+        return 0
+    updates = w.count * w.n * R * T
+    ms = timing["fixed<4,2>"]
+    line = {
+        "metric": METRIC, "value": updates / (ms * 1e-3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp8e4m3/i32 (ap_fixed<4,2> decisions)",
+        "data": "synthetic",
+        "config": {"workload": f"maxcut{w.n}_{w.count}inst_{R}rep_{T}sweeps_fixed_point_study",
+                   "schedule": "linear beta 0.1->3, eta=sqrt(beta/5), xi=0.7",
+                   "success": "best energy <= 0.999 x best found over all configurations"},
+        "study": study,
+        "cpu_baseline": cpu_baseline(w),
+        "e2e": None,
+        "gpu_launches": 2 * args.steps * len(configs),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_mimo(args, w: Workload):
     """MIMO detection serving (16-QAM, Rayleigh, Eb/N0 ~ U[10, 25] dB per request).
     value: device-resident throughput of all requests as one batch plan (instances staged
@@ -631,6 +710,8 @@ def main():
         return run_reference(args, w)
     if w.kind == "mimo":
         return run_mimo(args, w)
+    if w.kind == "fixed":
+        return run_fixed(args, w)
     return run_ours(args, w)
 
 

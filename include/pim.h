@@ -125,6 +125,24 @@ int pim_set_schedule(pim_instance* inst, int steps, const float* beta, const flo
                      float xi, int noise_kind, int act_kind, int lut_levels);
 
 /*
+ * pim_set_schedule_fixed -- as pim_set_schedule, with the decision of Eq. 4 evaluated in
+ * the fixed-point datapath of the supplementary quantization section:
+ * ap_fixed<total_bits, int_bits, AP_TRN_ZERO, AP_SAT> (int_bits include the sign; each
+ * value truncated toward zero to a multiple of 2^-(total_bits - int_bits), then saturated).
+ * Order of the datapath (every intermediate quantized, Q = that format):
+ *   u = Q(c I)  (normalisation after the multiply-accumulate),  x = Q(beta_t u),
+ *   tau = Q(tanh(x)) or Q(L-level staircase(x)),  a = Q(tau + s Q(xi)),
+ *   n = Q(Q(eta_t) Q(z)),  s' = +1 iff Q(a + n) >= 0.
+ * The paper uses <4,2> for Max-Cut / SK and <16,4> for MIMO.  The decision stays monotone
+ * in the noise key, so the same kernels run it from exact key thresholds, built on the host.
+ *   total_bits in [2, 32], int_bits in [1, total_bits]; integer couplings only.
+ * Errors: PIM_ERR_INVALID, PIM_ERR_UNSUPPORTED (real couplings), PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* beta, const float* eta,
+                           float xi, int noise_kind, int act_kind, int lut_levels, int total_bits,
+                           int int_bits);
+
+/*
  * pim_anneal -- run sweeps t_begin .. t_begin+sweeps-1 of Eq. 4 on `replicas` replicas.
  * Box 1 (PIMI loop) and the supplementary algorithm "Fully unrolled PIMI update".
  *   replicas      R >= 1 independent trials.

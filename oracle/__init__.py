@@ -16,6 +16,8 @@ from .pimi import (  # noqa: F401
     decide,
     delta,
     round_bf16,
+    quantize,
+    decide_fixed,
     field,
     energy,
     anneal,

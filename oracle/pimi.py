@@ -165,6 +165,37 @@ def decide(tau: np.ndarray, s: np.ndarray, xi: float, eta_t: float, z: np.ndarra
     return np.where(delta(tau, s, xi, eta_t, z) >= np.float32(0.0), 1, -1).astype(np.int8)
 
 
+# ---------------------------------------------------------------------------------------
+# Fixed-point emulation of the FPGA datapath (supplementary quantization section).
+# ---------------------------------------------------------------------------------------
+def quantize(v, total_bits: int, int_bits: int) -> np.ndarray:
+    """ap_fixed<W, I, AP_TRN_ZERO, AP_SAT>: signed, I integer bits (sign included), W - I
+    fractional bits; truncation toward zero, then saturation to [-2^(I-1), 2^(I-1) - 2^-F]."""
+    F = total_bits - int_bits
+    step = 2.0 ** -F
+    q = np.trunc(np.asarray(v, dtype=np.float64) / step) * step
+    return np.clip(q, -(2.0 ** (int_bits - 1)), 2.0 ** (int_bits - 1) - step)
+
+
+def decide_fixed(I, s, c: float, beta_t, xi: float, eta_t, z, total_bits: int, int_bits: int,
+                 act: str = "tanh", lut_levels: int = 4) -> np.ndarray:
+    """Eq. 4 with every intermediate in ap_fixed<W, I> (the reading of the datapath order):
+    u = Q(c I) (normalisation after the multiply-accumulate), x = Q(beta_t u),
+    tau = Q(act(x)), a = Q(tau + s Q(xi)), n = Q(Q(eta_t) Q(z)), delta = Q(a + n),
+    s' = +1 iff delta >= 0.  Products and sums of quantized values are formed exactly."""
+    Q = lambda v: quantize(v, total_bits, int_bits)  # noqa: E731
+    u = Q(float(c) * np.asarray(I, dtype=np.float64))
+    x = Q(float(np.float32(beta_t)) * u)
+    if act == "tanh":
+        tau = Q(np.tanh(x))
+    else:
+        tau = Q(np.vectorize(lambda v: lut_tanh(float(v), lut_levels))(x))
+    a = Q(tau + np.where(np.asarray(s) > 0, 1.0, -1.0) * Q(float(np.float32(xi))))
+    n = Q(Q(float(np.float32(eta_t))) * Q(np.asarray(z, dtype=np.float64)))
+    d = Q(a + n)
+    return np.where(d >= 0.0, 1, -1).astype(np.int8)
+
+
 def round_bf16(x) -> np.ndarray:
     """Round float64 values to the nearest bfloat16 value (8 significant bits, ties to even),
     returned as float64: x = m 2^e with 1/2 <= |m| < 1, kept as rint(256 m) 2^(e-8)."""
@@ -215,14 +246,15 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
            init: np.ndarray | None = None, target: float | None = None,
            noise: str = "gauss", act: str = "tanh", lut_levels: int = 4,
            replica_ids=None, record: bool = False, record_states: bool = False,
-           prev: dict | None = None) -> dict:
+           prev: dict | None = None, fixed: tuple | None = None) -> dict:
     """Run fully parallel PIMI sweeps t = t_begin .. t_begin+sweeps-1.
 
     Each sweep: fields I(t) = J s(t) + h (Eq. 2); energy H(s(t)) (Eq. 1) with best and
     first-hit bookkeeping; then every spin decides s_i(t+1) from Eq. 4 with the draws
     described in the module docstring.  After the loop H(s(T)) is evaluated once more.
     Returns best_E, best_t, first_hit (-1 if never), final_E, best_state, final_state
-    (and 'energies', shape (sweeps+1, R), when record=True)."""
+    (and 'energies', shape (sweeps+1, R), when record=True).  fixed = (W, I) replaces the
+    float32 decision by the ap_fixed<W, I> datapath of decide_fixed."""
     J = np.asarray(J)
     h = np.asarray(h)
     n = J.shape[0]
@@ -271,11 +303,15 @@ def anneal(J, h, c: float, beta, eta, xi: float, *, replicas: int | None = None,
         I = field(J, h, s)                                  # Eq. 2, all i and r
         E = energy(J, h, s)                                 # Eq. 1 of s(t)
         bookkeep(E, t)
-        b_t = np.float32(np.float64(beta[t]) * c)
-        tau = activation(b_t, I, act, lut_levels)
         d = noise_draw16(seed, q, replica_ids[:, None], t, ivec[None, :])
         z = z_table[d >> 4]
-        s = decide(tau, s, xi, eta[t], z)                   # Eq. 4, synchronous
+        if fixed is not None:                               # fixed-point datapath
+            s = decide_fixed(I, s, c, beta[t], xi, eta[t], z, fixed[0], fixed[1], act,
+                             lut_levels)
+        else:
+            b_t = np.float32(np.float64(beta[t]) * c)
+            tau = activation(b_t, I, act, lut_levels)
+            s = decide(tau, s, xi, eta[t], z)               # Eq. 4, synchronous
         if record_states:
             states.append(s.copy())
     E = energy(J, h, s)

@@ -67,4 +67,53 @@ float scaled_beta(float beta, double c) {
   return static_cast<float>(static_cast<double>(beta) * c);
 }
 
+namespace {
+
+// ap_fixed<W, I, AP_TRN_ZERO, AP_SAT> value of v: drop the bits below 2^-(W-I) toward
+// zero, then clamp to the signed range.  All inputs here are small multiples of powers of
+// two or doubles whose truncation is exact in double arithmetic.
+struct FixedFormat {
+  double step, lo, hi;
+  FixedFormat(int total_bits, int int_bits)
+      : step(std::ldexp(1.0, int_bits - total_bits)),
+        lo(-std::ldexp(1.0, int_bits - 1)),
+        hi(std::ldexp(1.0, int_bits - 1) - std::ldexp(1.0, int_bits - total_bits)) {}
+  double operator()(double v) const {
+    const double q = std::trunc(v / step) * step;
+    return q < lo ? lo : (q > hi ? hi : q);
+  }
+};
+
+}  // namespace
+
+void fixed_thresholds(double c, float beta_t, float eta_t, float xi, int act, int lut_levels,
+                      int total_bits, int int_bits, const float* z, int imax, uint32_t* word) {
+  const FixedFormat Q(total_bits, int_bits);
+  const double qxi = Q(static_cast<double>(xi));
+  const double qeta = Q(static_cast<double>(eta_t));
+  // quantized noise term per key, non-decreasing in the key
+  static thread_local double noise[kNoiseLevels];
+  for (int m = 0; m < kNoiseLevels; ++m) noise[m] = Q(qeta * Q(static_cast<double>(z[m])));
+  for (int I = -imax; I <= imax; ++I) {
+    const double u = Q(c * static_cast<double>(I));          // scaling after the MAC
+    const double x = Q(static_cast<double>(beta_t) * u);     // inverse temperature
+    const double tau = Q(act == 0 ? std::tanh(x) : staircase(x, lut_levels));
+    uint32_t w = 0;
+    for (int s = 0; s < 2; ++s) {
+      const double a = Q(tau + (s ? qxi : -qxi));
+      // least key m with Q(a + noise[m]) >= 0, by bisection (the decision is monotone)
+      int lo = 0, hi = kNoiseLevels;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Q(a + noise[mid]) >= 0.0)
+          hi = mid;
+        else
+          lo = mid + 1;
+      }
+      w |= static_cast<uint32_t>(lo) << (16 * s);
+    }
+    word[I + imax] = w;
+  }
+}
+
 }  // namespace pim

@@ -692,6 +692,82 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
 
 namespace {
 
+// Decision thresholds of the fixed-point datapath, built on the host (fixed_thresholds)
+// and uploaded; the diagonal-encoded re-indexing runs on the device as for float32 tables.
+int build_fixed_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
+                         const float* eta, float xi, int noise, int act, int lut, double c,
+                         int imax, int total_bits, int int_bits, int device) {
+  auto s = std::make_shared<Schedule>();
+  s->steps = steps;
+  s->imax = imax;
+  s->device = device;
+  s->stride_words = (2 * imax + 1 + 3) & ~3;
+  std::vector<float> z(kNoiseLevels);
+  noise_levels(noise == PIM_NOISE_GAUSS ? 0 : 1, z.data());
+  std::vector<uint32_t> words(static_cast<size_t>(steps) * s->stride_words, 0u);
+  for (int t = 0; t < steps; ++t)
+    fixed_thresholds(c, beta[t], eta[t], xi, act, lut, total_bits, int_bits, z.data(), imax,
+                     words.data() + static_cast<size_t>(t) * s->stride_words);
+  CK(cudaMalloc(&s->d_thr, words.size() * 4), "cudaMalloc thresholds");
+  CK(cudaMemcpy(s->d_thr, words.data(), words.size() * 4, cudaMemcpyHostToDevice), "upload thresholds");
+  if (imax <= kMaxImaxDiag) {
+    CK(cudaMalloc(&s->d_thr_diag, static_cast<size_t>(steps) * 1024 * 2), "cudaMalloc diagonal thresholds");
+    CK(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, s->d_thr_diag, nullptr),
+       "diagonal threshold kernel");
+    CK(cudaDeviceSynchronize(), "diagonal threshold kernel");
+  }
+  out = s;
+  return PIM_OK;
+}
+
+}  // namespace
+
+PIM_API int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* beta,
+                                   const float* eta, float xi, int noise_kind, int act_kind,
+                                   int lut_levels, int total_bits, int int_bits) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: instance is NULL");
+  if (inst->real)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: integer couplings only");
+  if (total_bits < 2 || total_bits > 32 || int_bits < 1 || int_bits > total_bits)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: need 2 <= W <= 32, 1 <= I <= W");
+  if (steps < 1 || !beta || !eta) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: bad steps/arrays");
+  if (!std::isfinite(xi) || xi < 0.0f) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: xi must be finite, >= 0");
+  if (noise_kind != PIM_NOISE_GAUSS && noise_kind != PIM_NOISE_UNIFORM)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: unknown noise kind %d", noise_kind);
+  if (act_kind != PIM_ACT_TANH && act_kind != PIM_ACT_LUT)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: unknown activation %d", act_kind);
+  if (act_kind == PIM_ACT_LUT && lut_levels < 2)
+    return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: lut_levels must be >= 2");
+  if (act_kind == PIM_ACT_TANH) lut_levels = 0;
+  for (int t = 0; t < steps; ++t)
+    if (!std::isfinite(beta[t]) || beta[t] < 0.0f || !std::isfinite(eta[t]) || eta[t] < 0.0f)
+      return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: beta/eta[%d] must be finite and >= 0", t);
+  const int imax = table_imax(inst);
+  std::string key = schedule_key(steps, beta, eta, xi, noise_kind, act_kind, lut_levels, inst->c,
+                                 imax, inst->device);
+  key += "fixed";
+  key.append(reinterpret_cast<const char*>(&total_bits), sizeof total_bits);
+  key.append(reinterpret_cast<const char*>(&int_bits), sizeof int_bits);
+  std::shared_ptr<Schedule> s;
+  {
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    auto it = g_sched_cache.find(key);
+    if (it != g_sched_cache.end()) s = it->second.lock();
+  }
+  if (!s) {
+    const int rc = build_fixed_schedule(s, steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
+                                        inst->c, imax, total_bits, int_bits, inst->device);
+    if (rc != PIM_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched_cache[key] = s;
+  }
+  if (inst->done) cudaEventSynchronize(inst->done);
+  inst->sched = s;
+  return PIM_OK;
+}
+
+namespace {
+
 // Tile plan of the large-N kernel for one instance.
 struct BigPlan {
   int nt = 0;                // output spins per CTA (64 or 128)

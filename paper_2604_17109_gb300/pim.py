@@ -48,6 +48,8 @@ SIGNATURES = {
     "pim_activation_levels": (C.c_int, [C.c_float, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "pim_thresholds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_set_schedule_fixed": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
+                                         C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                         C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -157,6 +159,19 @@ def pim_set_schedule(inst: int, beta, eta, xi: float, noise="gauss", act="tanh",
     act = _ACT.get(act, act)
     _check(lib().pim_set_schedule(inst, beta.size, _ptr(beta), _ptr(eta), float(xi), int(noise),
                                   int(act), int(lut_levels)), "pim_set_schedule")
+
+
+def pim_set_schedule_fixed(inst: int, beta, eta, xi: float, total_bits: int, int_bits: int,
+                           noise="gauss", act="tanh", lut_levels: int = 4) -> None:
+    beta = np.ascontiguousarray(beta, dtype=np.float32)
+    eta = np.ascontiguousarray(eta, dtype=np.float32)
+    if beta.shape != eta.shape:
+        raise ValueError("beta and eta must have the same length")
+    noise = _NOISE.get(noise, noise)
+    act = _ACT.get(act, act)
+    _check(lib().pim_set_schedule_fixed(inst, beta.size, _ptr(beta), _ptr(eta), float(xi),
+                                        int(noise), int(act), int(lut_levels), int(total_bits),
+                                        int(int_bits)), "pim_set_schedule_fixed")
 
 
 def pim_anneal(inst: int, replicas: int, sweeps: int, seed: int, instance_id: int = 0,

@@ -391,3 +391,51 @@ def test_sequential_update_sees_the_new_spin():
     par = oracle.anneal(J, h, 1.0, beta, eta, 0.0, replicas=1, init=init)
     assert seq["final_state"].tolist() == [[-1, -1]]
     assert par["final_state"].tolist() == [[-1, 1]]
+
+
+# ------------------------------------------------ fixed-point datapath (quantization section)
+def test_quantize_truncates_toward_zero_and_saturates():
+    q = oracle.quantize([0.3, -0.3, 1.9, -2.5, 1.75, 0.2499, -0.2499], 4, 2)
+    assert q.tolist() == [0.25, -0.25, 1.75, -2.0, 1.75, 0.0, 0.0]
+    step = 2.0 ** -12
+    q = oracle.quantize([7.99999, -9.0, 3 * step + step / 2, -(3 * step + step / 2)], 16, 4)
+    assert q.tolist() == [8 - step, -8.0, 3 * step, -3 * step]
+
+
+def test_fixed_point_decision_hand_case():
+    """ap_fixed<4,2> (step 1/4, range [-2, 1.75]), c = 1/2, I = 3, beta = 1: u = 1.5,
+    x = 1.5, tanh(1.5) = 0.905 -> 0.75; s = -1, xi = 0.7 -> 0.5: a = 0.25; eta = 0.6 -> 0.5.
+    z = -0.9 -> -0.75: n = Q(-0.375) = -0.25, delta = 0 -> +1.
+    z = -1.3 -> -1.25: n = Q(-0.625) = -0.5, delta = -0.25 -> -1."""
+    got = oracle.decide_fixed(np.array([3, 3]), np.array([-1, -1]), 0.5, 1.0, 0.7, 0.6,
+                              np.array([-0.9, -1.3]), 4, 2)
+    assert got.tolist() == [1, -1]
+
+
+def test_fixed_point_decision_monotone_in_key():
+    """The quantized decision never decreases with the noise key, so exact key thresholds
+    represent it (the table form the kernels use)."""
+    Q = pimi.gaussian_quantiles()
+    I = np.arange(-40, 41)
+    for W, Ib, act in ((4, 2, "tanh"), (6, 2, "lut"), (16, 4, "tanh")):
+        for s in (-1, 1):
+            dec = oracle.decide_fixed(np.repeat(I[:, None], 4096, 1), np.full((I.size, 4096), s),
+                                      2 / np.sqrt(40), 1.3, 0.5, 0.8,
+                                      np.broadcast_to(Q, (I.size, 4096)), W, Ib, act)
+            assert np.all(np.diff(dec.astype(int), axis=1) >= 0), (W, Ib, act, s)
+
+
+def test_fixed_point_at_high_precision_is_the_exact_rule():
+    """With 32 fractional bits the datapath is Eq. 4 itself: decisions equal
+    sign(tanh(beta c I) + xi s + eta z) evaluated in float64 wherever the margin exceeds
+    1e-6 (a dropped or mis-signed term would fail this)."""
+    rng = np.random.default_rng(3)
+    I = rng.integers(-30, 31, 20000)
+    s = np.where(rng.random(20000) < 0.5, -1, 1)
+    z = rng.standard_normal(20000)
+    c, beta, xi, eta = 2 / np.sqrt(50), 0.9, 0.7, 0.6
+    beta32, xi32, eta32 = (float(np.float32(v)) for v in (beta, xi, eta))
+    exact = np.tanh(beta32 * c * I) + xi32 * s + eta32 * z
+    got = oracle.decide_fixed(I, s, c, beta, xi, eta, z, 40, 8)
+    ok = np.abs(exact) > 1e-6
+    assert np.array_equal(got[ok], np.where(exact[ok] >= 0, 1, -1))
