@@ -54,6 +54,7 @@ class Workload:
 WORKLOADS = {
     "sk200": Workload("sk200", "sk", 200, 100, 1024, 2000, 0.5),
     "sk4096": Workload("sk4096", "sk", 4096, 1, 256, 10000, 0.5),
+    "sk512": Workload("sk512", "sk", 512, 152, 256, 1000, 0.5),  # a batch on the mid-N kernel
     "maxcut100": Workload("maxcut100", "maxcut", 100, 1, 64, 1000, 0.7),
     "maxcut8192": Workload("maxcut8192", "maxcut_gauss", 8192, 1, 256, 10000, 0.7),
     # n ~ U[64, 1024], replicas ~ U{32, .., 512}; n and replicas here are the maxima
@@ -77,6 +78,20 @@ MIMO_RATE = {"mimo16": 4000.0, "mimo64": 1000.0}  # offered load, requests per s
 ALU_OPS_PER_SPIN_UPDATE = 5.0 + 2 + 1 + 1 + 2 + 1 + 0.75
 SM_COUNT = 152
 LANES_PER_SM = 128
+
+# DRAM bytes (read + write) of the dominant kernel per launch, from ncu captures of these
+# workloads (the summaries under profiles/ name the commands), as fixed + per-pass bytes
+# (passes = sweeps + 1):
+#   sk200       sweep_tc_kernel<256,0>, full-size launch: 14.56 MB, nothing grows per pass
+#   sk4096      sweep_big_kernel<64,FP8>, 50-sweep capture 18.85 MB = 16.8 MB image (L2-resident
+#               afterwards) + misc, and one 32 KB threshold table per pass
+#   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.194 GB = the 134 MB image
+#               streamed from HBM every pass (it exceeds L2)
+DRAM_TRAFFIC = {
+    "sk200": (14.556e6, 0.0),
+    "sk4096": (18.848e6 - 51 * 32768.0, 32768.0),
+    "maxcut8192": (0.0, 7.194e9 / 51),
+}
 
 
 def _schedule(sweeps: int):
@@ -652,14 +667,25 @@ def run_ours(args, w: Workload):
                     "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
     elif w.kind == "uneven":
         roofline = dict(tensor, kernel="sweep_mid_kernel (+ fused sweep kernels for n <= 256)")
+    elif w.n <= 1024 and n_inst > 1:
+        roofline = dict(tensor, kernel="sweep_mid_kernel")
     else:
         roofline = dict(tensor, kernel=f"sweep_big_kernel<{'BF16' if real else 'FP8'}>")
-        # couplings stream from L2 / HBM once per replica tile per sweep
-        j_bytes = sum(i.n * i.n * (2 if real else 1) * ((r + 127) // 128)
-                      for i, r in zip(insts, reps)) * sweeps
-        hbm = j_bytes / (k_ms * 1e-3) / 1e9
-        roofline["coupling_stream"] = {"achieved": hbm, "unit": "GB/s",
-                                       "frac_of_hbm": hbm / float(peaks["hbm_gbs"])}
+        # every replica tile streams the whole coupling image from L2 each sweep; HBM sees it
+        # once per sweep when it does not fit L2 (the tiles meet in L2)
+        l2_bytes = sum(i.n * i.n * (2 if real else 1) * ((r + 127) // 128)
+                       for i, r in zip(insts, reps)) * sweeps
+        roofline["coupling_l2_to_sm"] = {"achieved": l2_bytes / (k_ms * 1e-3) / 1e9,
+                                         "unit": "GB/s"}
+    traffic = DRAM_TRAFFIC.get(w.key)
+    if traffic is not None and args.sweeps is None and args.instances is None:
+        fixed, per_pass = traffic
+        roofline["traffic"] = fixed + per_pass * (sweeps + 1)
+        roofline["traffic_basis"] = "ncu dram__bytes_read + write of this kernel, fixed + per pass"
+        if w.n > 256:
+            hbm = roofline["traffic"] / (k_ms * 1e-3) / 1e9
+            roofline["hbm"] = {"achieved": hbm, "unit": "GB/s",
+                               "frac": hbm / float(peaks["hbm_gbs"])}
     config = {"workload": w.name, "n": w.n, "instances_per_gpu": n_inst,
               "replicas": w.replicas if w.kind != "uneven" else "32..512",
               "sweeps": sweeps, "couplings": _couplings(w),
