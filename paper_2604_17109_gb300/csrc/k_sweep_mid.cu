@@ -51,6 +51,42 @@ __device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint3
   *reinterpret_cast<uint4*>(sA + sw128_offset(row, col + 16, 128)) = fp8x16_from_bits(bits >> 16);
 }
 
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: integer D in the low mantissa bits
+constexpr uint32_t kMagicBits = 0x4B400000u;
+
+// Sixteen spins of one replica, general-bias table without bias (h = 0, plain image):
+// vb = bits(D + 1.5 * 2^23) = 0x4B400000 + I, the 16-bit threshold of (s, I) at shared
+// address tab_c + 4 vb + 2 s (tab_c = table + 4 (imax - 0x4B400000), mod 2^32), and
+// key >= M  <=>  d >= 16 M for the 16-bit draw d (key = d >> 4); the sign bits of d - 16 M
+// (new spin -1) are shifted in by two chains.  sum_all / sum_up collect vb over all spins /
+// the +1 spins for the energy.  Returns the new spins as bits 0..15.
+__device__ __forceinline__ uint32_t bias_chunk16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
+                                                 uint32_t cw16, uint32_t tab_c, uint32_t& sum_all,
+                                                 uint32_t& sum_up, bool decide) {
+  uint32_t neg_hi = 0, neg_lo = 0, sa = 0, su = 0;
+#pragma unroll
+  for (int e = 15; e >= 0; --e) {
+    const uint32_t vb = __float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic));
+    const uint32_t s = (cw16 >> e) & 1u;
+    sa += vb;
+    su += s * vb;
+    if (decide) {
+      uint32_t m;
+      asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(tab_c + 4u * vb + 2u * s));
+      const uint32_t w = rw[e >> 1];
+      const uint32_t d = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+      const uint32_t diff = d + m * 0xFFFFFFF0u;  // d - 16 m
+      if (e >= 8)
+        neg_hi = __funnelshift_l(diff, neg_hi, 1);
+      else
+        neg_lo = __funnelshift_l(diff, neg_lo, 1);
+    }
+  }
+  sum_all += sa;
+  sum_up += su;
+  return ~((neg_hi << 8) | neg_lo) & 0xFFFFu;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_constant__ Launch L) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -235,8 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       const bool has_target = P.has_target != 0;
       const int dg = P.diag_img ? 256 : 0;  // diagonal-encoded image: D = I + 256 s
       const bool fast = P.h == nullptr && !P.diag_img && tab_smem;
-      const uint16_t* sTab16 = reinterpret_cast<const uint16_t*>(sTab);
-      const uint32_t toff = 2u * static_cast<uint32_t>(imax) - 2u * 0x4B400000u;  // mod 2^32
+      const uint32_t tab_c = smem_u32(sTab) + 4u * static_cast<uint32_t>(imax) - 4u * kMagicBits;  // mod 2^32
       for (int t = t_begin; t <= t_end && !stop; ++t) {
         const bool last = t == t_end;
         if (tab_smem && !last) {
@@ -255,97 +290,91 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           ++cpass;
           if (!mbar_wait_sleep(tfull0 + 8 * b, buse & 1, L.wait_ns)) waitfail = true;
           tc_fence_after();
-          // All kCols fields of this thread: four TMEM loads in flight while the Philox
-          // blocks of its first 32 spins are drawn, one wait, then the buffer is released.
-          uint32_t v[kCols / 16][16];
-          uint32_t rw[4][4];
+          const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) + b * kNT + grp * kCols;
           const uint32_t blk0 = static_cast<uint32_t>((c * kNT + grp * kCols) >> 3);
-          auto draw = [&](int w) {  // Philox blocks of spins 32w .. 32w+31
+          if (fast) {
+            // 16 columns at a time: the TMEM load runs while their two Philox blocks are
+            // drawn, then the decisions (bias_chunk16); the buffer is released at the end.
+            if (warp_active) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              PhiloxOut o{};
-              if (!last)
-                o = philox4x32_10_rk(blk0 + 4 * w + k, static_cast<uint32_t>(rg),
-                                     static_cast<uint32_t>(t), q, L.round_keys);
-              rw[k][0] = o.x0;
-              rw[k][1] = o.x1;
-              rw[k][2] = o.x2;
-              rw[k][3] = o.x3;
-            }
-          };
-          if (warp_active) {
-            const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) + b * kNT + grp * kCols;
-#pragma unroll
-            for (int h2 = 0; h2 < kCols / 16; ++h2) tmem_ld16(ta + 16 * h2, v[h2]);
-            draw(0);
-#pragma unroll
-            for (int h2 = 0; h2 < kCols / 16; ++h2) tmem_wait_ld(v[h2]);
-          }
-          // TMEM buffer b drained by this warp: let the MMA issuer reuse it.
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-          if (warp_active && fast) {
-            // h = 0, plain image, table in shared memory.  With vb = bits(D + 1.5 * 2^23) the
-            // field is I = vb - 0x4B400000, the 16-bit threshold of (s, I) sits at entry
-            // 2 (I + imax) + s of the table, and key < threshold (new spin -1) is the sign of
-            // key - threshold, shifted into `down`.  Energies sum the raw vb and are corrected
-            // once per 32 spins (mod 2^32 arithmetic; the true sums fit in int32).
-#pragma unroll
-            for (int w = 0; w < kWordsPT; ++w) {
-              if (w > 0) draw(w);
-              const uint32_t cw = cur[c][w];
-              uint32_t down = 0, sum_all = 0, sum_up = 0;
-#pragma unroll
-              for (int bit = 0; bit < 32; ++bit) {
-                const int e = 32 * w + bit;
-                const uint32_t vb = __float_as_uint(__fadd_rn(__uint_as_float(v[e >> 4][e & 15]), 12582912.0f));
-                const uint32_t s = (cw >> bit) & 1u;
-                sum_all += vb;
-                sum_up += s * vb;
+              for (int h2 = 0; h2 < kCols / 16; ++h2) {
+                uint32_t v[16];
+                tmem_ld16(ta + 16 * h2, v);
+                PhiloxOut o0{}, o1{};
                 if (!last) {
-                  const uint32_t th = sTab16[2u * vb + s + toff];
-                  const uint32_t word = rw[bit >> 3][(bit & 7) >> 1];
-                  const uint32_t key = (bit & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
-                  down = __funnelshift_l(key - th, down, 1);
+                  o0 = philox4x32_10_rk(blk0 + 2 * h2, static_cast<uint32_t>(rg),
+                                        static_cast<uint32_t>(t), q, L.round_keys);
+                  o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, static_cast<uint32_t>(rg),
+                                        static_cast<uint32_t>(t), q, L.round_keys);
                 }
+                tmem_wait_ld(v);
+                const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+                const int w = h2 >> 1;
+                const uint32_t cw16 = (cur[c][w] >> (16 * (h2 & 1))) & 0xFFFFu;
+                uint32_t sa = 0, su = 0;
+                const uint32_t nb = bias_chunk16(v, rw8, cw16, tab_c, sa, su, !last);
+                eacc += static_cast<int>(2u * (su - static_cast<uint32_t>(__popc(cw16)) * kMagicBits) -
+                                         (sa - 16u * kMagicBits));
+                if (h2 & 1)
+                  nxt[c][w] = (nxt[c][w] | (nb << 16)) & valid_mask(c, w);
+                else
+                  nxt[c][w] = nb;
               }
-              const uint32_t up_sum = sum_up - static_cast<uint32_t>(__popc(cw)) * 0x4B400000u;
-              const uint32_t all_sum = sum_all - 32u * 0x4B400000u;
-              eacc += static_cast<int>(2u * up_sum - all_sum);
-              nxt[c][w] = ~__brev(down) & valid_mask(c, w);
             }
-          } else if (warp_active) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+            continue;
+          }
+          // General path (bias, diagonal-encoded image or a table in global memory), 16
+          // columns at a time like the fast path.
+          if (warp_active) {
 #pragma unroll
-            for (int w = 0; w < kWordsPT; ++w) {
-              if (w > 0) draw(w);
-              const uint32_t cw = cur[c][w];
+            for (int h2 = 0; h2 < kCols / 16; ++h2) {
+              uint32_t v[16];
+              tmem_ld16(ta + 16 * h2, v);
+              PhiloxOut o0{}, o1{};
+              if (!last) {
+                o0 = philox4x32_10_rk(blk0 + 2 * h2, static_cast<uint32_t>(rg),
+                                      static_cast<uint32_t>(t), q, L.round_keys);
+                o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, static_cast<uint32_t>(rg),
+                                      static_cast<uint32_t>(t), q, L.round_keys);
+              }
+              tmem_wait_ld(v);
+              const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+              const int w = h2 >> 1;
+              const uint32_t cw16 = (cur[c][w] >> (16 * (h2 & 1))) & 0xFFFFu;
               uint32_t nb = 0;
 #pragma unroll
-              for (int bit = 0; bit < 32; ++bit) {
-                const int e = 32 * w + bit;  // column of this thread inside the chunk
-                const int col = c * kNT + grp * kCols + e;
-                const uint32_t s = (cw >> bit) & 1u;
+              for (int e = 0; e < 16; ++e) {
+                const int col = c * kNT + grp * kCols + 16 * h2 + e;
+                const uint32_t s = (cw16 >> e) & 1u;
                 const int hv = sH[col];
                 const int dgc = col < n ? (s ? dg : -dg) : 0;  // image diagonal inside n only
-                // exact float -> int of the integer-valued field (|D| < 2^22) by the
-                // 1.5 * 2^23 shift, at full FP32/INT rate
-                const int D = __float_as_int(__fadd_rn(__uint_as_float(v[e >> 4][e & 15]), 12582912.0f)) -
-                              0x4B400000;
+                // exact float -> int of the integer-valued field (|D| < 2^22)
+                const int D = static_cast<int>(__float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic)) -
+                                               kMagicBits);
                 const int I = D + hv - dgc;
                 const int term = I + hv;
                 eacc += s ? term : -term;
                 if (!last) {
                   const uint32_t wd = tab[I + imax];
                   const uint32_t th = s ? (wd >> 16) : (wd & 0xFFFFu);
-                  const uint32_t word = rw[bit >> 3][(bit & 7) >> 1];
-                  const uint32_t key = (bit & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
-                  nb |= (key >= th ? 1u : 0u) << bit;
+                  const uint32_t word = rw8[e >> 1];
+                  const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+                  nb |= (key >= th ? 1u : 0u) << e;
                 }
               }
-              nxt[c][w] = nb & valid_mask(c, w);
+              if (h2 & 1)
+                nxt[c][w] = (nxt[c][w] | (nb << 16)) & valid_mask(c, w);
+              else
+                nxt[c][w] = nb;
             }
           }
+          // TMEM buffer b drained by this warp: let the MMA issuer reuse it.
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
         }
         if (!last && warp_active) {
           // Every MMA of sweep t has completed (the last chunk's commit was awaited): the A
