@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
       const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * NT * 128;
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = loads % kStages, use = loads / kStages;
-        if (use > 0 && !mbar_wait_bounded(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
+        if (use > 0 && !mbar_wait_fast(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
         mbar_expect_tx(bar_full0 + 8 * s, kABytes + kBBytes);
         bulk_g2s(smem_u32(sA + s * kABytes), a_src + static_cast<size_t>(kb) * rpad * 128, kABytes,
                  bar_full0 + 8 * s);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     auto multiply = [&]() -> bool {
       for (int kb = 0; kb < kblocks; ++kb) {
         const uint32_t s = mmas % kStages, use = mmas / kStages;
-        if (!mbar_wait_bounded(bar_full0 + 8 * s, use & 1, L.wait_ns)) return false;
+        if (!mbar_wait_fast(bar_full0 + 8 * s, use & 1, L.wait_ns)) return false;
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
             reinterpret_cast<uint4*>(sTab)[k] = __ldg(src + k);
         }
         asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
-        const bool ok = mbar_wait_bounded(bar_done, done_phase, L.wait_ns);
+        const bool ok = mbar_wait_fast(bar_done, done_phase, L.wait_ns);
         if (!ok) {
           atomicOr(L.err, kDevErrTimeout);
           atomicExch(&L.bar[2], 1u);

@@ -45,6 +45,12 @@ constexpr int kABytes = 128 * kMaxNpad;     // spin image: 128 rows x npad FP8
 constexpr int kStageBytes = kNT * 128;      // one K-block of 128 coupling rows
 constexpr int kBarCount = 2 * kStages + 2 * kBufs + 2;
 
+// Bounded wait with the common case (phase already complete) inline; the out-of-line wait
+// sleeps inside try_wait between checks.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  return mbar_try_wait(bar, parity) || mbar_wait_sleep(bar, parity, limit_ns);
+}
+
 // 32 spins (bits) -> their 32 FP8 +-1 bytes in one row of the A image.
 __device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint32_t bits) {
   *reinterpret_cast<uint4*>(sA + sw128_offset(row, col, 128)) = fp8x16_from_bits(bits & 0xFFFFu);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
         for (int c = 0; c < nchunks && ok; ++c)
           for (int kb = 0; kb < kblocks; ++kb) {
             const uint32_t s = loads % kStages, use = loads / kStages;
-            if ((use > 0 && !mbar_wait_sleep(empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) ||
+            if ((use > 0 && !wait_phase(empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) ||
                 *sAbort != 0) {
               ok = false;
               break;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       // ---- MMA issuer: per sweep, wait for s(t) in the A image, then every chunk --------
       bool ok = true;
       for (int t = t_begin; t <= t_end && ok; ++t) {
-        if (!mbar_wait_sleep(aready, apass & 1, L.wait_ns)) {
+        if (!wait_phase(aready, apass & 1, L.wait_ns)) {
           ok = false;
           break;
         }
@@ -189,14 +195,14 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
         tc_fence_after();
         for (int c = 0; c < nchunks && ok; ++c) {
           const uint32_t b = cpass % kBufs, buse = cpass / kBufs;
-          if (buse > 0 && !mbar_wait_sleep(tempty0 + 8 * b, (buse - 1) & 1, L.wait_ns)) {
+          if (buse > 0 && !wait_phase(tempty0 + 8 * b, (buse - 1) & 1, L.wait_ns)) {
             ok = false;
             break;
           }
           tc_fence_after();
           for (int kb = 0; kb < kblocks; ++kb) {
             const uint32_t s = mmas % kStages, use = mmas / kStages;
-            if (!mbar_wait_sleep(full0 + 8 * s, use & 1, L.wait_ns)) {
+            if (!wait_phase(full0 + 8 * s, use & 1, L.wait_ns)) {
               ok = false;
               break;
             }
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t b = cpass % kBufs, buse = cpass / kBufs;
           ++cpass;
-          if (!mbar_wait_sleep(tfull0 + 8 * b, buse & 1, L.wait_ns)) waitfail = true;
+          if (!wait_phase(tfull0 + 8 * b, buse & 1, L.wait_ns)) waitfail = true;
           tc_fence_after();
           const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) + b * kNT + grp * kCols;
           const uint32_t blk0 = static_cast<uint32_t>((c * kNT + grp * kCols) >> 3);
@@ -441,10 +447,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
   // ---- teardown: no copy or MMA of this CTA may still be in flight ------------------------
   if (tid == 32) {
     mma_commit(drain);
-    mbar_wait_sleep(drain, 0, L.wait_ns);
+    wait_phase(drain, 0, L.wait_ns);
   } else if (tid == 0) {
     for (uint32_t k = loads > kStages ? loads - kStages : 0; k < loads; ++k)
-      mbar_wait_sleep(full0 + 8 * (k % kStages), (k / kStages) & 1, L.wait_ns);
+      wait_phase(full0 + 8 * (k % kStages), (k / kStages) & 1, L.wait_ns);
   }
   tc_fence_before();
   __syncthreads();

@@ -75,6 +75,12 @@ static __device__ __noinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parit
   return true;
 }
 
+// Bounded wait with the common case (phase already complete) inline: the out-of-line wait
+// (a call) only runs when the data is not there yet.
+__device__ __forceinline__ bool mbar_wait_fast(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  return mbar_try_wait(bar, parity) || mbar_wait_bounded(bar, parity, limit_ns);
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
