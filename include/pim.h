@@ -308,10 +308,15 @@ int pim_mimo_server_replay(pim_mimo_server* server, int count, const double* H_a
                            const double* y_all, const double* reg_all,
                            const double* arrival_us, double* x_hat_all,
                            double* best_energy_all, double* latency_us_all);
+/* Stops admitting, finishes the batches in flight, drops requests still queued and frees
+   the server; no other call on the server may run concurrently with it. */
 void pim_mimo_server_destroy(pim_mimo_server* server);
 
 /* pim_sync -- block until the instance's last anneal has finished.
- * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up). */
+ * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up).
+ * Device-side error bits are kept per device and cleared when reported: with concurrent
+ * launches on one device, a PIM_ERR_TIMEOUT is reported by the first synchronising call
+ * after it was raised, which may belong to another instance of that device. */
 int pim_sync(pim_instance* inst);
 
 /*
