@@ -312,6 +312,20 @@ int pim_mimo_server_replay(pim_mimo_server* server, int count, const double* H_a
    the server; no other call on the server may run concurrently with it. */
 void pim_mimo_server_destroy(pim_mimo_server* server);
 
+/*
+ * pim_results_dev -- the last anneal's records copied device to device, stream-ordered
+ * after it on `cuda_stream` (the host does not wait): for callers that keep results on
+ * the GPU (a serving loop, a framework's tensors).  Device pointers, each may be NULL:
+ *   best_E, final_E       R doubles;  best_t, first_hit_t  R int32;
+ *   best_bits, final_bits R x pim_state_words(inst) uint32 words, bit i of word i/32 set
+ *                         <=> spin i = +1 (bits past n are 0).
+ * pim_state_words -- words per replica of the bit arrays (0 for NULL).
+ * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (no anneal has run), PIM_ERR_CUDA.
+ */
+int pim_results_dev(pim_instance* inst, double* best_E, int32_t* best_t, int32_t* first_hit_t,
+                    double* final_E, uint32_t* best_bits, uint32_t* final_bits, void* cuda_stream);
+int pim_state_words(const pim_instance* inst);
+
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up).
  * Device-side error bits are kept per device and cleared when reported: with concurrent

@@ -1547,6 +1547,28 @@ int copy_state(pim_instance* inst, const uint32_t* d_bits, int8_t* out) {
 }
 }  // namespace
 
+PIM_API int pim_results_dev(pim_instance* inst, double* best_E, int32_t* best_t,
+                            int32_t* first_hit_t, double* final_E, uint32_t* best_bits,
+                            uint32_t* final_bits, void* cuda_stream) {
+  if (!inst) return fail(PIM_ERR_INVALID, "pim_results_dev: instance is NULL");
+  if (!inst->has_results) return fail(PIM_ERR_STATE, "pim_results_dev: no anneal has run");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  CK(cudaStreamWaitEvent(st, inst->done, 0), "cudaStreamWaitEvent");
+  const size_t R = inst->R, bits = R * inst->words * sizeof(uint32_t);
+  auto d2d = [&](void* dst, const void* src, size_t bytes) {
+    return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+  };
+  CK(d2d(best_E, inst->d_bestE, R * 8), "copy best energies");
+  CK(d2d(final_E, inst->d_finalE, R * 8), "copy final energies");
+  CK(d2d(best_t, inst->d_bestT, R * 4), "copy best steps");
+  CK(d2d(first_hit_t, inst->d_first, R * 4), "copy first hits");
+  CK(d2d(best_bits, inst->d_best_bits, bits), "copy best states");
+  CK(d2d(final_bits, inst->d_cur_bits, bits), "copy final states");
+  return PIM_OK;
+}
+
+PIM_API int pim_state_words(const pim_instance* inst) { return inst ? inst->words : 0; }
+
 PIM_API int pim_best_state(pim_instance* inst, int8_t* out) {
   if (!inst) return fail(PIM_ERR_INVALID, "pim_best_state: instance is NULL");
   return copy_state(inst, inst->d_best_bits, out);

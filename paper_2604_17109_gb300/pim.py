@@ -50,6 +50,9 @@ SIGNATURES = {
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pim_set_schedule_fixed": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "pim_results_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_state_words": (C.c_int, [C.c_void_p]),
     "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                         C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -335,6 +338,22 @@ def pim_batch_info(batch: int) -> dict:
 
 def pim_batch_destroy(batch: int) -> None:
     lib().pim_batch_destroy(batch)
+
+
+def pim_state_words(inst: int) -> int:
+    return lib().pim_state_words(inst)
+
+
+def pim_results_dev(inst: int, best_E=None, best_t=None, first_hit=None, final_E=None,
+                    best_bits=None, final_bits=None, stream=None) -> None:
+    """Device-to-device copies of the records into caller buffers given as device pointers
+    (ints) or objects with a data_ptr() (e.g. torch tensors); None skips a record."""
+    def dp(x):
+        if x is None:
+            return None
+        return x if isinstance(x, int) else int(x.data_ptr())
+    _check(lib().pim_results_dev(inst, dp(best_E), dp(best_t), dp(first_hit), dp(final_E),
+                                 dp(best_bits), dp(final_bits), _stream(stream)), "pim_results_dev")
 
 
 def pim_sync(inst: int) -> None:

@@ -348,3 +348,34 @@ def test_sk4096_sampled_replicas():
     assert_same(got, want, rows=rows, label="sk4096")
     assert np.array_equal(oracle.energy(inst.J, inst.h, got["final_state"]), got["final_E"])
     assert np.array_equal(oracle.energy(inst.J, inst.h, got["best_state"]), got["best_E"])
+
+
+def test_results_dev_equal_host_getters():
+    """pim_results_dev copies the records device to device, stream-ordered: they equal the
+    host getters (energies, steps, and the bit words unpacked)."""
+    import torch
+    P = pim()
+    inst = sk_pm1(70, 3)
+    beta = linear_beta(20)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta_power(beta), 0.5)
+        R = 150
+        stream = torch.cuda.Stream()
+        P.pim_anneal(hd, R, 20, 4, target=-40, stream=stream)
+        words = P.pim_state_words(hd)
+        dev = torch.device("cuda")
+        bE, fE = torch.empty(R, dtype=torch.float64, device=dev), torch.empty(R, dtype=torch.float64, device=dev)
+        bt, fh = torch.empty(R, dtype=torch.int32, device=dev), torch.empty(R, dtype=torch.int32, device=dev)
+        bb, fb = (torch.empty(R * words, dtype=torch.int32, device=dev) for _ in range(2))
+        P.pim_results_dev(hd, bE, bt, fh, fE, bb, fb, stream=stream)
+        stream.synchronize()
+        host = collect(hd, 70)
+    finally:
+        P.pim_destroy(hd)
+    assert np.array_equal(bE.cpu().numpy(), host["best_E"]) and np.array_equal(fE.cpu().numpy(), host["final_E"])
+    assert np.array_equal(bt.cpu().numpy(), host["best_t"]) and np.array_equal(fh.cpu().numpy(), host["first_hit"])
+    for words_t, key in ((bb, "best_state"), (fb, "final_state")):
+        w = words_t.cpu().numpy().view(np.uint32).reshape(R, words)
+        bits = (w[:, np.arange(70) // 32] >> (np.arange(70) % 32)) & 1
+        assert np.array_equal(np.where(bits > 0, 1, -1), host[key])
