@@ -687,6 +687,7 @@ def run_ours(args, w: Workload):
             roofline["hbm"] = {"achieved": hbm, "unit": "GB/s",
                                "frac": hbm / float(peaks["hbm_gbs"])}
     config = {"workload": w.name, "n": w.n, "instances_per_gpu": n_inst,
+              "us_per_sweep": ms_per_step * 1000.0 / sweeps,
               "replicas": w.replicas if w.kind != "uneven" else "32..512",
               "sweeps": sweeps, "couplings": _couplings(w),
               "schedule": f"linear beta 0.1->3, eta=sqrt(beta/5), xi={w.xi if w.kind != 'uneven' else '0.7/0.5'}",
