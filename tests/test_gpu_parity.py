@@ -379,3 +379,65 @@ def test_results_dev_equal_host_getters():
         w = words_t.cpu().numpy().view(np.uint32).reshape(R, words)
         bits = (w[:, np.arange(70) // 32] >> (np.arange(70) % 32)) & 1
         assert np.array_equal(np.where(bits > 0, 1, -1), host[key])
+
+
+def test_sk4096_full_configuration_properties():
+    """SK N = 4096, 256 replicas x 10 000 sweeps (the configuration the benchmark times):
+    every replica's reported best / final energies are the exact energies of the reported
+    states, best <= final, and the best step lies in range."""
+    P = pim()
+    inst = sk_pm1(4096, 0)
+    T = 10000
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal(hd, 256, T, 0, instance_id=0)
+        got = collect(hd, 4096)
+    finally:
+        P.pim_destroy(hd)
+    assert np.array_equal(oracle.energy(inst.J, inst.h, got["final_state"]), got["final_E"])
+    assert np.array_equal(oracle.energy(inst.J, inst.h, got["best_state"]), got["best_E"])
+    assert np.all(got["best_E"] <= got["final_E"])
+    assert np.all((got["best_t"] >= 0) & (got["best_t"] <= T))
+
+
+def test_uneven4096_full_batch_plan():
+    """The 4096-instance uneven batch (n ~ U[64, 1024], replicas ~ U{32..512}, 1000 sweeps)
+    as one graph-replayed batch plan, the configuration the benchmark times: sampled
+    instances bit-exact against the oracle on sampled replicas, energy identities for every
+    replica of the sampled instances."""
+    from workloads import uneven_batch
+    P = pim()
+    insts, reps = uneven_batch(4096, seed=0)
+    T = 1000
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    xis = [0.7 if k % 2 == 0 else 0.5 for k in range(len(insts))]
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    try:
+        for hd, xi in zip(handles, xis):
+            P.pim_set_schedule(hd, beta, eta, xi)
+        b = P.pim_batch_create(handles, reps, instance_ids=list(range(len(insts))))
+        P.pim_batch_run(b, T, 0)
+        P.pim_sync(handles[0])
+        sizes = np.array([i.n for i in insts])
+        small = [int(k) for k in np.flatnonzero(sizes <= 256)[:3]]
+        mid = [int(k) for k in np.flatnonzero((sizes > 256) & (sizes <= 400))[:2]]
+        for k in small + mid:
+            got = collect(handles[k], insts[k].n)
+            rows = [0, reps[k] - 1]
+            want = oracle_run(insts[k], beta, eta, xis[k], replica_ids=rows, seed=0, q=k)
+            assert_same(got, want, rows=rows, label=f"instance {k} n={insts[k].n}")
+        for k in small + mid + [int(np.argmax(sizes))]:
+            got = collect(handles[k], insts[k].n)
+            J, h = insts[k].J, insts[k].h
+            assert np.array_equal(oracle.energy(J, h, got["best_state"]), got["best_E"])
+            assert np.array_equal(oracle.energy(J, h, got["final_state"]), got["final_E"])
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)
