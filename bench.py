@@ -588,7 +588,11 @@ def run_ours(args, w: Workload):
     # batched anneal, read every replica's best energy and best state back, release.
     e2e_steps = 1 if n_inst > 1000 else max(1, min(3, args.steps))
     h2d = sum(i.n * i.n * (2 if real else 1) for i in insts)  # BF16 or int8 couplings copied
-    d2h = sum(r * (8 + 4 + 4 + 8) + r * (((i.n + 63) // 64) * 2) * 4 for i, r in zip(insts, reps))
+    # results come back with the run (PIM_RESULTS_TO_HOST): the whole result block of each
+    # instance, per-replica scalars and best and final state bits, each part 256-byte aligned
+    def _al(x):
+        return (x + 255) // 256 * 256
+    d2h = sum(_al(r * 24) + 2 * _al(r * ((i.n + 63) // 64) * 2 * 4) for i, r in zip(insts, reps))
     out_E = [None] * n_inst
     torch.cuda.synchronize()
     _barrier(world)
@@ -597,7 +601,8 @@ def run_ours(args, w: Workload):
         hs = [pim.pim_create(i.J, None, i.c) for i in insts]
         for hd, xi in zip(hs, xis):
             pim.pim_set_schedule(hd, beta, eta, xi)
-        pim.pim_anneal_batch(hs, reps, sweeps, seed=0, instance_ids=ids, stream=stream)
+        pim.pim_anneal_batch(hs, reps, sweeps, seed=0, instance_ids=ids, stream=stream,
+                             flags=pim.PIM_RESULTS_TO_HOST)
         for q, (hd, inst) in enumerate(zip(hs, insts)):
             out_E[q] = pim.pim_energies(hd)["best_E"]
             pim.pim_best_state(hd, inst.n)

@@ -75,9 +75,15 @@ typedef enum pim_flags {
                            of the fused tensor-core sweep kernel (same decisions) */
   PIM_PATH_MID = 4,     /* put every integer instance with n <= 1024 on the persistent mid-N
                            kernel (same decisions; for tests and tuning) */
-  PIM_PATH_BIG = 8      /* put every instance with n > 256 on the large-N cooperative kernel
+  PIM_PATH_BIG = 8,     /* put every instance with n > 256 on the large-N cooperative kernel
                            (same decisions; for tests and tuning).  Without either flag the
                            library picks the kernel of each instance from its cost model. */
+  PIM_RESULTS_TO_HOST = 16 /* after the run, copy every instance's results (all of what
+                           pim_energies, pim_best_state and pim_final_state return) into
+                           library-owned pinned host memory on the same stream, so those
+                           getters wait for the run and read host memory instead of issuing
+                           a synchronous copy each.  Costs R * (24 + 8 * words) bytes of
+                           device-to-host traffic per instance and run. */
 } pim_flags;
 
 typedef struct pim_instance pim_instance;
@@ -202,7 +208,8 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
  * pim_batch_run runs sweeps t_begin .. t_begin+sweeps-1 of every instance, asynchronously on
  * `cuda_stream`: the first run with given (t_begin, sweeps, seed, run_flags) captures the
  * batch's launches into a CUDA graph (later changes update the instantiated graph in
- * place) and every run replays it with one cudaGraphLaunch.  run_flags: 0 or PIM_CONTINUE.
+ * place) and every run replays it with one cudaGraphLaunch.  run_flags: PIM_CONTINUE and / or
+ * PIM_RESULTS_TO_HOST.
  * Results are read with the per-instance getters.  A batch whose launches cannot be
  * captured runs them directly instead (pim_batch_info reports which).
  * pim_batch_info: kernel launches per run and whether runs replay a graph (1) or not (0).
@@ -227,7 +234,7 @@ void pim_batch_destroy(pim_batch* batch);
  *   Energies are evaluated on the state at the start of every sweep and on the final
  *   state; best / first-hit / final records are read with the usual getters.
  *   replicas, t_begin, sweeps, seed, instance_id, init_spins, target_energy, cuda_stream
- *   as pim_anneal; flags: 0 or PIM_CONTINUE.  One warp per replica.
+ *   as pim_anneal; flags: PIM_CONTINUE and / or PIM_RESULTS_TO_HOST.  One warp per replica.
  * Errors: PIM_ERR_INVALID, PIM_ERR_STATE, PIM_ERR_UNSUPPORTED (real couplings, n too large
  *         for shared memory), PIM_ERR_NOMEM, PIM_ERR_CUDA.
  */
@@ -328,8 +335,10 @@ int pim_state_words(const pim_instance* inst);
 
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up).
- * Device-side error bits are kept per device and cleared when reported: with concurrent
- * launches on one device, a PIM_ERR_TIMEOUT is reported by the first synchronising call
+ * Device-side error bits are kept per device and cleared when reported.  Every run copies
+ * them into host memory at its end, before it is marked finished; a synchronising call
+ * reports the bits of the latest such copy.  With concurrent launches on one device, a
+ * PIM_ERR_TIMEOUT is thus reported by the first synchronising call on a run that ended
  * after it was raised, which may belong to another instance of that device. */
 int pim_sync(pim_instance* inst);
 

@@ -92,19 +92,90 @@ std::atomic<uint64_t> g_wait_ns{0};
 std::mutex g_sched_mu;
 std::map<std::string, std::weak_ptr<Schedule>> g_sched_cache;
 
-// Per-device error word written by the kernels.
+// Per-device error word written by the kernels, and a pinned host mirror that every run
+// refreshes (stream-ordered) before it records its completion event, so result getters read
+// host memory instead of issuing a synchronous copy.
+struct ErrWord {
+  int* d = nullptr;
+  int* h = nullptr;
+};
 std::mutex g_err_mu;
-std::map<int, int*> g_err_word;
+std::map<int, ErrWord> g_err_word;
 
-int* device_error_word(int dev) {
+ErrWord* error_word(int dev) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   auto it = g_err_word.find(dev);
-  if (it != g_err_word.end()) return it->second;
-  int* p = nullptr;
-  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
-  cudaMemset(p, 0, sizeof(int));
-  g_err_word[dev] = p;
+  if (it != g_err_word.end()) return &it->second;
+  ErrWord w;
+  if (cudaMalloc(&w.d, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaHostAlloc(&w.h, sizeof(int), cudaHostAllocPortable) != cudaSuccess) {
+    cudaFree(w.d);
+    return nullptr;
+  }
+  cudaMemset(w.d, 0, sizeof(int));
+  *w.h = 0;
+  return &(g_err_word[dev] = w);
+}
+
+int* device_error_word(int dev) {
+  ErrWord* w = error_word(dev);
+  return w ? w->d : nullptr;
+}
+
+// CUDA events without timing, reused across instances (creating and destroying two per
+// instance is a visible share of staging small instances).
+std::mutex g_ev_mu;
+std::map<int, std::vector<cudaEvent_t>> g_free_events;
+
+cudaError_t take_event(int dev, cudaEvent_t* ev) {
+  {
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    auto& v = g_free_events[dev];
+    if (!v.empty()) {
+      *ev = v.back();
+      v.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+}
+
+void give_event(int dev, cudaEvent_t ev) {
+  if (!ev) return;
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  g_free_events[dev].push_back(ev);
+}
+
+// Pinned host blocks for results copied back with the run, kept in power-of-two size
+// classes and reused (page-locking memory costs far more than a small copy).
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_free_pinned;
+
+size_t pinned_class(size_t bytes) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+void* take_pinned(size_t cls) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_free_pinned.find(cls);
+    if (it != g_free_pinned.end()) {
+      void* p = it->second;
+      g_free_pinned.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, cls, cudaHostAllocPortable) != cudaSuccess) return nullptr;
   return p;
+}
+
+void give_pinned(void* p, size_t cls) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_free_pinned.emplace(cls, p);
 }
 
 // Per device: a non-blocking stream for staging and freeing, and a memory pool that keeps
@@ -187,6 +258,10 @@ struct pim_instance {
   uint32_t* d_best_bits = nullptr;
   uint32_t* d_cur_bits = nullptr;
   bool has_results = false;
+  size_t res_bytes = 0;      // size of the d_res block
+  char* h_res = nullptr;     // pinned copy of d_res (PIM_RESULTS_TO_HOST)
+  size_t h_res_cap = 0;
+  bool h_res_valid = false;  // the last run copied its results into h_res
   cudaEvent_t done = nullptr;
   uint64_t ticket = 0;
   std::shared_ptr<LaunchTimer> timer;
@@ -208,6 +283,7 @@ void free_results(pim_instance* p) {
 int ensure_results(pim_instance* p, int R, cudaStream_t st) {
   if (R <= p->R_cap) return PIM_OK;
   free_results(p);
+  p->h_res_valid = false;
   const size_t bits = static_cast<size_t>(R) * p->words * sizeof(uint32_t);
   const size_t scal = align256(static_cast<size_t>(R) * 24);
   void* d = nullptr;
@@ -220,16 +296,18 @@ int ensure_results(pim_instance* p, int R, cudaStream_t st) {
   p->d_best_bits = reinterpret_cast<uint32_t*>(p->d_res + scal);
   p->d_cur_bits = reinterpret_cast<uint32_t*>(p->d_res + scal + align256(bits));
   p->R_cap = R;
+  p->res_bytes = scal + 2 * align256(bits);
   return PIM_OK;
 }
 
+// After a run's completion event: the mirror holds the error bits as of that run's end.
 int check_device_errors(int dev) {
-  int* w = device_error_word(dev);
+  ErrWord* w = error_word(dev);
   if (!w) return PIM_OK;
-  int h = 0;
-  CK(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost), "reading device error word");
+  const int h = *static_cast<volatile int*>(w->h);
   if (h != 0) {
-    cudaMemset(w, 0, sizeof(int));
+    cudaMemset(w->d, 0, sizeof(int));
+    *static_cast<volatile int*>(w->h) = 0;
     if (h & kDevErrTimeout) return fail(PIM_ERR_TIMEOUT, "a device-side bounded wait gave up");
     return fail(PIM_ERR_CUDA, "device error bits 0x%x", h);
   }
@@ -521,9 +599,9 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
                              ctx->staging)) != cudaSuccess)
       return bail(e, "upload h");
   }
-  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+  if ((e = take_event(p->device, &p->done)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
-  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess)
+  if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
   if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
   *out = p;
@@ -643,9 +721,9 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging)) !=
       cudaSuccess)
     return bail(e, "stage J image");
-  if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+  if ((e = take_event(p->device, &p->done)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
-  if ((e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess)
+  if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
   if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
   *out = p;
@@ -953,7 +1031,7 @@ int check_batch(pim_instance* const* insts, int count, const int* replicas, int 
                 int sweeps, const double* targets, int flags, bool check_steps) {
   if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
   if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
-  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG))
+  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG | PIM_RESULTS_TO_HOST))
     return fail(PIM_ERR_INVALID, "anneal: unknown flags");
   const bool cont = (flags & PIM_CONTINUE) != 0;
   const bool ref = (flags & PIM_PATH_FP32REF) != 0;
@@ -1180,8 +1258,28 @@ int prepare_instances(pim_instance* const* insts, int count, const int* replicas
 }
 
 int finish_run(pim_instance* const* insts, int count, const int* replicas,
-               const std::shared_ptr<LaunchTimer>& timer, cudaStream_t st) {
+               const std::shared_ptr<LaunchTimer>& timer, cudaStream_t st, bool to_host) {
+  for (int k = 0; k < count && to_host; ++k) {
+    pim_instance* p = insts[k];
+    if (p->h_res_cap < p->res_bytes) {
+      // the previous block may still be the target of an earlier run's copy
+      if (p->h_res) {
+        CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
+        give_pinned(p->h_res, p->h_res_cap);
+      }
+      p->h_res_cap = pinned_class(p->res_bytes);
+      p->h_res = static_cast<char*>(take_pinned(p->h_res_cap));
+      if (!p->h_res) {
+        p->h_res_cap = 0;
+        return fail(PIM_ERR_NOMEM, "pinned results buffer of %zu bytes", p->res_bytes);
+      }
+    }
+    CK(cudaMemcpyAsync(p->h_res, p->d_res, p->res_bytes, cudaMemcpyDeviceToHost, st), "results to host");
+  }
+  ErrWord* w = error_word(insts[0]->device);
+  if (w) CK(cudaMemcpyAsync(w->h, w->d, sizeof(int), cudaMemcpyDeviceToHost, st), "error word mirror");
   for (int k = 0; k < count; ++k) {
+    insts[k]->h_res_valid = to_host;
     insts[k]->R = replicas[k];
     insts[k]->has_results = true;
     insts[k]->timer = timer;
@@ -1218,7 +1316,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
                     d_err, nullptr, st);
   if (rc != PIM_OK) return rc;
   CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
-  return finish_run(insts, count, replicas, timer, st);
+  return finish_run(insts, count, replicas, timer, st, (flags & PIM_RESULTS_TO_HOST) != 0);
 }
 
 }  // namespace
@@ -1347,7 +1445,8 @@ PIM_API int pim_batch_create(pim_batch** out, pim_instance* const* insts, int co
 PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, int run_flags,
                           void* cuda_stream) {
   if (!b) return fail(PIM_ERR_INVALID, "pim_batch_run: batch is NULL");
-  if (run_flags & ~PIM_CONTINUE) return fail(PIM_ERR_INVALID, "pim_batch_run: run flags take only PIM_CONTINUE");
+  if (run_flags & ~(PIM_CONTINUE | PIM_RESULTS_TO_HOST))
+    return fail(PIM_ERR_INVALID, "pim_batch_run: run flags take only PIM_CONTINUE, PIM_RESULTS_TO_HOST");
   const int count = static_cast<int>(b->insts.size());
   int rc = check_batch(b->insts.data(), count, b->replicas.data(), t_begin, sweeps, b->targets.data(),
                        b->flags | run_flags, true);
@@ -1410,7 +1509,8 @@ PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, 
                       false, b->timer.get(), d_err, &b->launches, st);
     if (rc != PIM_OK) return rc;
   }
-  return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st);
+  return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st,
+                    (run_flags & PIM_RESULTS_TO_HOST) != 0);
 }
 
 PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_graph) {
@@ -1431,7 +1531,8 @@ PIM_API int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin,
                                   uint64_t seed, uint32_t instance_id, const int8_t* init_spins,
                                   double target_energy, int flags, void* cuda_stream) {
   if (!inst) return fail(PIM_ERR_INVALID, "pim_anneal_sequential: instance is NULL");
-  if (flags & ~PIM_CONTINUE) return fail(PIM_ERR_INVALID, "pim_anneal_sequential: flags take only PIM_CONTINUE");
+  if (flags & ~(PIM_CONTINUE | PIM_RESULTS_TO_HOST))
+    return fail(PIM_ERR_INVALID, "pim_anneal_sequential: flags take only PIM_CONTINUE, PIM_RESULTS_TO_HOST");
   if (inst->real)
     return fail(PIM_ERR_UNSUPPORTED, "pim_anneal_sequential: integer couplings only");
   // (the plain-path flag only skips the fused kernel's field-range check)
@@ -1476,7 +1577,7 @@ PIM_API int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin,
   CK(launch_sequential(L, st), "sequential kernel");
   CK(cudaEventRecord(timer->stop, st), "cudaEventRecord");
   CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
-  return finish_run(&inst, 1, &replicas, timer, st);
+  return finish_run(&inst, 1, &replicas, timer, st, (flags & PIM_RESULTS_TO_HOST) != 0);
 }
 
 PIM_API int pim_sync(pim_instance* inst) {
@@ -1509,12 +1610,17 @@ PIM_API int pim_energies(pim_instance* inst, double* best_E, int32_t* best_t,
   if (rc != PIM_OK) return rc;
   // The four per-replica arrays are contiguous on the device: one copy.
   const size_t R = inst->R, cap = inst->R_cap;
-  std::vector<char> h(cap * 24);
-  CK(cudaMemcpy(h.data(), inst->d_res, cap * 24, cudaMemcpyDeviceToHost), "copy energies");
-  if (best_E) std::memcpy(best_E, h.data(), R * 8);
-  if (final_E) std::memcpy(final_E, h.data() + cap * 8, R * 8);
-  if (best_t) std::memcpy(best_t, h.data() + cap * 16, R * 4);
-  if (first_hit_t) std::memcpy(first_hit_t, h.data() + cap * 20, R * 4);
+  std::vector<char> hv;
+  const char* h = inst->h_res;
+  if (!inst->h_res_valid) {
+    hv.resize(cap * 24);
+    CK(cudaMemcpy(hv.data(), inst->d_res, cap * 24, cudaMemcpyDeviceToHost), "copy energies");
+    h = hv.data();
+  }
+  if (best_E) std::memcpy(best_E, h, R * 8);
+  if (final_E) std::memcpy(final_E, h + cap * 8, R * 8);
+  if (best_t) std::memcpy(best_t, h + cap * 16, R * 4);
+  if (first_hit_t) std::memcpy(first_hit_t, h + cap * 20, R * 4);
   return PIM_OK;
 }
 
@@ -1524,8 +1630,15 @@ int copy_state(pim_instance* inst, const uint32_t* d_bits, int8_t* out) {
   if (!inst->has_results) return fail(PIM_ERR_STATE, "state copy: no anneal has run");
   int rc = sync_instance(inst);
   if (rc != PIM_OK) return rc;
-  std::vector<uint32_t> bits(static_cast<size_t>(inst->R) * inst->words);
-  CK(cudaMemcpy(bits.data(), d_bits, bits.size() * 4, cudaMemcpyDeviceToHost), "copy state bits");
+  std::vector<uint32_t> bv;
+  const uint32_t* bits = nullptr;
+  if (inst->h_res_valid) {
+    bits = reinterpret_cast<const uint32_t*>(inst->h_res + (reinterpret_cast<const char*>(d_bits) - inst->d_res));
+  } else {
+    bv.resize(static_cast<size_t>(inst->R) * inst->words);
+    CK(cudaMemcpy(bv.data(), d_bits, bv.size() * 4, cudaMemcpyDeviceToHost), "copy state bits");
+    bits = bv.data();
+  }
   // Byte -> eight int8 spins (+1 where the bit is set, -1 elsewhere), 8 spins per lookup.
   static const std::vector<uint64_t> expand = [] {
     std::vector<uint64_t> tab(256);
@@ -1624,10 +1737,11 @@ PIM_API void pim_destroy(pim_instance* inst) {
   }
   // Blocks go back to the pool on the staging stream once the last anneal has finished.
   free_results(inst);
+  give_pinned(inst->h_res, inst->h_res_cap);  // its copies ended with the synchronised run
   pool_free_after(inst->d_slab, inst->device, inst->done);
   pool_free_after(inst->d_jf, inst->device, inst->done);
-  if (inst->done) cudaEventDestroy(inst->done);
-  if (inst->ready) cudaEventDestroy(inst->ready);
+  give_event(inst->device, inst->done);
+  give_event(inst->device, inst->ready);
   inst->sched.reset();
   delete inst;
 }

@@ -103,3 +103,50 @@ def test_batch_plan_rejects_changed_instance():
             P.pim_batch_destroy(b)
         for hd in handles:
             P.pim_destroy(hd)
+
+
+def test_results_to_host_matches_oracle_on_every_entry_point():
+    """PIM_RESULTS_TO_HOST: the getters read the pinned copy taken at the end of the run.
+    Results are bit-exact against the oracle after pim_anneal_batch, a graph-replayed batch
+    plan (replays alternating with and without the flag, so a stale host copy would show)
+    and a resumed run without the flag; the sequential loop reads the same way."""
+    P = pim()
+    F = P.PIM_RESULTS_TO_HOST
+    insts, reps = _batch([120, 333, 64], [70, 96, 40], seed0=500)
+    ids = [1, 2, 3]
+    T = 12
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, reps, T, 4, instance_ids=ids, flags=F)
+        _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, 4)
+        b = P.pim_batch_create(handles, reps, instance_ids=ids)
+        for seed, fl in ((5, F), (6, 0), (7, F), (7, 0)):
+            P.pim_batch_run(b, T, seed, run_flags=fl)
+            _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, seed)
+        P.pim_batch_destroy(b)
+        b = None
+        # first half with the host copy, second half resumed without it
+        P.pim_anneal_batch(handles, reps, T // 2, 9, instance_ids=ids, flags=F)
+        P.pim_anneal_batch(handles, reps, T - T // 2, 9, t_begin=T // 2, instance_ids=ids,
+                           flags=P.PIM_CONTINUE)
+        _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, 9)
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)
+    inst = insts[0]
+    hd = P.pim_create(inst.J, None, inst.c)
+    try:
+        P.pim_set_schedule(hd, beta, eta, 0.0)
+        P.pim_anneal_sequential(hd, 33, T, 2, instance_id=4, flags=F)
+        got = collect(hd, inst.n)
+        P.pim_anneal_sequential(hd, 33, T, 2, instance_id=4)
+        assert_same(got, collect(hd, inst.n), label="sequential host copy")
+    finally:
+        P.pim_destroy(hd)
