@@ -476,6 +476,73 @@ std::pair<int, int> first_asymmetry(const T* a, int n) {
   return {-1, -1};
 }
 
+// sum_j |row[j]| into *sum and whether some entry lies outside [-16, 16].  Byte arithmetic
+// with 16-bit partial sums (|v| <= 128, 256 of them fit) so that the loop vectorises.
+bool abs_row_sum_i8(const int8_t* row, int n, int* sum) {
+  int s = 0;
+  uint8_t out = 0;
+  for (int j0 = 0; j0 < n; j0 += 256) {
+    const int j1 = std::min(n, j0 + 256);
+    uint16_t part = 0;
+    for (int j = j0; j < j1; ++j) {
+      const uint8_t u = static_cast<uint8_t>(row[j]);
+      const uint8_t neg = static_cast<uint8_t>(-(u >> 7));  // 0xFF for negative entries
+      part += static_cast<uint8_t>((u ^ neg) - neg);        // |v| (128 for -128)
+      out |= static_cast<uint8_t>(static_cast<uint8_t>(u + 16) > 32);
+    }
+    s += part;
+  }
+  *sum = s;
+  return out != 0;
+}
+
+// Transposes an 8 x 8 byte block held as 8 words (word k = row k, byte c = column c,
+// little-endian byte order) with three rounds of masked swaps: 4x4, 2x2, then 1x1 blocks.
+void transpose_8x8_bytes(uint64_t* w) {
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t t = ((w[k] >> 32) ^ w[k + 4]) & 0x00000000FFFFFFFFull;
+    w[k] ^= t << 32;
+    w[k + 4] ^= t;
+  }
+  for (int k : {0, 1, 4, 5}) {
+    const uint64_t t = ((w[k] >> 16) ^ w[k + 2]) & 0x0000FFFF0000FFFFull;
+    w[k] ^= t << 16;
+    w[k + 2] ^= t;
+  }
+  for (int k = 0; k < 8; k += 2) {
+    const uint64_t t = ((w[k] >> 8) ^ w[k + 1]) & 0x00FF00FF00FF00FFull;
+    w[k] ^= t << 8;
+    w[k + 1] ^= t;
+  }
+}
+
+// Whether a byte matrix equals its transpose: 8 x 8 blocks of the upper triangle against the
+// transposed mirror block, the ragged edge element by element.  first_asymmetry locates
+// the mismatch when there is one.
+bool symmetric_i8(const int8_t* a, int n) {
+  const int nb = n / 8;
+  std::atomic<int> next{0};
+  std::atomic<bool> ok{true};
+  parallel_for(nb, [&](int, int) {
+    uint64_t diff = 0;
+    for (int I = next++; I < nb; I = next++)
+      for (int K = I; K < nb; ++K) {
+        uint64_t A[8], B[8];
+        for (int k = 0; k < 8; ++k) {
+          std::memcpy(&A[k], a + static_cast<size_t>(8 * I + k) * n + 8 * K, 8);
+          std::memcpy(&B[k], a + static_cast<size_t>(8 * K + k) * n + 8 * I, 8);
+        }
+        transpose_8x8_bytes(A);
+        for (int k = 0; k < 8; ++k) diff |= A[k] ^ B[k];
+      }
+    if (diff) ok = false;
+  }, 8, static_cast<size_t>(n) * n);
+  for (int i = 0; i < n && ok; ++i)
+    for (int j = std::max(8 * nb, i + 1); j < n; ++j)
+      if (a[static_cast<size_t>(i) * n + j] != a[static_cast<size_t>(j) * n + i]) return false;
+  return ok;
+}
+
 // Round a double to the nearest BF16 value (8 significant bits, ties to even) and return
 // its bit pattern: round the 52-bit double significand at bit 45 (a carry moves into the
 // exponent), then narrow to float, which is exact for finite values in float range.
@@ -653,15 +720,17 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     for (int i = i0; i < i1; ++i) {
       const int8_t* row = J8 + static_cast<size_t>(i) * n;
       long long s = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
-      for (int j = 0; j < n; ++j) {
-        const int v = row[j];
-        if ((i == j && v != 0) || v < -16 || v > 16) {
-          bad[i] = j;
-          break;
+      int sum = 0;
+      if (abs_row_sum_i8(row, n, &sum) || row[i] != 0) {
+        for (int j = 0; j < n; ++j) {  // locate the first offending entry of the row
+          const int v = row[j];
+          if ((i == j && v != 0) || v < -16 || v > 16) {
+            bad[i] = j;
+            break;
+          }
         }
-        s += v < 0 ? -v : v;
       }
-      rowsum[i] = s;
+      rowsum[i] = s + sum;
     }
   }, 64, static_cast<size_t>(n) * n);
   long long imax = 0;
@@ -674,9 +743,10 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     }
     imax = std::max(imax, rowsum[i]);
   }
-  const auto asym = first_asymmetry(J8, n);
-  if (asym.first >= 0)
+  if (!symmetric_i8(J8, n)) {
+    const auto asym = first_asymmetry(J8, n);
     return fail(PIM_ERR_INVALID, "pim_create: J is not symmetric at (%d, %d)", asym.first, asym.second);
+  }
   if (imax > (1 << 20)) return fail(PIM_ERR_INVALID, "pim_create: field range too large");
   auto* p = new (std::nothrow) pim_instance();
   if (!p) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");

@@ -77,3 +77,34 @@ def test_invalid_arguments_are_rejected_on_host(pim):
     with pytest.raises(pim.PimError) as e:
         pim.pim_poll(123456789)
     assert e.value.code == pim.PIM_ERR_INVALID
+
+
+@pytest.mark.parametrize("n", [2, 7, 8, 9, 16, 23, 64, 200, 257])
+def test_validation_finds_first_asymmetry_and_range_errors(pim, n):
+    """The host checks of integer couplings (8 x 8 block transposes, byte row sums) report
+    the first asymmetric pair in row-major order and the first out-of-range entry, at sizes
+    with and without a ragged edge; a valid matrix passes them (it then fails only where no
+    GPU is present, with a CUDA error)."""
+    import re
+    rng = np.random.default_rng(n)
+    A = rng.integers(-16, 17, size=(n, n))
+    J = np.triu(A, 1)
+    J = (J + J.T).astype(np.int8)
+    try:
+        pim.pim_destroy(pim.pim_create(J))
+    except pim.PimError as e:
+        assert e.code != pim.PIM_ERR_INVALID, str(e)
+    for _ in range(6):
+        i, j = sorted(rng.choice(n, size=2, replace=False))
+        K = J.copy()
+        K[j, i] = np.int8(K[j, i] + (1 if K[j, i] < 16 else -1))  # lower triangle: first hit is (i, j)
+        with pytest.raises(pim.PimError) as e:
+            pim.pim_create(K)
+        assert e.value.code == pim.PIM_ERR_INVALID
+        assert re.search(rf"not symmetric at \({i}, {j}\)", str(e.value)), str(e.value)
+        K = J.copy()
+        K[i, j] = K[j, i] = -17 if _ % 2 else -128
+        with pytest.raises(pim.PimError) as e:
+            pim.pim_create(K)
+        assert e.value.code == pim.PIM_ERR_INVALID
+        assert re.search(rf"\|J\[{i}\]\[{j}\]\| = {17 if _ % 2 else 128} > 16", str(e.value)), str(e.value)
