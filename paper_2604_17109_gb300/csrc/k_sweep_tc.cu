@@ -95,7 +95,11 @@ __device__ __forceinline__ uint32_t diag_chunk(uint32_t taddr, uint32_t c, uint3
   return ~((neg_hi << (W / 2)) | neg_lo) & ((1u << W) - 1u);
 }
 
-template <int NPAD, int MODE>
+// QUEUE = false: CTA b runs work item b, all sweeps.  QUEUE = true: persistent CTAs take
+// (chunk, item) segments from the launch's counter until none is left; a segment with
+// chunk c > 0 starts from the state that chunk c-1 of its item (taken earlier from the
+// counter, hence by a CTA already running) published.
+template <int NPAD, int MODE, bool QUEUE>
 __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   constexpr int kMaxSlots = NPAD / 32;  // 16-column chunks per column half
   constexpr int kWordsPerThread = kMaxSlots / 2;
@@ -116,29 +120,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   const int quad = warp & 3, half = warp >> 2;
   const int row = quad * 32 + lane;
 
-  const WorkItem wk = L.work[blockIdx.x];
-  const Problem& P = L.probs[wk.prob];
-  const int n = P.n;
-  const int imax = P.imax;
-  const int stride = MODE == kModeDiag ? kDiagEntries / 2 : P.stride_words;
-  const uint32_t* thr = MODE == kModeDiag ? P.thr_diag : P.thr;
-  const int R = P.R;
-  const uint32_t q = P.q;
-  const int rg = wk.rbase + row;
-  const bool row_valid = rg < R;
-  const bool warp_active = (wk.rbase + quad * 32) < R;
-  // Column halves split at the 16-column boundary nearest n/2.
-  const int nch = (n + 15) >> 4;
-  const int split = (n + 16) >> 5;
-  const int c0 = half == 0 ? 0 : split;
-  const int myc = half == 0 ? split : nch - split;
-  const int ksteps = (n + 31) >> 5;
-  const int mma_n = (n + 15) & ~15;
-  const int t_begin = L.t_begin, t_end = L.t_begin + L.sweeps;
   const uint32_t bar_mma = smem_u32(&bars[0]);
   const uint32_t bar_j = smem_u32(&bars[1]);
 
-  // ---- prologue: TMEM, barriers, zeroed A operand, bias, first threshold table --------
+  // ---- per-CTA set-up: tensor memory and barriers, kept across the CTA's segments -----
   if (warp == 0) {
     tmem_alloc(smem_u32(sTmem), NPAD);
     tmem_relinquish();
@@ -149,217 +134,283 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
     fence_mbar_init();
     *sAbort = 0;
   }
-  for (int k = tid; k < kTileM * NPAD / 16; k += kThreads)
-    reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
-  if (MODE == kModeBias)
-    for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.h != nullptr && k < n) ? P.h[k] : 0;
-  if (L.sweeps > 0) {
-    const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t_begin) * stride);
-    uint4* dst = reinterpret_cast<uint4*>(sT + (t_begin & 1) * SW);
-    for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
   const uint32_t tmem_warp = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+  uint32_t phase = 0, jphase = 0;
+  bool aborted = false;
+  const int nseg = QUEUE ? L.nwork * L.chunks : 1;
 
-  if (tid == 0) {
-    constexpr uint32_t kJBytes = NPAD * NPAD;
-    mbar_expect_tx(bar_j, kJBytes);
-    for (uint32_t off = 0; off < kJBytes; off += 16384)
-      bulk_g2s(smem_u32(sJ + off), P.jimg + off, 16384u < kJBytes - off ? 16384u : kJBytes - off,
-               bar_j);
-  }
-
-  // ---- per-thread replica state: 16-bit spin chunks of this thread's column half ------
-  uint32_t cur[kWordsPerThread], best[kWordsPerThread];
-  const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
-#pragma unroll
-  for (int w = 0; w < kWordsPerThread; ++w) cur[w] = 0;
-  if (row_valid) {
-#pragma unroll
-    for (int k = 0; k < kMaxSlots; ++k)
-      if (k < myc) {
-        const uint32_t v = cur_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)];
-        cur[k >> 1] |= v << ((k & 1) * 16);
-      }
-  }
-  int best_E = INT_MAX, best_t = -1, first_hit = -1;
-  const long long target = P.target;
-  const bool has_target = P.has_target != 0;
-  if (L.cont && row_valid) {
-    best_E = static_cast<int>(P.best_E[rg]);
-    best_t = P.best_t[rg];
-    first_hit = P.first_hit[rg];
-    const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
-#pragma unroll
-    for (int w = 0; w < kWordsPerThread; ++w) best[w] = 0;
-#pragma unroll
-    for (int k = 0; k < kMaxSlots; ++k)
-      if (k < myc) {
-        const uint32_t v = best_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)];
-        best[k >> 1] |= v << ((k & 1) * 16);
-      }
-  } else {
-#pragma unroll
-    for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
-  }
-
-  // Write s(t_begin) into the A operand (row = replica, K = spin).
-  if (warp_active) {
-#pragma unroll
-    for (int k = 0; k < kMaxSlots; ++k)
-      if (k < myc) {
-        const int c = c0 + k;
-        const uint32_t nb = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = fp8x16_from_bits(nb);
-      }
-  }
-  fence_proxy_async_smem();
-  __syncthreads();
-
-  const uint32_t idesc = idesc_e4m3(kTileM, mma_n);
-  const uint32_t sA_addr = smem_u32(sA), sJ_addr = smem_u32(sJ);
-  auto issue_fields = [&]() {
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
-      mma_e4m3(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
-               sw128_desc(sJ_addr + kb * (NPAD * 128) + ko), idesc, ks > 0 ? 1u : 0u);
+  for (int iter = 0; !aborted; ++iter) {
+    // ---- segment: work item, chunk and sweep range ------------------------------------
+    int seg = static_cast<int>(blockIdx.x);
+    if (QUEUE) {
+      if (tid == 0) sAbort[1] = static_cast<int>(atomicAdd(&L.ready[L.nwork], 1u));
+      __syncthreads();
+      seg = sAbort[1];
+      if (seg >= nseg) break;
+    } else if (iter > 0) {
+      break;
     }
-    mma_commit(bar_mma);
-  };
+    const int item = QUEUE ? seg % L.nwork : seg;
+    const int chunk = QUEUE ? seg / L.nwork : 0;
+    const WorkItem wk = L.work[item];
+    const Problem& P = L.probs[wk.prob];
+    const int n = P.n;
+    const int imax = P.imax;
+    const int stride = MODE == kModeDiag ? kDiagEntries / 2 : P.stride_words;
+    const uint32_t* thr = MODE == kModeDiag ? P.thr_diag : P.thr;
+    const int R = P.R;
+    const uint32_t q = P.q;
+    const int rg = wk.rbase + row;
+    const bool row_valid = rg < R;
+    const bool warp_active = (wk.rbase + quad * 32) < R;
+    // Column halves split at the 16-column boundary nearest n/2.
+    const int nch = (n + 15) >> 4;
+    const int split = (n + 16) >> 5;
+    const int c0 = half == 0 ? 0 : split;
+    const int myc = half == 0 ? split : nch - split;
+    const int ksteps = (n + 31) >> 5;
+    const int mma_n = (n + 15) & ~15;
+    const int t_begin =
+        QUEUE ? L.t_begin + static_cast<int>(static_cast<long long>(chunk) * L.sweeps / L.chunks) : L.t_begin;
+    const int t_end = QUEUE ? L.t_begin + static_cast<int>(static_cast<long long>(chunk + 1) * L.sweeps /
+                                                           L.chunks)
+                            : L.t_begin + L.sweeps;
+    const bool cont = L.cont != 0 || chunk > 0;
 
-  if (tid == 0) {
-    if (!mbar_wait_bounded(bar_j, 0, L.wait_ns)) {
-      atomicOr(L.err, kDevErrTimeout);
-      *sAbort = 1;
-    } else if (L.inject != 1) {  // injected fault: the first wait below cannot complete
-      tc_fence_after();
-      issue_fields();
-    }
-  }
-  __syncthreads();
-  bool aborted = *sAbort != 0;
-  uint32_t phase = 0;
-  // kModeBias: word index of field I is (bits of I + 1.5*2^23) - (0x4B400000 - imax).
-  const uint32_t ioff = kMagicBits - static_cast<uint32_t>(imax);
-
-  // ---- sweep loop ----------------------------------------------------------------------
-  for (int t = t_begin; t < t_end && !aborted; ++t) {
-    if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
-      atomicOr(L.err, kDevErrTimeout);
-      *sAbort = 1;
-    }
-    phase ^= 1;
-    tc_fence_after();
-    // Next step's thresholds: loaded into registers now, stored to the other table buffer
-    // after this sweep's epilogue (so the load latency overlaps the epilogue).
-    uint4 pre[kMaxPrefetch];
-    const uint4* pre_src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t + 1) * stride);
-    const bool do_pre = t + 1 < t_end;
-#pragma unroll
-    for (int j = 0; j < kMaxPrefetch; ++j) {
-      const int k = tid + j * kThreads;
-      if (do_pre && k < stride / 4) pre[j] = __ldg(pre_src + k);
-    }
-    const uint32_t* tab = sT + (t & 1) * SW;
-    // kModeDiag: byte address of entry D is 2 * (bits of D + 1.5*2^23) + this bias (mod 2^32).
-    const uint32_t diag_bias = smem_u32(tab) + 2u * (kDiagEntries / 2) - 2u * kMagicBits;
-    uint32_t nxt[kWordsPerThread];
-#pragma unroll
-    for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
-    float eacc = 0.0f;
-    if (warp_active) {
-#pragma unroll
-      for (int k = 0; k < kMaxSlots; ++k) {
-        if (k < myc) {
-          const int c = c0 + k;
-          const int valid = n - c * 16;
-          uint32_t nb;
-          if (MODE == kModeDiag) {
-            if (valid > 8) {
-              nb = diag_chunk<16>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
-              if (valid < 16) nb &= (1u << valid) - 1u;
-              *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
-                  fp8x16_from_bits(nb);
-            } else {  // last chunk with at most 8 spins: half the work
-              nb = diag_chunk<8>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
-              if (valid < 8) nb &= (1u << valid) - 1u;
-              *reinterpret_cast<uint2*>(sA + sw128_offset(row, c * 16, kTileM)) =
-                  make_uint2(fp8x4_from_bits(nb & 0xFu), fp8x4_from_bits((nb >> 4) & 0xFu));
-            }
-          } else {
-            uint32_t v[16];
-            tmem_ld16(tmem_warp + c * 16, v);
-            const PhiloxOut o0 = philox4x32_10_rk(2u * c, static_cast<uint32_t>(rg),
-                                                  static_cast<uint32_t>(t), q, L.round_keys);
-            const PhiloxOut o1 = philox4x32_10_rk(2u * c + 1u, static_cast<uint32_t>(rg),
-                                                  static_cast<uint32_t>(t), q, L.round_keys);
-            tmem_wait_ld(v);
-            const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-            const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-            nb = 0;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int hv = sH[c * 16 + e];
-              const uint32_t ib = __float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic)) + hv;
-              const uint32_t w = tab[ib - ioff];
-              const uint32_t s = (ob >> e) & 1u;
-              const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
-              const uint32_t word = rw[e >> 1];
-              const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
-              nb |= (key >= th ? 1u : 0u) << e;
-              const int term = static_cast<int>(ib - kMagicBits) + hv;
-              eacc += static_cast<float>(s ? term : -term);
-            }
-            if (valid < 16) nb &= (1u << valid) - 1u;
-            *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
-                fp8x16_from_bits(nb);
+    // The item's previous chunk publishes its state first.
+    if (QUEUE && chunk > 0) {
+      if (tid == 0) {
+        const uint64_t limit = L.wait_ns ? L.wait_ns : 2000000000ull;
+        const uint64_t w0 = global_ns();
+        while (ld_acquire_gpu(&L.ready[item]) < static_cast<uint32_t>(chunk)) {
+          if (global_ns() - w0 > limit) {
+            atomicOr(L.err, kDevErrTimeout);
+            *sAbort = 1;
+            break;
           }
-          nxt[k >> 1] |= nb << ((k & 1) * 16);
+          __nanosleep(128);
         }
       }
-    }
-    sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
-    {
-      uint4* pre_dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
-#pragma unroll
-      for (int j = 0; j < kMaxPrefetch; ++j) {
-        const int k = tid + j * kThreads;
-        if (do_pre && k < stride / 4) pre_dst[k] = pre[j];
+      __syncthreads();
+      if (*sAbort != 0) {
+        aborted = true;
+        break;
       }
     }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    aborted = *sAbort != 0;
-    if (aborted) break;
-    if (tid == 0) {
-      tc_fence_after();
-      issue_fields();  // fields of s(t+1)
+
+    // ---- segment prologue: zeroed A operand, bias, first threshold table, J image -----
+    for (int k = tid; k < kTileM * NPAD / 16; k += kThreads)
+      reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
+    if (MODE == kModeBias)
+      for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.h != nullptr && k < n) ? P.h[k] : 0;
+    if (t_end > t_begin) {
+      const uint4* src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t_begin) * stride);
+      uint4* dst = reinterpret_cast<uint4*>(sT + (t_begin & 1) * SW);
+      for (int k = tid; k < stride / 4; k += kThreads) dst[k] = __ldg(src + k);
     }
-    const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
-    const int E = MODE == kModeDiag
-                      ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
-                      : -(static_cast<int>(etot) / 2);
-    if (E < best_E) {
-      best_E = E;
-      best_t = t;
+    __syncthreads();  // the zeroed operand is complete before any row writes its spins
+    if (tid == 0) {
+      constexpr uint32_t kJBytes = NPAD * NPAD;
+      mbar_expect_tx(bar_j, kJBytes);
+      for (uint32_t off = 0; off < kJBytes; off += 16384)
+        bulk_g2s(smem_u32(sJ + off), P.jimg + off, 16384u < kJBytes - off ? 16384u : kJBytes - off,
+                 bar_j);
+    }
+
+    // ---- per-thread replica state: 16-bit spin chunks of this thread's column half ----
+    // (L2 loads: a later chunk's state was written by another CTA of this launch)
+    uint32_t cur[kWordsPerThread], best[kWordsPerThread];
+    const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
+#pragma unroll
+    for (int w = 0; w < kWordsPerThread; ++w) cur[w] = 0;
+    if (row_valid) {
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k)
+        if (k < myc) {
+          const uint32_t v = __ldcg(cur_in + static_cast<size_t>(rg) * P.words * 2 + (c0 + k));
+          cur[k >> 1] |= v << ((k & 1) * 16);
+        }
+    }
+    int best_E = INT_MAX, best_t = -1, first_hit = -1;
+    const long long target = P.target;
+    const bool has_target = P.has_target != 0;
+    if (cont && row_valid) {
+      best_E = static_cast<int>(__ldcg(P.best_E + rg));
+      best_t = __ldcg(P.best_t + rg);
+      first_hit = __ldcg(P.first_hit + rg);
+      const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) best[w] = 0;
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k)
+        if (k < myc) {
+          const uint32_t v = __ldcg(best_in + static_cast<size_t>(rg) * P.words * 2 + (c0 + k));
+          best[k >> 1] |= v << ((k & 1) * 16);
+        }
+    } else {
 #pragma unroll
       for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
     }
-    if (has_target && first_hit < 0 && E <= target) first_hit = t;
-#pragma unroll
-    for (int w = 0; w < kWordsPerThread; ++w) cur[w] = nxt[w];
-  }
 
-  // ---- energy of the final state s(t_end) ---------------------------------------------
-  if (!aborted) {
+    // Write s(t_begin) into the A operand (row = replica, K = spin).
+    if (warp_active) {
+#pragma unroll
+      for (int k = 0; k < kMaxSlots; ++k)
+        if (k < myc) {
+          const int c = c0 + k;
+          const uint32_t nb = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+          *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) = fp8x16_from_bits(nb);
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+
+    const uint32_t idesc = idesc_e4m3(kTileM, mma_n);
+    const uint32_t sA_addr = smem_u32(sA), sJ_addr = smem_u32(sJ);
+    auto issue_fields = [&]() {
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
+        mma_e4m3(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
+                 sw128_desc(sJ_addr + kb * (NPAD * 128) + ko), idesc, ks > 0 ? 1u : 0u);
+      }
+      mma_commit(bar_mma);
+    };
+
+    if (tid == 0) {
+      if (!mbar_wait_bounded(bar_j, jphase, L.wait_ns)) {
+        atomicOr(L.err, kDevErrTimeout);
+        *sAbort = 1;
+      } else if (L.inject != 1) {  // injected fault: the first wait below cannot complete
+        tc_fence_after();
+        issue_fields();
+      }
+    }
+    jphase ^= 1u;
+    __syncthreads();
+    aborted = *sAbort != 0;
+    // kModeBias: word index of field I is (bits of I + 1.5*2^23) - (0x4B400000 - imax).
+    const uint32_t ioff = kMagicBits - static_cast<uint32_t>(imax);
+
+    // ---- sweep loop ----------------------------------------------------------------------
+    for (int t = t_begin; t < t_end && !aborted; ++t) {
+      if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
+        atomicOr(L.err, kDevErrTimeout);
+        *sAbort = 1;
+      }
+      phase ^= 1;
+      tc_fence_after();
+      // Next step's thresholds: loaded into registers now, stored to the other table buffer
+      // after this sweep's epilogue (so the load latency overlaps the epilogue).
+      uint4 pre[kMaxPrefetch];
+      const uint4* pre_src = reinterpret_cast<const uint4*>(thr + static_cast<size_t>(t + 1) * stride);
+      const bool do_pre = t + 1 < t_end;
+#pragma unroll
+      for (int j = 0; j < kMaxPrefetch; ++j) {
+        const int k = tid + j * kThreads;
+        if (do_pre && k < stride / 4) pre[j] = __ldg(pre_src + k);
+      }
+      const uint32_t* tab = sT + (t & 1) * SW;
+      // kModeDiag: byte address of entry D is 2 * (bits of D + 1.5*2^23) + this bias (mod 2^32).
+      const uint32_t diag_bias = smem_u32(tab) + 2u * (kDiagEntries / 2) - 2u * kMagicBits;
+      uint32_t nxt[kWordsPerThread];
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
+      float eacc = 0.0f;
+      if (warp_active) {
+#pragma unroll
+        for (int k = 0; k < kMaxSlots; ++k) {
+          if (k < myc) {
+            const int c = c0 + k;
+            const int valid = n - c * 16;
+            uint32_t nb;
+            if (MODE == kModeDiag) {
+              if (valid > 8) {
+                nb = diag_chunk<16>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
+                if (valid < 16) nb &= (1u << valid) - 1u;
+                *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                    fp8x16_from_bits(nb);
+              } else {  // last chunk with at most 8 spins: half the work
+                nb = diag_chunk<8>(tmem_warp + c * 16, c, rg, t, q, L.round_keys, diag_bias, eacc);
+                if (valid < 8) nb &= (1u << valid) - 1u;
+                *reinterpret_cast<uint2*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                    make_uint2(fp8x4_from_bits(nb & 0xFu), fp8x4_from_bits((nb >> 4) & 0xFu));
+              }
+            } else {
+              uint32_t v[16];
+              tmem_ld16(tmem_warp + c * 16, v);
+              const PhiloxOut o0 = philox4x32_10_rk(2u * c, static_cast<uint32_t>(rg),
+                                                    static_cast<uint32_t>(t), q, L.round_keys);
+              const PhiloxOut o1 = philox4x32_10_rk(2u * c + 1u, static_cast<uint32_t>(rg),
+                                                    static_cast<uint32_t>(t), q, L.round_keys);
+              tmem_wait_ld(v);
+              const uint32_t rw[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+              const uint32_t ob = (cur[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+              nb = 0;
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int hv = sH[c * 16 + e];
+                const uint32_t ib = __float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic)) + hv;
+                const uint32_t w = tab[ib - ioff];
+                const uint32_t s = (ob >> e) & 1u;
+                const uint32_t th = s ? (w >> 16) : (w & 0xFFFFu);
+                const uint32_t word = rw[e >> 1];
+                const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+                nb |= (key >= th ? 1u : 0u) << e;
+                const int term = static_cast<int>(ib - kMagicBits) + hv;
+                eacc += static_cast<float>(s ? term : -term);
+              }
+              if (valid < 16) nb &= (1u << valid) - 1u;
+              *reinterpret_cast<uint4*>(sA + sw128_offset(row, c * 16, kTileM)) =
+                  fp8x16_from_bits(nb);
+            }
+            nxt[k >> 1] |= nb << ((k & 1) * 16);
+          }
+        }
+      }
+      sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+      {
+        uint4* pre_dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
+#pragma unroll
+        for (int j = 0; j < kMaxPrefetch; ++j) {
+          const int k = tid + j * kThreads;
+          if (do_pre && k < stride / 4) pre_dst[k] = pre[j];
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      aborted = *sAbort != 0;
+      if (aborted) break;
+      if (tid == 0) {
+        tc_fence_after();
+        issue_fields();  // fields of s(t+1)
+      }
+      const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+      const int E = MODE == kModeDiag
+                        ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
+                        : -(static_cast<int>(etot) / 2);
+      if (E < best_E) {
+        best_E = E;
+        best_t = t;
+#pragma unroll
+        for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
+      }
+      if (has_target && first_hit < 0 && E <= target) first_hit = t;
+#pragma unroll
+      for (int w = 0; w < kWordsPerThread; ++w) cur[w] = nxt[w];
+    }
+    if (aborted) break;
+
+    // ---- energy of the state s(t_end) -------------------------------------------------
     if (!mbar_wait_bounded(bar_mma, phase, L.wait_ns)) {
       atomicOr(L.err, kDevErrTimeout);
       *sAbort = 1;
     }
+    phase ^= 1u;
     tc_fence_after();
     float eacc = 0.0f;
     if (warp_active) {
@@ -416,26 +467,48 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
         P.final_E[rg] = static_cast<double>(E);
       }
     }
-  } else if (tid == 0) {
-    // An earlier wait gave up: give the in-flight MMA a bounded chance to land before the
-    // tensor memory is released.
-    mbar_wait_bounded(bar_mma, phase, L.wait_ns);
+    // Publish the state to the item's next chunk; the barrier also keeps every thread's
+    // reads of this segment's shared memory ahead of the next segment's writes.
+    __syncthreads();
+    if (QUEUE && !aborted && tid == 0 && chunk + 1 < L.chunks) {
+      __threadfence();
+      st_release_gpu(&L.ready[item], static_cast<uint32_t>(chunk + 1));
+    }
   }
 
+  if (aborted && tid == 0) {
+    // A wait gave up: give an in-flight MMA and J copy a bounded chance to land before the
+    // tensor and shared memory are released.
+    mbar_wait_bounded(bar_mma, phase, L.wait_ns);
+    mbar_wait_bounded(bar_j, jphase ^ 1u, L.wait_ns);
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, NPAD);
 }
 
-template <int NPAD, int MODE>
-cudaError_t launch_variant(const Launch& L, int blocks, cudaStream_t st) {
+// Without a queue (L.chunks == 0): one CTA per work item.  With one: `blocks` persistent
+// CTAs, the counter and ready flags zeroed first.  The queue needs no co-residency: a CTA
+// only waits for a chunk that an already running CTA took from the counter before it.
+template <int NPAD, int MODE, bool QUEUE>
+cudaError_t launch_one(const Launch& L, int blocks, cudaStream_t st) {
   const int smem = sweep_tc_smem_bytes(NPAD, MODE == kModeDiag ? kDiagEntries / 2 : L.stride_words_max) +
                    (MODE == kModeBias ? NPAD * 4 : 0);
-  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel<NPAD, MODE>,
+  cudaError_t e = cudaFuncSetAttribute(sweep_tc_kernel<NPAD, MODE, QUEUE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  sweep_tc_kernel<NPAD, MODE><<<blocks, kThreads, smem, st>>>(L);
+  if (QUEUE) {
+    e = cudaMemsetAsync(L.ready, 0, (static_cast<size_t>(L.nwork) + 1) * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+  }
+  sweep_tc_kernel<NPAD, MODE, QUEUE><<<blocks, kThreads, smem, st>>>(L);
   return cudaGetLastError();
+}
+
+template <int NPAD, int MODE>
+cudaError_t launch_variant(const Launch& L, int blocks, cudaStream_t st) {
+  return L.chunks > 0 ? launch_one<NPAD, MODE, true>(L, blocks, st)
+                      : launch_one<NPAD, MODE, false>(L, blocks, st);
 }
 
 }  // namespace

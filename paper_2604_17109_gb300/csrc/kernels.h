@@ -37,7 +37,8 @@ cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int ma
                              const int8_t* d_init, uint32_t key_lo, uint32_t key_hi,
                              cudaStream_t st);
 
-// Fused tensor-core sweep kernel (n <= 256).
+// Fused tensor-core sweep kernel (n <= 256): `blocks` CTAs, one per work item, or, when
+// L.chunks > 0, persistent CTAs that take (chunk, item) segments from a queue.
 cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
                             bool diag);
 int sweep_tc_smem_bytes(int npad, int stride_words_max);

@@ -76,6 +76,12 @@ struct Launch {
   uint64_t wait_ns;        // limit of every device-side wait (0 = 2 s)
   int inject;              // fault injection for tests: 1 = skip the first field MMA
   unsigned int* next;      // persistent kernels: global unit counter (zeroed per launch)
+  // Fused kernel, chunked queue (chunks > 0): every work item's sweeps are cut into
+  // `chunks` consecutive shares; persistent CTAs take (chunk, item) segments in the order
+  // q = chunk * nwork + item from ready[nwork] and hand an item's state on through
+  // ready[item] = chunks done.  ready holds nwork + 1 words, zeroed per launch.
+  int chunks;
+  unsigned int* ready;
 };
 
 // Launch of the large-N kernel: one instance, all sweeps, cooperative grid of

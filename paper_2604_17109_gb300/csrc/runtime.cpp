@@ -1092,6 +1092,7 @@ struct BatchPlan {
   std::vector<WorkItem> work[kGroups];
   int maxR = 0, max_words = 0, stride_max = 4;
   size_t work_off[kGroups] = {};
+  size_t ready_off[kGroups] = {};  // fused groups: chunked-queue counter and ready flags
   size_t init_off = 0, init_bytes = 0, counters_off = 0, total = 0;
   size_t big_scratch = 0;  // largest scratch one large-N launch of this batch needs
 };
@@ -1130,6 +1131,14 @@ int check_batch(pim_instance* const* insts, int count, const int* replicas, int 
       return fail(PIM_ERR_INVALID, "anneal: target %d not finite", k);
   }
   return PIM_OK;
+}
+
+// Streaming multiprocessors of the current device.
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms);
 }
 
 // Host side of a batch: descriptors (instances must have their result buffers), routing,
@@ -1206,6 +1215,11 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
   for (int g = 0; g < kGroups; ++g) {
     B.work_off[g] = off;
     off += B.work[g].size() * sizeof(WorkItem);
+    if (g < 4 && !B.work[g].empty()) {
+      off = align256(off);
+      B.ready_off[g] = off;
+      off += (B.work[g].size() + 1) * sizeof(unsigned int);
+    }
   }
   B.init_off = align256(off);
   B.init_bytes = init_bytes;
@@ -1282,6 +1296,20 @@ int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instanc
       L.wait_ns = g_wait_ns.load();
       L.inject = g_inject.load();
       L.next = reinterpret_cast<unsigned int*>(d_buf + B.counters_off);
+      int blocks = L.nwork;
+      if (g < 4) {
+        // More units than the two CTAs per SM that run at once: cut every unit's sweeps into
+        // chunks and let persistent CTAs take them from a queue, so that no SM idles or
+        // runs a lone CTA while others finish a last partial wave (about kQueueDepth
+        // segments per CTA bound the imbalance at the end to a small share of the run).
+        constexpr int kQueueDepth = 24;
+        const int ctas = 2 * device_sms();
+        if (L.nwork > ctas && sweeps > 0) {
+          L.chunks = std::min(sweeps, (kQueueDepth * ctas + L.nwork - 1) / L.nwork);
+          L.ready = reinterpret_cast<unsigned int*>(d_buf + B.ready_off[g]);
+          blocks = ctas;
+        }
+      }
       if (g == kMidGroup) {
         const int blocks = std::min(L.nwork, sweep_mid_max_blocks());
         if (blocks < 1) return fail(PIM_ERR_CUDA, "anneal: mid-N kernel cannot be resident");
@@ -1289,7 +1317,7 @@ int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instanc
       } else if (g >= 4) {
         CK(launch_sweep_float(L, (g & 1) ? 256 : 128, L.nwork, st), "real-valued sweep kernel");
       } else {
-        CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, L.nwork, st, g < 2), "fused sweep kernel");
+        CK(launch_sweep_tc(L, (g & 1) ? 256 : 128, blocks, st, g < 2), "fused sweep kernel");
       }
       ++nl;
     }

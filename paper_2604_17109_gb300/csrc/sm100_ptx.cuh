@@ -50,6 +50,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Flag handshake between CTAs of one launch (gpu scope).
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const unsigned int* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Wait for the phase with the given parity; gives up after `limit_ns` (0 = 2 s) and
 // returns false.
 static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,

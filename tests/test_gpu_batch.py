@@ -150,3 +150,50 @@ def test_results_to_host_matches_oracle_on_every_entry_point():
         assert_same(got, collect(hd, inst.n), label="sequential host copy")
     finally:
         P.pim_destroy(hd)
+
+
+def test_chunked_queue_matches_oracle():
+    """More fused units than the two CTAs per SM that run at once: persistent CTAs take
+    (chunk, unit) segments from a queue, each chunk after the first starting from the state
+    its predecessor (run by another CTA) published.  Units of three sizes on one kernel
+    variant; every unit equals the oracle after pim_anneal_batch, and sampled units after
+    graph-replayed batch-plan runs of 1 and 2 sweeps (chunks down to one sweep) and a
+    PIM_CONTINUE resumption to the full schedule."""
+    import torch
+    P = pim()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    K = int(2.5 * 2 * sms) + 3
+    sizes = [64, 40, 100]
+    insts = [(sk_pm1 if k % 2 else maxcut_er)(sizes[k % 3], 900 + k) for k in range(K)]
+    reps = [128] * K
+    ids = list(range(K))
+    T = 12
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    b = None
+    sample = list(range(0, K, 9)) + [K - 1]
+
+    def pick(xs):
+        return [xs[k] for k in sample]
+
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, reps, T, 21, instance_ids=ids)
+        _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, 21)
+        b = P.pim_batch_create(handles, reps, instance_ids=ids)
+        P.pim_batch_run(b, 1, 23)
+        _check_all(P, pick(handles), pick(insts), pick(reps), pick(ids), beta, eta, 0.5, 23,
+                   sweeps=1)
+        P.pim_batch_run(b, 2, 22)
+        _check_all(P, pick(handles), pick(insts), pick(reps), pick(ids), beta, eta, 0.5, 22,
+                   sweeps=2)
+        P.pim_batch_run(b, T - 2, 22, t_begin=2, run_flags=P.PIM_CONTINUE)
+        _check_all(P, pick(handles), pick(insts), pick(reps), pick(ids), beta, eta, 0.5, 22)
+        assert P.pim_batch_info(b)["uses_graph"]
+    finally:
+        if b is not None:
+            P.pim_batch_destroy(b)
+        for hd in handles:
+            P.pim_destroy(hd)
