@@ -12,7 +12,7 @@ namespace pim {
 // value J_ij; zero outside n x n.  One thread per image byte.
 // ---------------------------------------------------------------------------------------
 __global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int npad, int diag,
-                                       uint8_t* __restrict__ img) {
+                                       int e5m2, uint8_t* __restrict__ img) {
   const uint32_t off = blockIdx.x * blockDim.x + threadIdx.x;
   if (off >= static_cast<uint32_t>(npad) * npad) return;
   const uint32_t block_bytes = static_cast<uint32_t>(npad) * 128u;
@@ -25,17 +25,17 @@ __global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int 
   uint8_t v = 0;
   if (i < n && j < n) {
     const int val = i == j ? diag : J[static_cast<size_t>(i) * n + j];
-    const __nv_fp8_storage_t e =
-        __nv_cvt_float_to_fp8(static_cast<float>(val), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8_storage_t e = __nv_cvt_float_to_fp8(static_cast<float>(val), __NV_SATFINITE,
+                                                       e5m2 ? __NV_E5M2 : __NV_E4M3);
     v = static_cast<uint8_t>(e);
   }
   img[off] = v;
 }
 
 cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool e5m2) {
   const uint32_t total = static_cast<uint32_t>(npad) * npad;
-  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, diag, d_img);
+  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, diag, e5m2 ? 1 : 0, d_img);
   return cudaGetLastError();
 }
 
@@ -106,27 +106,27 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
 // unreachable entries are zero.
 // ---------------------------------------------------------------------------------------
 __global__ void diag_thresholds_kernel(const uint32_t* __restrict__ thr, int imax, int stride_words,
-                                       uint16_t* __restrict__ out) {
+                                       int K, uint16_t* __restrict__ out) {
   const int t = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0 .. 1023
-  if (k >= 1024) return;
-  const int D = k - 512;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;  // 0 .. 4K-1
+  if (k >= 4 * K) return;
+  const int D = k - 2 * K;
   uint16_t v = 0;
   if (D != 0) {
     const bool up = D > 0;
-    const int I = D - (up ? 256 : -256);
+    const int I = D - (up ? K : -K);
     if (I >= -imax && I <= imax) {
       const uint32_t w = thr[static_cast<size_t>(t) * stride_words + (I + imax)];
       v = static_cast<uint16_t>(up ? (w >> 16) : (w & 0xFFFFu));
     }
   }
-  out[static_cast<size_t>(t) * 1024 + k] = v;
+  out[static_cast<size_t>(t) * 4 * K + k] = v;
 }
 
 cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
-                                   uint32_t* d_thr_diag, cudaStream_t st) {
-  dim3 grid(1024 / 256, steps);
-  diag_thresholds_kernel<<<grid, 256, 0, st>>>(d_thr, imax, stride_words,
+                                   int K, uint32_t* d_thr_diag, cudaStream_t st) {
+  dim3 grid(4 * K / 256, steps);
+  diag_thresholds_kernel<<<grid, 256, 0, st>>>(d_thr, imax, stride_words, K,
                                                reinterpret_cast<uint16_t*>(d_thr_diag));
   return cudaGetLastError();
 }

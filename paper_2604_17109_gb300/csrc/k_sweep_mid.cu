@@ -51,10 +51,12 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, uint64
   return mbar_try_wait(bar, parity) || mbar_wait_sleep(bar, parity, limit_ns);
 }
 
-// 32 spins (bits) -> their 32 FP8 +-1 bytes in one row of the A image.
-__device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint32_t bits) {
-  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col, 128)) = fp8x16_from_bits(bits & 0xFFFFu);
-  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col + 16, 128)) = fp8x16_from_bits(bits >> 16);
+// 32 spins (bits) -> their 32 FP8 +-1 bytes in one row of the A image (neg: the bytes of -1
+// in the unit's format).
+__device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint32_t bits,
+                                            uint32_t neg) {
+  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col, 128)) = fp8x16_from_bits(bits & 0xFFFFu, neg);
+  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col + 16, 128)) = fp8x16_from_bits(bits >> 16, neg);
 }
 
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: integer D in the low mantissa bits
@@ -90,6 +92,38 @@ __device__ __forceinline__ uint32_t bias_chunk16(const uint32_t (&v)[16], const 
   }
   sum_all += sa;
   sum_up += su;
+  return ~((neg_hi << 8) | neg_lo) & 0xFFFFu;
+}
+
+// Sixteen spins of one replica, diagonal-encoded image (D = I + dk s, |I| < dk, h = 0): the
+// 16-bit threshold of (s, I) is the table entry of D at shared address 2 vb + tab_d
+// (vb = bits(D + 1.5 * 2^23), tab_d = table + 2 (2 dk) - 2 * 0x4B400000, mod 2^32), and
+// |D| = s I + dk sums to the energy.  Returns the new spins as bits 0..15.
+__device__ __forceinline__ uint32_t diag_chunk16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
+                                                 uint32_t tab_d, float& esum, bool decide) {
+  uint32_t neg_hi = 0, neg_lo = 0;
+  float e_a = 0.0f, e_b = 0.0f;
+#pragma unroll
+  for (int e = 15; e >= 0; --e) {
+    const float fd = __uint_as_float(v[e]);
+    if (decide) {
+      const uint32_t vb = __float_as_uint(__fadd_rn(fd, kMagic));
+      uint32_t m;
+      asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(vb * 2u + tab_d));
+      const uint32_t w = rw[e >> 1];
+      const uint32_t d = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+      const uint32_t diff = d + m * 0xFFFFFFF0u;  // d - 16 m
+      if (e >= 8)
+        neg_hi = __funnelshift_l(diff, neg_hi, 1);
+      else
+        neg_lo = __funnelshift_l(diff, neg_lo, 1);
+    }
+    if (e & 1)
+      e_a += fabsf(fd);
+    else
+      e_b += fabsf(fd);
+  }
+  esum += e_a + e_b;
   return ~((neg_hi << 8) | neg_lo) & 0xFFFFu;
 }
 
@@ -185,6 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       }
     } else if (tid == 32) {
       // ---- MMA issuer: per sweep, wait for s(t) in the A image, then every chunk --------
+      const uint32_t idesc_u = P.e5m2 ? idesc_e5m2(128, kNT) : idesc;
       bool ok = true;
       for (int t = t_begin; t <= t_end && ok; ++t) {
         if (!wait_phase(aready, apass & 1, L.wait_ns)) {
@@ -211,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
             const uint32_t b0 = smem_u32(sRing + s * kStageBytes);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
-              mma_e4m3(tmem + b * kNT, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+              mma_e4m3(tmem + b * kNT, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc_u,
                        (kb > 0 || ks > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * s);
             ++mmas;
@@ -242,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       uint32_t* cur_io = P.cur_bits + static_cast<size_t>(rg) * words;
       uint32_t* best_io = P.best_bits + static_cast<size_t>(rg) * words;
       auto word_of = [&](int c, int w) { return c * (kNT / 32) + grp * kWordsPT + w; };
+      const uint32_t neg8 = P.e5m2 ? 0xBCBCBCBCu : 0xB8B8B8B8u;  // -1 in the unit's FP8 format
       uint32_t cur[kMaxChunks][kWordsPT], nxt[kMaxChunks][kWordsPT];
       int best_E = INT_MAX, best_t = -1, first_hit = -1;
 #pragma unroll
@@ -262,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       for (int c = 0; c < kMaxChunks; ++c)
 #pragma unroll
         for (int w = 0; w < kWordsPT; ++w)
-          if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, cur[c][w]);
+          if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, cur[c][w], neg8);
       fence_proxy_async_smem();
       bool stop = bar_sync_or(1, kEpiThreads, false);
       if (etid == 0) mbar_arrive(aready);
@@ -270,13 +306,18 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       // Problem fields in registers: the loops below store to global memory, which would
       // otherwise make the compiler reload them from the descriptor.
       const uint32_t q = P.q;
-      const int imax = P.imax, stride = P.stride_words;
-      const uint32_t* thr = P.thr;
+      const int dk = P.dk;
+      const int imax = P.imax, stride = dk > 0 ? 2 * dk : P.stride_words;  // words per step
+      const uint32_t* thr = dk > 0 ? P.thr_diag : P.thr;
       const long long target = P.target;
       const bool tab_smem = stride <= kTabWords;
       const bool has_target = P.has_target != 0;
       const int dg = P.diag_img ? 256 : 0;  // diagonal-encoded image: D = I + 256 s
-      const bool fast = P.h == nullptr && !P.diag_img && tab_smem;
+      const bool fast = P.h == nullptr && !P.diag_img && dk == 0 && tab_smem;
+      const bool dfast = dk > 0 && tab_smem;  // diagonal-encoded table in shared memory
+      // byte address of the entry of D: 2 (bits of D + 1.5*2^23) + tab_d (mod 2^32)
+      const uint32_t tab_d = smem_u32(sTab) + 4u * static_cast<uint32_t>(dk) - 2u * kMagicBits;
+      const int e_off = dfast ? dk * n : 0;  // sum of |D| over the n spins = sum s I + n dk
       const uint32_t tab_c = smem_u32(sTab) + 4u * static_cast<uint32_t>(imax) - 4u * kMagicBits;  // mod 2^32
       for (int t = t_begin; t <= t_end && !stop; ++t) {
         const bool last = t == t_end;
@@ -298,6 +339,37 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           tc_fence_after();
           const uint32_t ta = tmem + (static_cast<uint32_t>(quad * 32) << 16) + b * kNT + grp * kCols;
           const uint32_t blk0 = static_cast<uint32_t>((c * kNT + grp * kCols) >> 3);
+          if (dfast) {
+            // Diagonal-encoded fields, 16 columns at a time (diag_chunk16).
+            if (warp_active) {
+              float esum = 0.0f;
+#pragma unroll
+              for (int h2 = 0; h2 < kCols / 16; ++h2) {
+                uint32_t v[16];
+                tmem_ld16(ta + 16 * h2, v);
+                PhiloxOut o0{}, o1{};
+                if (!last) {
+                  o0 = philox4x32_10_rk(blk0 + 2 * h2, static_cast<uint32_t>(rg),
+                                        static_cast<uint32_t>(t), q, L.round_keys);
+                  o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, static_cast<uint32_t>(rg),
+                                        static_cast<uint32_t>(t), q, L.round_keys);
+                }
+                tmem_wait_ld(v);
+                const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+                const int w = h2 >> 1;
+                const uint32_t nb = diag_chunk16(v, rw8, tab_d, esum, !last);
+                if (h2 & 1)
+                  nxt[c][w] = (nxt[c][w] | (nb << 16)) & valid_mask(c, w);
+                else
+                  nxt[c][w] = nb;
+              }
+              eacc += static_cast<int>(esum);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+            continue;
+          }
           if (fast) {
             // 16 columns at a time: the TMEM load runs while their two Philox blocks are
             // drawn, then the decisions (bias_chunk16); the buffer is released at the end.
@@ -389,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           for (int c = 0; c < kMaxChunks; ++c)
 #pragma unroll
             for (int w = 0; w < kWordsPT; ++w)
-              if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, nxt[c][w]);
+              if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, nxt[c][w], neg8);
           fence_proxy_async_smem();
         }
         sRed[grp * 128 + row] = eacc;
@@ -405,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
         int tot = 0;
 #pragma unroll
         for (int g = 0; g < kGroups; ++g) tot += sRed[g * 128 + row];
-        const int E = -(tot / 2);
+        const int E = -((tot - e_off) / 2);
         if (E < best_E) {
           // the best state lives in the output array: written when it improves
           best_E = E;

@@ -18,9 +18,10 @@ __host__ __device__ inline uint32_t sw128_offset(int row, int k, int rows) {
 }
 
 // Staging (once per instance).
-// diag != 0 puts that value on the diagonal of the image (inside n x n).
+// diag != 0 puts that value on the diagonal of the image (inside n x n); e5m2 selects the
+// E5M2 element format (default E4M3).
 cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool e5m2 = false);
 cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st);
 
 // Decision thresholds for all steps: tau [steps][2*imax+1], eta [steps], z [4096].
@@ -28,9 +29,10 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
                               float xi, int steps, int imax, int stride_words,
                               uint32_t* d_thr, cudaStream_t st);
 
-// Re-index the thresholds by D = I + 256 s (D = -512..511, 16-bit entries); needs imax <= 255.
+// Re-index the thresholds by D = I + K s (D = -2K..2K-1, 16-bit entries, [steps][4K]); needs
+// imax < K, K a power of two >= 64.
 cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
-                                   uint32_t* d_thr_diag, cudaStream_t st);
+                                   int K, uint32_t* d_thr_diag, cudaStream_t st);
 
 // Initial spin bits: from Philox (d_init == nullptr) or from int8 +-1 spins [R][n].
 cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int max_words,

@@ -186,7 +186,7 @@ PIM_API int pim_anneal_noalloc(int n, const int8_t* J, double scale_c, int steps
   CKN(launch_stage_fp8_image(d_J, n, npad, 256, d_img, st), "stage couplings");
   CKN(launch_thresholds(d_tau, d_eta, d_z, xi, steps, kTableImax, kStrideWords, d_thr, st),
       "decision thresholds");
-  CKN(launch_diag_thresholds(d_thr, steps, kTableImax, kStrideWords, d_diag, st),
+  CKN(launch_diag_thresholds(d_thr, steps, kTableImax, kStrideWords, 256, d_diag, st),
       "diagonal thresholds");
   CKN(launch_init_bits(d_prob, 1, replicas, words, nullptr, static_cast<uint32_t>(seed),
                        static_cast<uint32_t>(seed >> 32), st),

@@ -42,6 +42,11 @@ struct Problem {
   int lut_levels;
   double target_f;         // first-hit when energy <= target_f (real couplings)
   int diag_img;            // 1: the FP8 image carries 256 on the diagonal (D = I + 256 s)
+  // Mid-N kernel, diagonal-encoded decisions: jimg carries dk on the diagonal (dk = 256:
+  // E4M3 image; dk > 256: E5M2 image, e5m2 = 1) and thr_diag holds 16-bit thresholds by
+  // D = I + dk s, [steps][4 dk].  dk = 0: general table.
+  int dk;
+  int e5m2;
 };
 
 // One unit of work of the fused sweep kernel: (problem index, first replica).

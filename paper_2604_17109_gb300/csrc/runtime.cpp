@@ -55,6 +55,16 @@ constexpr int kMaxN = 8192;        // plain path limit
 constexpr int kMaxNTensor = 256;   // fused kernel limit
 constexpr int kMaxImaxTensor = 511;
 constexpr int kMaxImaxDiag = 255;  // |I| < 256: D = I + 256 s keeps the sign of s
+constexpr int kMaxDiagK = 2048;    // widest diagonal of the E5M2 images (table of 4K entries)
+
+// Diagonal K = 2^k > imax of the wide diagonal-encoded mode (E5M2 images, 256 < K <= 2048),
+// or 0 when the field range needs none or is too wide.
+int wide_diag_k(int imax) {
+  if (imax <= kMaxImaxDiag || imax >= kMaxDiagK) return 0;
+  int K = 512;
+  while (K <= imax) K <<= 1;
+  return K;
+}
 
 // Decision thresholds of one (schedule, c, field range), shared between instances.
 struct Schedule {
@@ -63,6 +73,8 @@ struct Schedule {
   int stride_words = 0;  // per-step stride, multiple of 4 words (16 bytes)
   uint32_t* d_thr = nullptr;
   uint32_t* d_thr_diag = nullptr;  // by D = I + 256 s (only when imax <= 255)
+  uint32_t* d_thr_dk = nullptr;    // by D = I + dk s, 16-bit entries [steps][4 dk] (wide mode)
+  int dk = 0;
   // Real-valued couplings: the decision is evaluated on the device from these.
   float* d_bt = nullptr;   // b_t = fl32(beta_t c)
   float* d_eta = nullptr;  // eta_t
@@ -71,12 +83,13 @@ struct Schedule {
   int act = 0, lut = 0;
   int device = 0;
   ~Schedule() {
-    if (d_thr || d_thr_diag || d_bt) {
+    if (d_thr || d_thr_diag || d_thr_dk || d_bt) {
       int prev = 0;
       cudaGetDevice(&prev);
       cudaSetDevice(device);
       cudaFree(d_thr);
       cudaFree(d_thr_diag);
+      cudaFree(d_thr_dk);
       cudaFree(d_bt);
       cudaFree(d_eta);
       cudaFree(d_z);
@@ -239,6 +252,11 @@ struct pim_instance {
   int imax = 0;  // exact max_i sum_j |J_ij| + |h_i|
   bool has_h = false;
   bool diag = false;  // image carries 256 on the diagonal (h = 0, imax <= 255)
+  // Mid-N range, h = 0, couplings exact in E5M2: a second image in E5M2 with dk5 = 2^k >
+  // the table's field bound (at least 256) on the diagonal, for the mid-N kernel's
+  // diagonal-encoded path.
+  uint8_t* d_img5 = nullptr;
+  int dk5 = 0;
   bool real = false;  // real-valued couplings: BF16 operand image, float bias
   float* d_hf = nullptr;
   char* d_slab = nullptr;   // J8 | image | bias (one pool block)
@@ -386,9 +404,18 @@ int build_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
     if ((rc = ck(cudaMalloc(&s->d_thr_diag, static_cast<size_t>(steps) * 1024 * 2),
                  "cudaMalloc diagonal thresholds")))
       return rc;
-    if ((rc = ck(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, s->d_thr_diag, st),
+    if ((rc = ck(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, 256, s->d_thr_diag, st),
                  "diagonal threshold kernel")))
       return rc;
+  }
+  if (const int K = wide_diag_k(imax)) {
+    if ((rc = ck(cudaMalloc(&s->d_thr_dk, static_cast<size_t>(steps) * 4 * K * 2),
+                 "cudaMalloc wide diagonal thresholds")))
+      return rc;
+    if ((rc = ck(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, K, s->d_thr_dk, st),
+                 "wide diagonal threshold kernel")))
+      return rc;
+    s->dk = K;
   }
   if ((rc = ck(cudaStreamSynchronize(st), "threshold build"))) return rc;
   cleanup();
@@ -476,23 +503,28 @@ std::pair<int, int> first_asymmetry(const T* a, int n) {
   return {-1, -1};
 }
 
-// sum_j |row[j]| into *sum and whether some entry lies outside [-16, 16].  Byte arithmetic
-// with 16-bit partial sums (|v| <= 128, 256 of them fit) so that the loop vectorises.
-bool abs_row_sum_i8(const int8_t* row, int n, int* sum) {
+// sum_j |row[j]| into *sum and whether some entry lies outside [-16, 16]; *not_e5m2 is set
+// when some |entry| in 9..16 is odd (9, 11, 13, 15 have no exact E5M2 encoding).  Byte
+// arithmetic with 16-bit partial sums (|v| <= 128, 256 of them fit) so that the loop
+// vectorises.
+bool abs_row_sum_i8(const int8_t* row, int n, int* sum, bool* not_e5m2) {
   int s = 0;
-  uint8_t out = 0;
+  uint8_t out = 0, odd = 0;
   for (int j0 = 0; j0 < n; j0 += 256) {
     const int j1 = std::min(n, j0 + 256);
     uint16_t part = 0;
     for (int j = j0; j < j1; ++j) {
       const uint8_t u = static_cast<uint8_t>(row[j]);
       const uint8_t neg = static_cast<uint8_t>(-(u >> 7));  // 0xFF for negative entries
-      part += static_cast<uint8_t>((u ^ neg) - neg);        // |v| (128 for -128)
+      const uint8_t a = static_cast<uint8_t>((u ^ neg) - neg);  // |v| (128 for -128)
+      part += a;
       out |= static_cast<uint8_t>(static_cast<uint8_t>(u + 16) > 32);
+      odd |= static_cast<uint8_t>((a > 8) & a);
     }
     s += part;
   }
   *sum = s;
+  *not_e5m2 = (odd & 1) != 0;
   return out != 0;
 }
 
@@ -716,12 +748,14 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   // row sums of |J| + |h| (the field bound); then the symmetry check.
   std::vector<long long> rowsum(n, 0);
   std::vector<int> bad(n, -1);
+  std::vector<uint8_t> no_e5m2(n, 0);
   parallel_for(n, [&](int i0, int i1) {
     for (int i = i0; i < i1; ++i) {
       const int8_t* row = J8 + static_cast<size_t>(i) * n;
       long long s = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
       int sum = 0;
-      if (abs_row_sum_i8(row, n, &sum) || row[i] != 0) {
+      bool ne = false;
+      if (abs_row_sum_i8(row, n, &sum, &ne) || row[i] != 0) {
         for (int j = 0; j < n; ++j) {  // locate the first offending entry of the row
           const int v = row[j];
           if ((i == j && v != 0) || v < -16 || v > 16) {
@@ -731,6 +765,7 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
         }
       }
       rowsum[i] = s + sum;
+      no_e5m2[i] = ne ? 1 : 0;
     }
   }, 64, static_cast<size_t>(n) * n);
   long long imax = 0;
@@ -772,9 +807,14 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if (!ctx) return bail(cudaErrorMemoryAllocation, "device context");
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t img = static_cast<size_t>(p->npad) * p->npad;
+  bool e5m2_exact = true;
+  for (int i = 0; i < n; ++i) e5m2_exact &= no_e5m2[i] == 0;
+  if (n > kMaxNTensor && p->npad <= sweep_mid_max_npad() && !p->has_h && e5m2_exact)
+    p->dk5 = table_imax(p) <= kMaxImaxDiag ? 256 : wide_diag_k(table_imax(p));
   const size_t o_img = align256(nn), o_h = o_img + align256(img);
+  const size_t o_img5 = o_h + align256(n * sizeof(int32_t));
   void* slab = nullptr;
-  if ((e = pool_alloc(&slab, o_h + align256(n * sizeof(int32_t)), p->device, ctx->staging)) != cudaSuccess)
+  if ((e = pool_alloc(&slab, o_img5 + (p->dk5 ? align256(img) : 0), p->device, ctx->staging)) != cudaSuccess)
     return bail(e, "allocating J");
   p->d_slab = static_cast<char*>(slab);
   p->d_J8 = reinterpret_cast<int8_t*>(p->d_slab);
@@ -791,6 +831,12 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging)) !=
       cudaSuccess)
     return bail(e, "stage J image");
+  if (p->dk5) {
+    p->d_img5 = reinterpret_cast<uint8_t*>(p->d_slab + o_img5);
+    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->dk5, p->d_img5, ctx->staging, true)) !=
+        cudaSuccess)
+      return bail(e, "stage E5M2 J image");
+  }
   if ((e = take_event(p->device, &p->done)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
@@ -860,9 +906,17 @@ int build_fixed_schedule(std::shared_ptr<Schedule>& out, int steps, const float*
   CK(cudaMemcpy(s->d_thr, words.data(), words.size() * 4, cudaMemcpyHostToDevice), "upload thresholds");
   if (imax <= kMaxImaxDiag) {
     CK(cudaMalloc(&s->d_thr_diag, static_cast<size_t>(steps) * 1024 * 2), "cudaMalloc diagonal thresholds");
-    CK(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, s->d_thr_diag, nullptr),
+    CK(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, 256, s->d_thr_diag, nullptr),
        "diagonal threshold kernel");
     CK(cudaDeviceSynchronize(), "diagonal threshold kernel");
+  }
+  if (const int K = wide_diag_k(imax)) {
+    CK(cudaMalloc(&s->d_thr_dk, static_cast<size_t>(steps) * 4 * K * 2),
+       "cudaMalloc wide diagonal thresholds");
+    CK(launch_diag_thresholds(s->d_thr, steps, imax, s->stride_words, K, s->d_thr_dk, nullptr),
+       "wide diagonal threshold kernel");
+    CK(cudaDeviceSynchronize(), "wide diagonal threshold kernel");
+    s->dk = K;
   }
   out = s;
   return PIM_OK;
@@ -1189,6 +1243,25 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
   if (!ref) {
     const int rc = route_batch(insts, replicas, count, flags, B.route);
     if (rc != PIM_OK) return rc;
+  }
+  // Mid-N units decide from the diagonal-encoded image when the instance has one: the
+  // E4M3 image with 256 on the diagonal, or the E5M2 image with dk5 and its schedule's table.
+  for (int k = 0; k < count && !ref; ++k) {
+    if (B.route[k] != kMid) continue;
+    const pim_instance* p = insts[k];
+    Problem& P = B.probs[k];
+    if (p->diag && p->sched->d_thr_diag) {
+      P.dk = 256;
+    } else if (p->d_img5) {
+      const uint32_t* tab = p->dk5 == 256 ? p->sched->d_thr_diag
+                                          : (p->sched->dk == p->dk5 ? p->sched->d_thr_dk : nullptr);
+      if (tab) {
+        P.jimg = p->d_img5;
+        P.thr_diag = tab;
+        P.dk = p->dk5;
+        P.e5m2 = 1;
+      }
+    }
   }
   for (auto& w : B.work) w.clear();
   for (int k = 0; k < count && !ref; ++k) {

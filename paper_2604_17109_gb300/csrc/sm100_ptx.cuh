@@ -168,6 +168,11 @@ __device__ __forceinline__ uint32_t idesc_e4m3(int m, int n) {
   return (1u << 4) | (0u << 7) | (0u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
          (static_cast<uint32_t>(m >> 4) << 24);
 }
+// Same shape, A and B both E5M2 (format code 1).
+__device__ __forceinline__ uint32_t idesc_e5m2(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
@@ -226,6 +231,15 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[16]) {
 // multiply moves bit j to bit 8j+7 (the sign bit of byte j) without carries.
 __device__ __forceinline__ uint32_t fp8x4_from_bits(uint32_t nib) {
   return ((nib * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u;
+}
+// Four spins as FP8 +-1 bytes of either format: neg = the bytes of -1 (E4M3 0xB8, E5M2 0xBC)
+// repeated; a set bit clears the sign.
+__device__ __forceinline__ uint32_t fp8x4_from_bits(uint32_t nib, uint32_t neg) {
+  return ((nib * 0x10204080u) & 0x80808080u) ^ neg;
+}
+__device__ __forceinline__ uint4 fp8x16_from_bits(uint32_t nb, uint32_t neg) {
+  return make_uint4(fp8x4_from_bits(nb & 0xFu, neg), fp8x4_from_bits((nb >> 4) & 0xFu, neg),
+                    fp8x4_from_bits((nb >> 8) & 0xFu, neg), fp8x4_from_bits((nb >> 12) & 0xFu, neg));
 }
 
 __device__ __forceinline__ uint4 fp8x16_from_bits(uint32_t nb) {

@@ -37,6 +37,12 @@ CASES = [
     ("sk", 1000, 100, 8, 12),   # largest mid-N image (npad 1024), ragged
     ("maxcut", 1024, 130, 6, 13),  # exactly npad 1024
     ("sk", 1025, 64, 4, 15),    # past the mid-N limit: large-N kernel on every path
+    # mid-N diagonal-encoded decisions from an E5M2 image with 2^k > field bound on the
+    # diagonal: 256 (Max-Cut N = 300), 2048 (couplings +-2, N = 600); couplings with an odd
+    # |J| > 8 have no E5M2 encoding and take the general table
+    ("maxcut", 300, 64, 12, 18),
+    ("sk2", 600, 130, 10, 16),
+    ("sk9", 400, 96, 10, 17),
 ]
 
 
@@ -44,6 +50,12 @@ def _inst(kind, n, seed):
     if kind == "sk2":
         base = sk_pm1(n, seed)
         return Instance("sk", n, (2 * base.J).astype(np.int8), base.h, base.c / 2, seed)
+    if kind == "sk9":
+        base = sk_pm1(n, seed)
+        J = base.J.astype(np.int8).copy()
+        i = np.arange(0, n - 1, 7)
+        J[i, i + 1] = J[i + 1, i] = 9 * J[i, i + 1]
+        return Instance("sk", n, J, base.h, base.c, seed)
     return sk_pm1(n, seed) if kind == "sk" else maxcut_er(n, seed)
 
 
