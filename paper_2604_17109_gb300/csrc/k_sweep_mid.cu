@@ -12,8 +12,8 @@
 //            128 output spins; chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one
 //            of four TMEM buffers (tcgen05.mma kind::f8f6f4), so the MMAs of chunk c+1 run
 //            while the epilogue decides chunk c;
-//   decision 8 epilogue warps (4 TMEM lane quadrants x 2 groups of 64 columns): each
-//            thread owns one replica and 64 spins of every chunk, keeps their old / new
+//   decision 16 epilogue warps (4 TMEM lane quadrants x 4 groups of 32 columns): each
+//            thread owns one replica and 32 spins of every chunk, keeps their old / new
 //            bits in registers, draws the Philox blocks and looks the threshold up in the
 //            step's table at I = D + h; after the last chunk it writes the new spins into
 //            the A image (all MMAs of the sweep have completed by then);
@@ -35,7 +35,7 @@ constexpr int kMaxChunks = kMaxNpad / kNT;
 constexpr int kStages = 4;                  // coupling ring depth
 constexpr int kBufs = 4;                    // TMEM accumulators of kNT columns
 constexpr int kTabWords = 4096;             // threshold table of one step in shared memory
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kGroups = kEpiWarps / 4;      // column groups per chunk
 constexpr int kCols = kNT / kGroups;        // columns of a chunk per epilogue thread
 constexpr int kWordsPT = kCols / 32;        // 32-bit spin words per thread and chunk
