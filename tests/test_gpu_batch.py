@@ -197,3 +197,39 @@ def test_chunked_queue_matches_oracle():
             P.pim_batch_destroy(b)
         for hd in handles:
             P.pim_destroy(hd)
+
+
+def test_chunked_queue_general_bias_variants():
+    """The chunked queue on the general-bias fused kernels (nonzero h): npad 128 (N = 100)
+    and npad 256 (N = 200) groups, each with more units than two CTAs per SM, in one batch
+    (one queue launch per group); sampled units equal the oracle."""
+    import torch
+    from workloads import Instance
+    P = pim()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_group = int(2.2 * 2 * sms) + 5
+    rng = np.random.default_rng(77)
+    insts = []
+    for k in range(2 * per_group):
+        n = 100 if k % 2 else 200
+        base = sk_pm1(n, 1200 + k)
+        h = rng.integers(-3, 4, size=n).astype(np.int32)
+        insts.append(Instance("sk", n, base.J, h, base.c, base.seed))
+    K = len(insts)
+    reps = [128] * K
+    ids = list(range(K))
+    T = 8
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(i.J, i.h, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, reps, T, 31, instance_ids=ids)
+        sample = list(range(0, K, 5)) + [K - 2, K - 1]
+        for k in sample:
+            want = oracle_run(insts[k], beta, eta, 0.5, replicas=128, seed=31, q=ids[k])
+            assert_same(collect(handles[k], insts[k].n), want, label=f"unit {k} n={insts[k].n}")
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
