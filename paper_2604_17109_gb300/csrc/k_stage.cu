@@ -172,4 +172,25 @@ cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int ma
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Gather copy: every job's block, 16 bytes per thread and step; one CTA per job in turn.
+// Results of many instances reach pinned host memory in one launch instead of one copy
+// command per instance.
+// ---------------------------------------------------------------------------------------
+__global__ void gather_copy_kernel(const CopyJob* __restrict__ jobs, int count) {
+  for (int j = blockIdx.x; j < count; j += gridDim.x) {
+    const uint4* src = static_cast<const uint4*>(jobs[j].src);
+    uint4* dst = static_cast<uint4*>(jobs[j].dst);
+    const unsigned long long n16 = jobs[j].bytes / 16;
+    for (unsigned long long i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_gather_copy(const CopyJob* d_jobs, int count, cudaStream_t st) {
+  if (count < 1) return cudaSuccess;
+  const int blocks = count < 1024 ? count : 1024;
+  gather_copy_kernel<<<blocks, 256, 0, st>>>(d_jobs, count);
+  return cudaGetLastError();
+}
+
 }  // namespace pim

@@ -34,6 +34,9 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
 cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
                                    int K, uint32_t* d_thr_diag, cudaStream_t st);
 
+// Copies every job's block (jobs in device memory).
+cudaError_t launch_gather_copy(const CopyJob* d_jobs, int count, cudaStream_t st);
+
 // Initial spin bits: from Philox (d_init == nullptr) or from int8 +-1 spins [R][n].
 cudaError_t launch_init_bits(const Problem* d_probs, int nprob, int maxR, int max_words,
                              const int8_t* d_init, uint32_t key_lo, uint32_t key_hi,

@@ -49,6 +49,14 @@ struct Problem {
   int e5m2;
 };
 
+// One block copy of a gather launch: `bytes` (a multiple of 16) from src to dst, both
+// 16-byte aligned device-visible addresses (dst may be mapped pinned host memory).
+struct CopyJob {
+  const void* src;
+  void* dst;
+  unsigned long long bytes;
+};
+
 // One unit of work of the fused sweep kernel: (problem index, first replica).
 struct WorkItem {
   int prob;

@@ -159,6 +159,14 @@ void give_event(int dev, cudaEvent_t ev) {
   g_free_events[dev].push_back(ev);
 }
 
+// Completion event of one run, shared by every instance of the run (one record per run,
+// however many instances it holds); back to the free list with its last holder.
+struct RunEvent {
+  cudaEvent_t ev = nullptr;
+  int device = 0;
+  ~RunEvent() { give_event(device, ev); }
+};
+
 // Pinned host blocks for results copied back with the run, kept in power-of-two size
 // classes and reused (page-locking memory costs far more than a small copy).
 std::mutex g_pin_mu;
@@ -181,7 +189,7 @@ void* take_pinned(size_t cls) {
     }
   }
   void* p = nullptr;
-  if (cudaHostAlloc(&p, cls, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+  if (cudaHostAlloc(&p, cls, cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) return nullptr;
   return p;
 }
 
@@ -196,6 +204,10 @@ void give_pinned(void* p, size_t cls) {
 struct DeviceCtx {
   cudaStream_t staging = nullptr;
   cudaMemPool_t pool = nullptr;
+  // Instances record their `ready` event on `staging` in the order of stage_seq, so a run
+  // waits only for the latest of its instances' events.
+  std::mutex stage_mu;
+  uint64_t stage_seq = 0;
 };
 std::mutex g_ctx_mu;
 std::map<int, DeviceCtx> g_ctx;
@@ -262,6 +274,7 @@ struct pim_instance {
   char* d_slab = nullptr;   // J8 | image | bias (one pool block)
   char* d_res = nullptr;    // results (one pool block)
   cudaEvent_t ready = nullptr;  // staging of the inputs done
+  uint64_t ready_seq = 0;       // order of `ready` on the device's staging stream
   int8_t* d_J8 = nullptr;
   uint8_t* d_img = nullptr;
   float* d_jf = nullptr;
@@ -278,9 +291,11 @@ struct pim_instance {
   bool has_results = false;
   size_t res_bytes = 0;      // size of the d_res block
   char* h_res = nullptr;     // pinned copy of d_res (PIM_RESULTS_TO_HOST)
+  void* h_res_dev = nullptr; // its device-side address (mapped pinned memory), or null
   size_t h_res_cap = 0;
   bool h_res_valid = false;  // the last run copied its results into h_res
-  cudaEvent_t done = nullptr;
+  std::shared_ptr<RunEvent> done;  // completion of the last run (shared with its batch)
+  cudaEvent_t done_ev() const { return done ? done->ev : nullptr; }
   uint64_t ticket = 0;
   std::shared_ptr<LaunchTimer> timer;
 };
@@ -288,7 +303,7 @@ struct pim_instance {
 namespace {
 
 void free_results(pim_instance* p) {
-  pool_free_after(p->d_res, p->device, p->done);
+  pool_free_after(p->d_res, p->device, p->done_ev());
   p->d_res = nullptr;
   p->d_bestE = p->d_finalE = nullptr;
   p->d_bestT = p->d_first = nullptr;
@@ -333,7 +348,7 @@ int check_device_errors(int dev) {
 }
 
 int sync_instance(pim_instance* p) {
-  if (p->done) CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
+  if (p->done) CK(cudaEventSynchronize(p->done->ev), "cudaEventSynchronize");
   return check_device_errors(p->device);
 }
 
@@ -698,11 +713,13 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
                              ctx->staging)) != cudaSuccess)
       return bail(e, "upload h");
   }
-  if ((e = take_event(p->device, &p->done)) != cudaSuccess)
-    return bail(e, "cudaEventCreate");
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
-  if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
+  {
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
+    p->ready_seq = ++ctx->stage_seq;
+  }
   *out = p;
   return PIM_OK;
 }
@@ -837,11 +854,13 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
         cudaSuccess)
       return bail(e, "stage E5M2 J image");
   }
-  if ((e = take_event(p->device, &p->done)) != cudaSuccess)
-    return bail(e, "cudaEventCreate");
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
-  if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
+  {
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    if ((e = cudaEventRecord(p->ready, ctx->staging)) != cudaSuccess) return bail(e, "cudaEventRecord");
+    p->ready_seq = ++ctx->stage_seq;
+  }
   *out = p;
   return PIM_OK;
 }
@@ -879,7 +898,7 @@ PIM_API int pim_set_schedule(pim_instance* inst, int steps, const float* beta, c
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched_cache[key] = s;
   }
-  if (inst->done) cudaEventSynchronize(inst->done);
+  if (inst->done) cudaEventSynchronize(inst->done->ev);
   inst->sched = s;
   return PIM_OK;
 }
@@ -963,7 +982,7 @@ PIM_API int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* b
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched_cache[key] = s;
   }
-  if (inst->done) cudaEventSynchronize(inst->done);
+  if (inst->done) cudaEventSynchronize(inst->done->ev);
   inst->sched = s;
   return PIM_OK;
 }
@@ -1408,13 +1427,22 @@ int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instanc
   return PIM_OK;
 }
 
+// Makes st wait for the staging of every instance (all on one device): one wait on the
+// ready event recorded last, which follows every earlier one on the staging stream.
+cudaError_t wait_staged(pim_instance* const* insts, int count, cudaStream_t st) {
+  const pim_instance* last = nullptr;
+  for (int k = 0; k < count; ++k)
+    if (!last || insts[k]->ready_seq > last->ready_seq) last = insts[k];
+  return last ? cudaStreamWaitEvent(st, last->ready, 0) : cudaSuccess;
+}
+
 // Prerequisites of a run on stream st: staged inputs, float32 couplings for the plain path,
 // result buffers for the replica counts.
 int prepare_instances(pim_instance* const* insts, int count, const int* replicas, bool ref,
                       cudaStream_t st) {
+  CK(wait_staged(insts, count, st), "cudaStreamWaitEvent");  // inputs staged
   for (int k = 0; k < count; ++k) {
     pim_instance* p = insts[k];
-    CK(cudaStreamWaitEvent(st, p->ready, 0), "cudaStreamWaitEvent");  // inputs staged
     if (ref && !p->d_jf) {  // float32 couplings of the plain path, built on first use
       void* d = nullptr;
       CK(pool_alloc(&d, static_cast<size_t>(p->n) * p->n * sizeof(float), p->device, st),
@@ -1428,33 +1456,52 @@ int prepare_instances(pim_instance* const* insts, int count, const int* replicas
   return PIM_OK;
 }
 
+// Pinned host buffer for the instance's result block (PIM_RESULTS_TO_HOST), with its device
+// address when the GPU can write it directly.
+int ensure_host_copy(pim_instance* p) {
+  if (p->h_res_cap >= p->res_bytes) return PIM_OK;
+  // the previous block may still be the target of an earlier run's copy
+  if (p->h_res) {
+    if (p->done) CK(cudaEventSynchronize(p->done->ev), "cudaEventSynchronize");
+    give_pinned(p->h_res, p->h_res_cap);
+  }
+  p->h_res_cap = pinned_class(p->res_bytes);
+  p->h_res = static_cast<char*>(take_pinned(p->h_res_cap));
+  p->h_res_dev = nullptr;
+  if (!p->h_res) {
+    p->h_res_cap = 0;
+    return fail(PIM_ERR_NOMEM, "pinned results buffer of %zu bytes", p->res_bytes);
+  }
+  if (cudaHostGetDevicePointer(&p->h_res_dev, p->h_res, 0) != cudaSuccess) {
+    cudaGetLastError();
+    p->h_res_dev = nullptr;
+  }
+  return PIM_OK;
+}
+
+// End of a run on st: results to host (unless `copied` says a gather launch already did
+// it), the error-word mirror, one completion event for all the run's instances.
 int finish_run(pim_instance* const* insts, int count, const int* replicas,
-               const std::shared_ptr<LaunchTimer>& timer, cudaStream_t st, bool to_host) {
-  for (int k = 0; k < count && to_host; ++k) {
+               const std::shared_ptr<LaunchTimer>& timer, cudaStream_t st, bool to_host,
+               bool copied = false) {
+  for (int k = 0; k < count && to_host && !copied; ++k) {
     pim_instance* p = insts[k];
-    if (p->h_res_cap < p->res_bytes) {
-      // the previous block may still be the target of an earlier run's copy
-      if (p->h_res) {
-        CK(cudaEventSynchronize(p->done), "cudaEventSynchronize");
-        give_pinned(p->h_res, p->h_res_cap);
-      }
-      p->h_res_cap = pinned_class(p->res_bytes);
-      p->h_res = static_cast<char*>(take_pinned(p->h_res_cap));
-      if (!p->h_res) {
-        p->h_res_cap = 0;
-        return fail(PIM_ERR_NOMEM, "pinned results buffer of %zu bytes", p->res_bytes);
-      }
-    }
+    const int rc = ensure_host_copy(p);
+    if (rc != PIM_OK) return rc;
     CK(cudaMemcpyAsync(p->h_res, p->d_res, p->res_bytes, cudaMemcpyDeviceToHost, st), "results to host");
   }
   ErrWord* w = error_word(insts[0]->device);
   if (w) CK(cudaMemcpyAsync(w->h, w->d, sizeof(int), cudaMemcpyDeviceToHost, st), "error word mirror");
+  auto done = std::make_shared<RunEvent>();
+  done->device = insts[0]->device;
+  CK(take_event(done->device, &done->ev), "cudaEventCreate");
+  CK(cudaEventRecord(done->ev, st), "cudaEventRecord");
   for (int k = 0; k < count; ++k) {
     insts[k]->h_res_valid = to_host;
     insts[k]->R = replicas[k];
     insts[k]->has_results = true;
     insts[k]->timer = timer;
-    CK(cudaEventRecord(insts[k]->done, st), "cudaEventRecord");
+    insts[k]->done = done;
   }
   return PIM_OK;
 }
@@ -1475,19 +1522,41 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   BatchPlan B;
   const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
   if ((rc = build_plan(insts, count, replicas, ids, targets, flags, init_bytes, B)) != PIM_OK) return rc;
+  // Results to host for many instances: one gather launch writes every block into its
+  // mapped pinned buffer (one copy command per instance would fill the launch queue).
+  constexpr int kGatherMin = 16;
+  std::vector<CopyJob> jobs;
+  if ((flags & PIM_RESULTS_TO_HOST) && count >= kGatherMin) {
+    for (int k = 0; k < count; ++k) {
+      if ((rc = ensure_host_copy(insts[k])) != PIM_OK) return rc;
+      if (!insts[k]->h_res_dev) {
+        jobs.clear();
+        break;
+      }
+      jobs.push_back(CopyJob{insts[k]->d_res, insts[k]->h_res_dev, insts[k]->res_bytes});
+    }
+  }
+  const size_t jobs_off = align256(B.total);
+  const size_t total = jobs_off + jobs.size() * sizeof(CopyJob);
   char* d_buf = nullptr;
-  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
+  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf;
   pack_plan(B, init_spins, h_buf);
-  CK(cudaMemcpyAsync(d_buf, h_buf.data(), B.total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  h_buf.resize(total, 0);
+  if (!jobs.empty()) std::memcpy(h_buf.data() + jobs_off, jobs.data(), jobs.size() * sizeof(CopyJob));
+  CK(cudaMemcpyAsync(d_buf, h_buf.data(), total, cudaMemcpyHostToDevice, st), "upload launch buffer");
   auto timer = std::make_shared<LaunchTimer>();
   CK(cudaEventCreate(&timer->start), "cudaEventCreate");
   CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
   rc = enqueue_plan(B, d_buf, nullptr, insts, count, t_begin, sweeps, seed, cont, ref, timer.get(),
                     d_err, nullptr, st);
   if (rc != PIM_OK) return rc;
+  if (!jobs.empty())
+    CK(launch_gather_copy(reinterpret_cast<const CopyJob*>(d_buf + jobs_off), static_cast<int>(jobs.size()), st),
+       "results gather");
   CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
-  return finish_run(insts, count, replicas, timer, st, (flags & PIM_RESULTS_TO_HOST) != 0);
+  return finish_run(insts, count, replicas, timer, st, (flags & PIM_RESULTS_TO_HOST) != 0,
+                    !jobs.empty());
 }
 
 }  // namespace
@@ -1633,7 +1702,7 @@ PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, 
   if (!d_err) return fail(PIM_ERR_NOMEM, "anneal: error word allocation failed");
   const bool cont = (run_flags & PIM_CONTINUE) != 0;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  for (int k = 0; k < count; ++k) CK(cudaStreamWaitEvent(st, b->insts[k]->ready, 0), "cudaStreamWaitEvent");
+  CK(wait_staged(b->insts.data(), count, st), "cudaStreamWaitEvent");
   // run parameters that the captured launches bake in
   std::string key;
   const uint64_t wait_ns = g_wait_ns.load();
@@ -1694,7 +1763,7 @@ PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_g
 PIM_API void pim_batch_destroy(pim_batch* b) {
   if (!b) return;
   for (pim_instance* p : b->insts)
-    if (p && p->done) cudaEventSynchronize(p->done);
+    if (p && p->done) cudaEventSynchronize(p->done->ev);
   batch_release(b);
 }
 
@@ -1837,7 +1906,7 @@ PIM_API int pim_results_dev(pim_instance* inst, double* best_E, int32_t* best_t,
   if (!inst) return fail(PIM_ERR_INVALID, "pim_results_dev: instance is NULL");
   if (!inst->has_results) return fail(PIM_ERR_STATE, "pim_results_dev: no anneal has run");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  CK(cudaStreamWaitEvent(st, inst->done, 0), "cudaStreamWaitEvent");
+  if (inst->done) CK(cudaStreamWaitEvent(st, inst->done->ev, 0), "cudaStreamWaitEvent");
   const size_t R = inst->R, bits = R * inst->words * sizeof(uint32_t);
   auto d2d = [&](void* dst, const void* src, size_t bytes) {
     return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
@@ -1893,7 +1962,7 @@ PIM_API int pim_poll(uint64_t ticket) {
                                            static_cast<unsigned long long>(ticket));
     inst = it->second;
   }
-  const cudaError_t e = cudaEventQuery(inst->done);
+  const cudaError_t e = inst->done ? cudaEventQuery(inst->done->ev) : cudaSuccess;
   if (e == cudaErrorNotReady) return PIM_PENDING;
   if (e != cudaSuccess) return cuda_fail(e, "pim_poll");
   return check_device_errors(inst->device);
@@ -1901,7 +1970,7 @@ PIM_API int pim_poll(uint64_t ticket) {
 
 PIM_API void pim_destroy(pim_instance* inst) {
   if (!inst) return;
-  if (inst->done) cudaEventSynchronize(inst->done);
+  if (inst->done) cudaEventSynchronize(inst->done->ev);
   {
     std::lock_guard<std::mutex> lk(g_ticket_mu);
     if (inst->ticket) g_tickets.erase(inst->ticket);
@@ -1909,9 +1978,9 @@ PIM_API void pim_destroy(pim_instance* inst) {
   // Blocks go back to the pool on the staging stream once the last anneal has finished.
   free_results(inst);
   give_pinned(inst->h_res, inst->h_res_cap);  // its copies ended with the synchronised run
-  pool_free_after(inst->d_slab, inst->device, inst->done);
-  pool_free_after(inst->d_jf, inst->device, inst->done);
-  give_event(inst->device, inst->done);
+  pool_free_after(inst->d_slab, inst->device, inst->done_ev());
+  pool_free_after(inst->d_jf, inst->device, inst->done_ev());
+  inst->done.reset();
   give_event(inst->device, inst->ready);
   inst->sched.reset();
   delete inst;

@@ -156,7 +156,8 @@ def test_chunked_queue_matches_oracle():
     """More fused units than the two CTAs per SM that run at once: persistent CTAs take
     (chunk, unit) segments from a queue, each chunk after the first starting from the state
     its predecessor (run by another CTA) published.  Units of three sizes on one kernel
-    variant; every unit equals the oracle after pim_anneal_batch, and sampled units after
+    variant; every unit equals the oracle after pim_anneal_batch (its results brought to the
+    host by one gather launch), and sampled units after
     graph-replayed batch-plan runs of 1 and 2 sweeps (chunks down to one sweep) and a
     PIM_CONTINUE resumption to the full schedule."""
     import torch
@@ -180,7 +181,8 @@ def test_chunked_queue_matches_oracle():
     try:
         for hd in handles:
             P.pim_set_schedule(hd, beta, eta, 0.5)
-        P.pim_anneal_batch(handles, reps, T, 21, instance_ids=ids)
+        # results come back through one gather launch (many instances, PIM_RESULTS_TO_HOST)
+        P.pim_anneal_batch(handles, reps, T, 21, instance_ids=ids, flags=P.PIM_RESULTS_TO_HOST)
         _check_all(P, handles, insts, reps, ids, beta, eta, 0.5, 21)
         b = P.pim_batch_create(handles, reps, instance_ids=ids)
         P.pim_batch_run(b, 1, 23)
