@@ -203,6 +203,9 @@ void give_pinned(void* p, size_t cls) {
 // freed blocks (instance buffers come and go with every request).
 struct DeviceCtx {
   cudaStream_t staging = nullptr;
+  // Copy-only stream for the inputs of pim_create: it never waits behind a kernel, so
+  // pageable uploads proceed while sweep kernels hold every SM.
+  cudaStream_t upload = nullptr;
   cudaMemPool_t pool = nullptr;
   // Instances record their `ready` event on `staging` in the order of stage_seq, so a run
   // waits only for the latest of its instances' events.
@@ -217,6 +220,7 @@ DeviceCtx* device_ctx(int dev) {
   DeviceCtx& c = g_ctx[dev];
   if (!c.staging) {
     if (cudaStreamCreateWithFlags(&c.staging, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&c.upload, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -224,8 +228,22 @@ DeviceCtx* device_ctx(int dev) {
     if (cudaMemPoolCreate(&c.pool, &props) != cudaSuccess) return nullptr;
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // No reuse through inserted cross-stream waits: an upload-stream allocation must not
+    // end up waiting for a staging-stream free queued behind a long run.
+    int no = 0;
+    cudaMemPoolSetAttribute(c.pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   }
   return &c;
+}
+
+// The staging stream waits for everything queued so far on the upload stream.
+cudaError_t staging_after_upload(DeviceCtx* c, int dev) {
+  cudaEvent_t up = nullptr;
+  cudaError_t e = take_event(dev, &up);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventRecord(up, c->upload)) == cudaSuccess) e = cudaStreamWaitEvent(c->staging, up, 0);
+  give_event(dev, up);  // the wait above holds this record
+  return e;
 }
 
 // Stream-ordered allocation from the library's pool.
@@ -698,21 +716,22 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t o_img = align256(nn * 2), o_h = o_img + align256(static_cast<size_t>(p->npad) * p->npad * 2);
   void* slab = nullptr;
-  if ((e = pool_alloc(&slab, o_h + align256(n * sizeof(float)), p->device, ctx->staging)) != cudaSuccess)
+  if ((e = pool_alloc(&slab, o_h + align256(n * sizeof(float)), p->device, ctx->upload)) != cudaSuccess)
     return bail(e, "allocating J");
   p->d_slab = static_cast<char*>(slab);
   uint16_t* d_bf = reinterpret_cast<uint16_t*>(p->d_slab);
   p->d_img = reinterpret_cast<uint8_t*>(p->d_slab + o_img);
-  if ((e = cudaMemcpyAsync(d_bf, jb.get(), nn * 2, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(d_bf, jb.get(), nn * 2, cudaMemcpyHostToDevice, ctx->upload)) != cudaSuccess)
     return bail(e, "upload J");
-  if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging)) != cudaSuccess)
-    return bail(e, "stage BF16 J image");
   if (has_h) {
     p->d_hf = reinterpret_cast<float*>(p->d_slab + o_h);
     if ((e = cudaMemcpyAsync(p->d_hf, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice,
-                             ctx->staging)) != cudaSuccess)
+                             ctx->upload)) != cudaSuccess)
       return bail(e, "upload h");
   }
+  if ((e = staging_after_upload(ctx, p->device)) != cudaSuccess) return bail(e, "staging order");
+  if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging)) != cudaSuccess)
+    return bail(e, "stage BF16 J image");
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
   {
@@ -831,19 +850,20 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   const size_t o_img = align256(nn), o_h = o_img + align256(img);
   const size_t o_img5 = o_h + align256(n * sizeof(int32_t));
   void* slab = nullptr;
-  if ((e = pool_alloc(&slab, o_img5 + (p->dk5 ? align256(img) : 0), p->device, ctx->staging)) != cudaSuccess)
+  if ((e = pool_alloc(&slab, o_img5 + (p->dk5 ? align256(img) : 0), p->device, ctx->upload)) != cudaSuccess)
     return bail(e, "allocating J");
   p->d_slab = static_cast<char*>(slab);
   p->d_J8 = reinterpret_cast<int8_t*>(p->d_slab);
   p->d_img = reinterpret_cast<uint8_t*>(p->d_slab + o_img);
-  if ((e = cudaMemcpyAsync(p->d_J8, J8, nn, cudaMemcpyHostToDevice, ctx->staging)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(p->d_J8, J8, nn, cudaMemcpyHostToDevice, ctx->upload)) != cudaSuccess)
     return bail(e, "upload J");
   if (p->has_h) {
     p->d_h = reinterpret_cast<int32_t*>(p->d_slab + o_h);
     if ((e = cudaMemcpyAsync(p->d_h, h32, n * sizeof(int32_t), cudaMemcpyHostToDevice,
-                             ctx->staging)) != cudaSuccess)
+                             ctx->upload)) != cudaSuccess)
       return bail(e, "upload h");
   }
+  if ((e = staging_after_upload(ctx, p->device)) != cudaSuccess) return bail(e, "staging order");
   p->diag = n <= kMaxNTensor && !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
   if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging)) !=
       cudaSuccess)
