@@ -590,9 +590,7 @@ def run_ours(args, w: Workload):
     # steps are in flight, as in a serving loop: step k+1 is staged and launched (queued on
     # the same stream behind step k's kernels) before step k's results are read, so the host
     # work of one step overlaps the device work of the other.
-    # (The first overlapped step also grows the library's memory pool, which waits for the
-    # running kernel; later steps reuse the blocks the previous step released.)
-    e2e_steps = 4 if n_inst > 1000 else max(2, min(10, args.steps))
+    e2e_steps = 3 if n_inst > 1000 else max(2, min(10, args.steps))
     h2d = sum(i.n * i.n * (2 if real else 1) for i in insts)  # BF16 or int8 couplings copied
     # results come back with the run (PIM_RESULTS_TO_HOST): the whole result block of each
     # instance, per-replica scalars and best and final state bits, each part 256-byte aligned
@@ -600,25 +598,32 @@ def run_ours(args, w: Workload):
         return (x + 255) // 256 * 256
     d2h = sum(_al(r * 24) + 2 * _al(r * ((i.n + 63) // 64) * 2 * 4) for i, r in zip(insts, reps))
     out_E = [None] * n_inst
+
+    def pipeline(steps):
+        in_flight = None
+        for step in range(steps + 1):
+            launched = None
+            if step < steps:
+                launched = [pim.pim_create(i.J, None, i.c) for i in insts]
+                for hd, xi in zip(launched, xis):
+                    pim.pim_set_schedule(hd, beta, eta, xi)
+                pim.pim_anneal_batch(launched, reps, sweeps, seed=0, instance_ids=ids, stream=stream,
+                                     flags=pim.PIM_RESULTS_TO_HOST)
+            if in_flight is not None:
+                for q, (hd, inst) in enumerate(zip(in_flight, insts)):
+                    out_E[q] = pim.pim_energies(hd)["best_E"]
+                    pim.pim_best_state(hd, inst.n)
+                for hd in in_flight:
+                    pim.pim_destroy(hd)
+            in_flight = launched
+
+    # untimed warm-up of the same pipeline: the library's memory pools reach the size two
+    # steps in flight need (growing a pool while a kernel runs would wait for the GPU)
+    pipeline(2)
     torch.cuda.synchronize()
     _barrier(world)
     e0 = time.perf_counter()
-    in_flight = None
-    for step in range(e2e_steps + 1):
-        launched = None
-        if step < e2e_steps:
-            launched = [pim.pim_create(i.J, None, i.c) for i in insts]
-            for hd, xi in zip(launched, xis):
-                pim.pim_set_schedule(hd, beta, eta, xi)
-            pim.pim_anneal_batch(launched, reps, sweeps, seed=0, instance_ids=ids, stream=stream,
-                                 flags=pim.PIM_RESULTS_TO_HOST)
-        if in_flight is not None:
-            for q, (hd, inst) in enumerate(zip(in_flight, insts)):
-                out_E[q] = pim.pim_energies(hd)["best_E"]
-                pim.pim_best_state(hd, inst.n)
-            for hd in in_flight:
-                pim.pim_destroy(hd)
-        in_flight = launched
+    pipeline(e2e_steps)
     e2e_s = _max_over_ranks(time.perf_counter() - e0, world) / e2e_steps
     e2e_value = updates_per_step * world / e2e_s
 
@@ -738,7 +743,8 @@ def run_ours(args, w: Workload):
         "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "pipeline": "2 steps in flight (stage + launch step k+1, then read step k)"},
+                "pipeline": "2 steps in flight (stage + launch step k+1, then read step k); "
+                            "2 untimed warm-up steps"},
         "gpu_launches": info["kernel_launches"] * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,

@@ -159,6 +159,54 @@ void give_event(int dev, cudaEvent_t ev) {
   g_free_events[dev].push_back(ev);
 }
 
+// Host-to-device uploads of run descriptors through pinned staging buffers: a copy from
+// pageable memory may make the driver synchronise with the stream first, which would stall
+// the host behind the previous run.  A buffer is reused once the event recorded after its
+// copy has completed.
+struct UploadBuf {
+  void* h = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+};
+std::mutex g_up_mu;
+std::map<int, std::vector<std::unique_ptr<UploadBuf>>> g_up;
+
+cudaError_t upload_async(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  UploadBuf* u = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_up_mu);
+    for (auto& b : g_up[dev])
+      if (!b->busy && b->cap >= bytes && cudaEventQuery(b->ev) == cudaSuccess) {
+        u = b.get();
+        break;
+      }
+    if (!u) {
+      auto b = std::make_unique<UploadBuf>();
+      size_t cap = 4096;
+      while (cap < bytes) cap <<= 1;
+      cudaError_t e = cudaHostAlloc(&b->h, cap, cudaHostAllocPortable);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming)) != cudaSuccess) {
+        cudaFreeHost(b->h);
+        return e;
+      }
+      b->cap = cap;
+      u = b.get();
+      g_up[dev].push_back(std::move(b));
+    }
+    u->busy = true;
+  }
+  std::memcpy(u->h, src, bytes);
+  cudaError_t e = cudaMemcpyAsync(dst, u->h, bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(u->ev, st);
+  std::lock_guard<std::mutex> lk(g_up_mu);
+  u->busy = false;
+  return e;
+}
+
 // Completion event of one run, shared by every instance of the run (one record per run,
 // however many instances it holds); back to the free list with its last holder.
 struct RunEvent {
@@ -206,6 +254,11 @@ struct DeviceCtx {
   // Copy-only stream for the inputs of pim_create: it never waits behind a kernel, so
   // pageable uploads proceed while sweep kernels hold every SM.
   cudaStream_t upload = nullptr;
+  // Kernel-free stream on which blocks go back to the pool once their run has finished, so
+  // the free executes right then and the next allocations reuse the block (a free queued
+  // behind staging kernels would wait for SMs that a running sweep kernel holds, and the
+  // pool would grow instead, which stalls the host until the GPU is idle).
+  cudaStream_t release = nullptr;
   cudaMemPool_t pool = nullptr;
   // Instances record their `ready` event on `staging` in the order of stage_seq, so a run
   // waits only for the latest of its instances' events.
@@ -221,6 +274,7 @@ DeviceCtx* device_ctx(int dev) {
   if (!c.staging) {
     if (cudaStreamCreateWithFlags(&c.staging, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     if (cudaStreamCreateWithFlags(&c.upload, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithFlags(&c.release, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     cudaMemPoolProps props = {};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -253,13 +307,21 @@ cudaError_t pool_alloc(void** p, size_t bytes, int dev, cudaStream_t st) {
   return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
 }
 
-// Free `p` on the staging stream once `after` (if any) has completed.
+// Free `p` on the release stream once `after` (if any) has completed.
 void pool_free_after(void* p, int dev, cudaEvent_t after) {
   if (!p) return;
   DeviceCtx* c = device_ctx(dev);
   if (!c) return;
-  if (after) cudaStreamWaitEvent(c->staging, after, 0);
-  cudaFreeAsync(p, c->staging);
+  if (after) cudaStreamWaitEvent(c->release, after, 0);
+  cudaFreeAsync(p, c->release);
+}
+
+// Stream-ordered scratch for one run on st, from the library's pool of the current device
+// (which keeps its memory, unlike the default pool that returns it at every sync).
+cudaError_t run_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return pool_alloc(p, bytes, dev, st);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -1071,7 +1133,7 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
     const size_t bytes = 2 * img_bytes + energy_bytes + 256;
     char* d = scratch;
     if (!scratch)
-      CK(cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st), "cudaMallocAsync large-N scratch");
+      CK(run_alloc(reinterpret_cast<void**>(&d), bytes, st), "cudaMallocAsync large-N scratch");
     CK(cudaMemsetAsync(d + 2 * img_bytes, 0, energy_bytes + 256, st), "clear large-N scratch");
     BigLaunch L{};
     L.P = P;
@@ -1379,8 +1441,8 @@ int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instanc
     size_t maxRn = 0;
     for (int k = 0; k < count; ++k)
       maxRn = std::max(maxRn, static_cast<size_t>(B.probs[k].R) * insts[k]->n);
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&d_S), maxRn * 4, st), "cudaMallocAsync S");
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&d_I), maxRn * 4, st), "cudaMallocAsync I");
+    CK(run_alloc(reinterpret_cast<void**>(&d_S), maxRn * 4, st), "cudaMallocAsync S");
+    CK(run_alloc(reinterpret_cast<void**>(&d_I), maxRn * 4, st), "cudaMallocAsync I");
     CK(record_event(timer->start, st), "cudaEventRecord");
     CK(launch_ref_anneal(B.probs.data(), d_probs, count, t_begin, sweeps, static_cast<uint32_t>(seed),
                          static_cast<uint32_t>(seed >> 32), cont ? 1 : 0, d_S, d_I, d_err, st),
@@ -1526,6 +1588,31 @@ int finish_run(pim_instance* const* insts, int count, const int* replicas,
   return PIM_OK;
 }
 
+// Results to host for many instances: one gather launch on st writes every instance's
+// result block into its mapped pinned buffer (one copy command per instance would fill the
+// launch queue behind a long run).  *copied = false when some buffer has no device address
+// (finish_run then copies instance by instance).
+constexpr int kGatherMin = 16;
+
+int gather_results(pim_instance* const* insts, int count, cudaStream_t st, bool* copied) {
+  *copied = false;
+  std::vector<CopyJob> jobs;
+  for (int k = 0; k < count; ++k) {
+    const int rc = ensure_host_copy(insts[k]);
+    if (rc != PIM_OK) return rc;
+    if (!insts[k]->h_res_dev) return PIM_OK;
+    jobs.push_back(CopyJob{insts[k]->d_res, insts[k]->h_res_dev, insts[k]->res_bytes});
+  }
+  CopyJob* d_jobs = nullptr;
+  const size_t bytes = jobs.size() * sizeof(CopyJob);
+  CK(run_alloc(reinterpret_cast<void**>(&d_jobs), bytes, st), "cudaMallocAsync gather table");
+  CK(upload_async(d_jobs, jobs.data(), bytes, st), "upload gather table");
+  CK(launch_gather_copy(d_jobs, static_cast<int>(jobs.size()), st), "results gather");
+  CK(cudaFreeAsync(d_jobs, st), "cudaFreeAsync gather table");
+  *copied = true;
+  return PIM_OK;
+}
+
 int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
                 int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
                 const int8_t* init_spins, int flags, cudaStream_t st) {
@@ -1542,41 +1629,23 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   BatchPlan B;
   const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
   if ((rc = build_plan(insts, count, replicas, ids, targets, flags, init_bytes, B)) != PIM_OK) return rc;
-  // Results to host for many instances: one gather launch writes every block into its
-  // mapped pinned buffer (one copy command per instance would fill the launch queue).
-  constexpr int kGatherMin = 16;
-  std::vector<CopyJob> jobs;
-  if ((flags & PIM_RESULTS_TO_HOST) && count >= kGatherMin) {
-    for (int k = 0; k < count; ++k) {
-      if ((rc = ensure_host_copy(insts[k])) != PIM_OK) return rc;
-      if (!insts[k]->h_res_dev) {
-        jobs.clear();
-        break;
-      }
-      jobs.push_back(CopyJob{insts[k]->d_res, insts[k]->h_res_dev, insts[k]->res_bytes});
-    }
-  }
-  const size_t jobs_off = align256(B.total);
-  const size_t total = jobs_off + jobs.size() * sizeof(CopyJob);
   char* d_buf = nullptr;
-  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), total, st), "cudaMallocAsync launch buffer");
+  CK(run_alloc(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf;
   pack_plan(B, init_spins, h_buf);
-  h_buf.resize(total, 0);
-  if (!jobs.empty()) std::memcpy(h_buf.data() + jobs_off, jobs.data(), jobs.size() * sizeof(CopyJob));
-  CK(cudaMemcpyAsync(d_buf, h_buf.data(), total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  CK(upload_async(d_buf, h_buf.data(), B.total, st), "upload launch buffer");
   auto timer = std::make_shared<LaunchTimer>();
   CK(cudaEventCreate(&timer->start), "cudaEventCreate");
   CK(cudaEventCreate(&timer->stop), "cudaEventCreate");
   rc = enqueue_plan(B, d_buf, nullptr, insts, count, t_begin, sweeps, seed, cont, ref, timer.get(),
                     d_err, nullptr, st);
   if (rc != PIM_OK) return rc;
-  if (!jobs.empty())
-    CK(launch_gather_copy(reinterpret_cast<const CopyJob*>(d_buf + jobs_off), static_cast<int>(jobs.size()), st),
-       "results gather");
   CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
-  return finish_run(insts, count, replicas, timer, st, (flags & PIM_RESULTS_TO_HOST) != 0,
-                    !jobs.empty());
+  const bool to_host = (flags & PIM_RESULTS_TO_HOST) != 0;
+  bool copied = false;
+  if (to_host && count >= kGatherMin && (rc = gather_results(insts, count, st, &copied)) != PIM_OK)
+    return rc;
+  return finish_run(insts, count, replicas, timer, st, to_host, copied);
 }
 
 }  // namespace
@@ -1769,8 +1838,12 @@ PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, 
                       false, b->timer.get(), d_err, &b->launches, st);
     if (rc != PIM_OK) return rc;
   }
-  return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st,
-                    (run_flags & PIM_RESULTS_TO_HOST) != 0);
+  const bool to_host = (run_flags & PIM_RESULTS_TO_HOST) != 0;
+  bool copied = false;
+  if (to_host && count >= kGatherMin &&
+      (rc = gather_results(b->insts.data(), count, st, &copied)) != PIM_OK)
+    return rc;
+  return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st, to_host, copied);
 }
 
 PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_graph) {
@@ -1814,10 +1887,10 @@ PIM_API int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin,
   if ((rc = build_plan(&inst, 1, &replicas, &id, &target_energy, PIM_PATH_FP32REF, init_bytes, B)) != PIM_OK)
     return rc;
   char* d_buf = nullptr;
-  CK(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
+  CK(run_alloc(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf;
   pack_plan(B, init_spins, h_buf);
-  CK(cudaMemcpyAsync(d_buf, h_buf.data(), B.total, cudaMemcpyHostToDevice, st), "upload launch buffer");
+  CK(upload_async(d_buf, h_buf.data(), B.total, st), "upload launch buffer");
   if (!cont) {
     const int8_t* d_init = init_bytes ? reinterpret_cast<const int8_t*>(d_buf + B.init_off) : nullptr;
     CK(launch_init_bits(reinterpret_cast<const Problem*>(d_buf), 1, replicas, inst->words, d_init,
@@ -1998,8 +2071,10 @@ PIM_API void pim_destroy(pim_instance* inst) {
   // Blocks go back to the pool on the staging stream once the last anneal has finished.
   free_results(inst);
   give_pinned(inst->h_res, inst->h_res_cap);  // its copies ended with the synchronised run
-  pool_free_after(inst->d_slab, inst->device, inst->done_ev());
-  pool_free_after(inst->d_jf, inst->device, inst->done_ev());
+  // after its last run, or (never run) after its own staging on the staging stream
+  cudaEvent_t after = inst->done ? inst->done->ev : inst->ready;
+  pool_free_after(inst->d_slab, inst->device, after);
+  pool_free_after(inst->d_jf, inst->device, after);
   inst->done.reset();
   give_event(inst->device, inst->ready);
   inst->sched.reset();

@@ -188,7 +188,7 @@ def test_chunked_queue_matches_oracle():
         P.pim_batch_run(b, 1, 23)
         _check_all(P, pick(handles), pick(insts), pick(reps), pick(ids), beta, eta, 0.5, 23,
                    sweeps=1)
-        P.pim_batch_run(b, 2, 22)
+        P.pim_batch_run(b, 2, 22, run_flags=P.PIM_RESULTS_TO_HOST)  # gather after a replay
         _check_all(P, pick(handles), pick(insts), pick(reps), pick(ids), beta, eta, 0.5, 22,
                    sweeps=2)
         P.pim_batch_run(b, T - 2, 22, t_begin=2, run_flags=P.PIM_CONTINUE)
