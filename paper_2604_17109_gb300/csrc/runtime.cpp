@@ -247,8 +247,8 @@ void give_pinned(void* p, size_t cls) {
   g_free_pinned.emplace(cls, p);
 }
 
-// Per device: a non-blocking stream for staging and freeing, and a memory pool that keeps
-// freed blocks (instance buffers come and go with every request).
+// Per device: non-blocking streams for input uploads, staging kernels and frees, and a memory
+// pool that keeps freed blocks (instance buffers come and go with every request).
 struct DeviceCtx {
   cudaStream_t staging = nullptr;
   // Copy-only stream for the inputs of pim_create: it never waits behind a kernel, so
@@ -283,7 +283,7 @@ DeviceCtx* device_ctx(int dev) {
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
     // No reuse through inserted cross-stream waits: an upload-stream allocation must not
-    // end up waiting for a staging-stream free queued behind a long run.
+    // end up waiting for a free that is still queued behind a long run.
     int no = 0;
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   }
@@ -898,8 +898,9 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     pim_destroy(p);
     return rc;
   };
-  // One pool block J8 | FP8 image | bias, filled and staged on the library's staging
-  // stream; anneals wait for the `ready` event instead of the host waiting here.
+  // One pool block J8 | FP8 image | bias (| E5M2 image), uploaded on the library's upload
+  // stream and staged on its staging stream; anneals wait for the `ready` event instead of
+  // the host waiting here.
   cudaError_t e;
   DeviceCtx* ctx = device_ctx(p->device);
   if (!ctx) return bail(cudaErrorMemoryAllocation, "device context");
@@ -2068,7 +2069,7 @@ PIM_API void pim_destroy(pim_instance* inst) {
     std::lock_guard<std::mutex> lk(g_ticket_mu);
     if (inst->ticket) g_tickets.erase(inst->ticket);
   }
-  // Blocks go back to the pool on the staging stream once the last anneal has finished.
+  // Blocks go back to the pool on the release stream once the last anneal has finished.
   free_results(inst);
   give_pinned(inst->h_res, inst->h_res_cap);  // its copies ended with the synchronised run
   // after its last run, or (never run) after its own staging on the staging stream
