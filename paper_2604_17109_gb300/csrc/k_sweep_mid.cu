@@ -127,6 +127,10 @@ __device__ __forceinline__ uint32_t diag_chunk16(const uint32_t (&v)[16], const 
   return ~((neg_hi << 8) | neg_lo) & 0xFFFFu;
 }
 
+// DIAG = true: every unit has a diagonal-encoded image (P.dk > 0) and decides from its
+// 16-bit table; DIAG = false: no unit has one (bias fast path or general path).  Two
+// variants keep the register allocation of each to the paths it runs.
+template <bool DIAG>
 __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_constant__ Launch L) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -306,15 +310,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       // Problem fields in registers: the loops below store to global memory, which would
       // otherwise make the compiler reload them from the descriptor.
       const uint32_t q = P.q;
-      const int dk = P.dk;
+      const int dk = DIAG ? P.dk : 0;
       const int imax = P.imax, stride = dk > 0 ? 2 * dk : P.stride_words;  // words per step
       const uint32_t* thr = dk > 0 ? P.thr_diag : P.thr;
       const long long target = P.target;
       const bool tab_smem = stride <= kTabWords;
       const bool has_target = P.has_target != 0;
       const int dg = P.diag_img ? 256 : 0;  // diagonal-encoded image: D = I + 256 s
-      const bool fast = P.h == nullptr && !P.diag_img && dk == 0 && tab_smem;
-      const bool dfast = dk > 0 && tab_smem;  // diagonal-encoded table in shared memory
+      const bool fast = !DIAG && P.h == nullptr && !P.diag_img && tab_smem;
+      constexpr bool dfast = DIAG;  // diagonal-encoded table in shared memory (2 dk <= kTabWords)
       // byte address of the entry of D: 2 (bits of D + 1.5*2^23) + tab_d (mod 2^32)
       const uint32_t tab_d = smem_u32(sTab) + 4u * static_cast<uint32_t>(dk) - 2u * kMagicBits;
       const int e_off = dfast ? dk * n : 0;  // sum of |D| over the n spins = sum s I + n dk
@@ -540,11 +544,11 @@ int sweep_mid_max_npad() { return kMaxNpad; }
 
 int sweep_mid_max_blocks() {
   const int smem = sweep_mid_smem_bytes();
-  if (cudaFuncSetAttribute(sweep_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+  if (cudaFuncSetAttribute(sweep_mid_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_mid_kernel, kThreads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_mid_kernel<false>, kThreads, smem) !=
       cudaSuccess)
     return 0;
   cudaGetDevice(&dev);
@@ -552,13 +556,17 @@ int sweep_mid_max_blocks() {
   return per_sm * sms;
 }
 
-cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st) {
+cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st, bool diag) {
   const int smem = sweep_mid_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(sweep_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(diag ? sweep_mid_kernel<true> : sweep_mid_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(L.next, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  sweep_mid_kernel<<<blocks, kThreads, smem, st>>>(L);
+  if (diag)
+    sweep_mid_kernel<true><<<blocks, kThreads, smem, st>>>(L);
+  else
+    sweep_mid_kernel<false><<<blocks, kThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 

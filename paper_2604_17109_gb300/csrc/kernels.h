@@ -62,7 +62,8 @@ int sweep_big_stages(int nt, bool real);      // depth of the K-block ring
 
 // Persistent mid-N kernel (integer couplings, npad <= 1024): `blocks` CTAs take the units
 // of L.work from the counter L.next (zeroed by the launch).
-cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st);
+// diag: every unit has P.dk > 0 (diagonal-encoded variant), else none has.
+cudaError_t launch_sweep_mid(const Launch& L, int blocks, cudaStream_t st, bool diag);
 int sweep_mid_max_blocks();
 int sweep_mid_max_npad();
 

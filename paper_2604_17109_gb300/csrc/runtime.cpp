@@ -1237,7 +1237,8 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
   return PIM_OK;
 }
 
-constexpr int kGroups = 7, kMidGroup = 6;
+// fused 0-5, mid-N general path 6, mid-N diagonal-encoded 7
+constexpr int kGroups = 8, kMidGroup = 6, kMidDiagGroup = 7;
 
 // Launch description of one batch: problem descriptors, the unit lists of each kernel group
 // (fused: npad 128 | 256 x diagonal-encoded | general bias | real-valued; persistent mid-N),
@@ -1376,16 +1377,16 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
                                                   sizeof(float) * 3 * rpad + 256);
       continue;
     }
-    const int g = B.route[k] == kMid ? kMidGroup
+    const int g = B.route[k] == kMid ? (B.probs[k].dk > 0 ? kMidDiagGroup : kMidGroup)
                                      : (insts[k]->npad <= 128 ? 0 : 1) +
                                            (insts[k]->real ? 4 : (insts[k]->diag ? 0 : 2));
     for (int rb = 0; rb < replicas[k]; rb += 128) B.work[g].push_back({k, rb});
   }
   // persistent launch: largest units first so the last wave is short
-  std::stable_sort(B.work[kMidGroup].begin(), B.work[kMidGroup].end(),
-                   [&](const WorkItem& a, const WorkItem& b) {
-                     return insts[a.prob]->npad > insts[b.prob]->npad;
-                   });
+  for (int g : {kMidGroup, kMidDiagGroup})
+    std::stable_sort(B.work[g].begin(), B.work[g].end(), [&](const WorkItem& a, const WorkItem& b) {
+      return insts[a.prob]->npad > insts[b.prob]->npad;
+    });
   size_t off = align256(B.probs.size() * sizeof(Problem));
   for (int g = 0; g < kGroups; ++g) {
     B.work_off[g] = off;
@@ -1485,10 +1486,10 @@ int enqueue_plan(const BatchPlan& B, char* d_buf, char* big_scratch, pim_instanc
           blocks = ctas;
         }
       }
-      if (g == kMidGroup) {
+      if (g == kMidGroup || g == kMidDiagGroup) {
         const int blocks = std::min(L.nwork, sweep_mid_max_blocks());
         if (blocks < 1) return fail(PIM_ERR_CUDA, "anneal: mid-N kernel cannot be resident");
-        CK(launch_sweep_mid(L, blocks, st), "persistent mid-N sweep kernel");
+        CK(launch_sweep_mid(L, blocks, st, g == kMidDiagGroup), "persistent mid-N sweep kernel");
       } else if (g >= 4) {
         CK(launch_sweep_float(L, (g & 1) ? 256 : 128, L.nwork, st), "real-valued sweep kernel");
       } else {

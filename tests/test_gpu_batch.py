@@ -235,3 +235,39 @@ def test_chunked_queue_general_bias_variants():
     finally:
         for hd in handles:
             P.pim_destroy(hd)
+
+
+def test_mid_batch_mixes_diagonal_and_general_units():
+    """One batch on the mid-N kernel with units of both kinds: SK N = 400 and Max-Cut N = 500
+    (diagonal-encoded from E5M2 images), SK N = 400 with a bias h and SK N = 350 with some
+    |J| = 9 (general table): the two kinds run as two persistent launches of one call and
+    every instance equals the oracle."""
+    from workloads import Instance
+    P = pim()
+    rng = np.random.default_rng(91)
+    a = sk_pm1(400, 601)
+    b = maxcut_er(500, 602)
+    base = sk_pm1(400, 603)
+    c = Instance("sk", 400, base.J, rng.integers(-2, 3, size=400).astype(np.int32), base.c, base.seed)
+    base = sk_pm1(350, 604)
+    J9 = base.J.astype(np.int8).copy()
+    i = np.arange(0, 349, 5)
+    J9[i, i + 1] = J9[i + 1, i] = 9 * J9[i, i + 1]
+    d = Instance("sk", 350, J9, base.h, base.c, base.seed)
+    insts = [a, b, c, d]
+    reps = [130, 64, 96, 200]
+    ids = [11, 12, 13, 14]
+    T = 9
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    handles = [P.pim_create(x.J, x.h if np.any(x.h) else None, x.c) for x in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta, 0.5)
+        P.pim_anneal_batch(handles, reps, T, 41, instance_ids=ids, flags=P.PIM_PATH_MID)
+        for hd, x, R, q in zip(handles, insts, reps, ids):
+            want = oracle_run(x, beta, eta, 0.5, replicas=R, seed=41, q=q)
+            assert_same(collect(hd, x.n), want, label=f"n={x.n} q={q}")
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
