@@ -22,7 +22,10 @@
  *  - Spin arrays on the host are int8 values -1/+1, row-major (replica, spin).
  *  - Annealing calls are asynchronous on the CUDA stream passed as `cuda_stream`
  *    (a cudaStream_t; NULL = the legacy default stream).  Result getters synchronise on
- *    the instance's last launch before copying.
+ *    the instance's last run before copying (an instance annealed in a batch completes
+ *    with the whole batch: one completion event per run).
+ *  - pim_create uploads and stages its inputs asynchronously on library-owned streams;
+ *    the first anneal of the instance waits for them on the device (the host does not).
  *  - One GPU: all device memory lives on the device that is current when pim_create
  *    runs; later calls must run with that device current.
  */
