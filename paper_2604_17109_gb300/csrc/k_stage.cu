@@ -193,4 +193,14 @@ cudaError_t launch_gather_copy(const CopyJob* d_jobs, int count, cudaStream_t st
   return cudaGetLastError();
 }
 
+// One word from device memory into mapped pinned host memory (the error-word mirror).
+__global__ void mirror_word_kernel(const int* __restrict__ d, int* h) {
+  *reinterpret_cast<volatile int*>(h) = *reinterpret_cast<const volatile int*>(d);
+}
+
+cudaError_t launch_mirror_word(const int* d, int* h_dev, cudaStream_t st) {
+  mirror_word_kernel<<<1, 1, 0, st>>>(d, h_dev);
+  return cudaGetLastError();
+}
+
 }  // namespace pim

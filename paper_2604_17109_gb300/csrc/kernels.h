@@ -34,6 +34,9 @@ cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const floa
 cudaError_t launch_diag_thresholds(const uint32_t* d_thr, int steps, int imax, int stride_words,
                                    int K, uint32_t* d_thr_diag, cudaStream_t st);
 
+// Copies one int from device memory to mapped pinned host memory (h_dev: its device address).
+cudaError_t launch_mirror_word(const int* d, int* h_dev, cudaStream_t st);
+
 // Copies every job's block (jobs in device memory).
 cudaError_t launch_gather_copy(const CopyJob* d_jobs, int count, cudaStream_t st);
 

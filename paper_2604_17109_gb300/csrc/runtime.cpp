@@ -105,12 +105,15 @@ std::atomic<uint64_t> g_wait_ns{0};
 std::mutex g_sched_mu;
 std::map<std::string, std::weak_ptr<Schedule>> g_sched_cache;
 
-// Per-device error word written by the kernels, and a pinned host mirror that every run
-// refreshes (stream-ordered) before it records its completion event, so result getters read
-// host memory instead of issuing a synchronous copy.
+// Per-device error word written by the kernels, and a mapped pinned host mirror that a
+// one-thread kernel refreshes at the end of every run, before its completion event, so
+// result getters read host memory instead of issuing a synchronous copy.  (A copy command
+// would queue on the copy engine behind copies of other streams that wait for their own
+// kernels, delaying this run's completion; a kernel does not.)
 struct ErrWord {
   int* d = nullptr;
   int* h = nullptr;
+  int* h_dev = nullptr;  // device address of h; null: read d synchronously instead
 };
 std::mutex g_err_mu;
 std::map<int, ErrWord> g_err_word;
@@ -121,9 +124,13 @@ ErrWord* error_word(int dev) {
   if (it != g_err_word.end()) return &it->second;
   ErrWord w;
   if (cudaMalloc(&w.d, sizeof(int)) != cudaSuccess) return nullptr;
-  if (cudaHostAlloc(&w.h, sizeof(int), cudaHostAllocPortable) != cudaSuccess) {
+  if (cudaHostAlloc(&w.h, sizeof(int), cudaHostAllocPortable | cudaHostAllocMapped) != cudaSuccess) {
     cudaFree(w.d);
     return nullptr;
+  }
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&w.h_dev), w.h, 0) != cudaSuccess) {
+    cudaGetLastError();
+    w.h_dev = nullptr;
   }
   cudaMemset(w.d, 0, sizeof(int));
   *w.h = 0;
@@ -282,10 +289,6 @@ DeviceCtx* device_ctx(int dev) {
     if (cudaMemPoolCreate(&c.pool, &props) != cudaSuccess) return nullptr;
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    // No reuse through inserted cross-stream waits: an upload-stream allocation must not
-    // end up waiting for a free that is still queued behind a long run.
-    int no = 0;
-    cudaMemPoolSetAttribute(c.pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   }
   return &c;
 }
@@ -417,7 +420,11 @@ int ensure_results(pim_instance* p, int R, cudaStream_t st) {
 int check_device_errors(int dev) {
   ErrWord* w = error_word(dev);
   if (!w) return PIM_OK;
-  const int h = *static_cast<volatile int*>(w->h);
+  int h = 0;
+  if (w->h_dev)
+    h = *static_cast<volatile int*>(w->h);
+  else
+    CK(cudaMemcpy(&h, w->d, sizeof(int), cudaMemcpyDeviceToHost), "reading device error word");
   if (h != 0) {
     cudaMemset(w->d, 0, sizeof(int));
     *static_cast<volatile int*>(w->h) = 0;
@@ -1575,7 +1582,7 @@ int finish_run(pim_instance* const* insts, int count, const int* replicas,
     CK(cudaMemcpyAsync(p->h_res, p->d_res, p->res_bytes, cudaMemcpyDeviceToHost, st), "results to host");
   }
   ErrWord* w = error_word(insts[0]->device);
-  if (w) CK(cudaMemcpyAsync(w->h, w->d, sizeof(int), cudaMemcpyDeviceToHost, st), "error word mirror");
+  if (w && w->h_dev) CK(launch_mirror_word(w->d, w->h_dev, st), "error word mirror");
   auto done = std::make_shared<RunEvent>();
   done->device = insts[0]->device;
   CK(take_event(done->device, &done->ev), "cudaEventCreate");
@@ -1594,7 +1601,7 @@ int finish_run(pim_instance* const* insts, int count, const int* replicas,
 // result block into its mapped pinned buffer (one copy command per instance would fill the
 // launch queue behind a long run).  *copied = false when some buffer has no device address
 // (finish_run then copies instance by instance).
-constexpr int kGatherMin = 16;
+constexpr int kGatherMin = 1;
 
 int gather_results(pim_instance* const* insts, int count, cudaStream_t st, bool* copied) {
   *copied = false;
@@ -1850,7 +1857,7 @@ PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, 
 
 PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_graph) {
   if (!b) return fail(PIM_ERR_INVALID, "pim_batch_info: batch is NULL");
-  if (kernel_launches) *kernel_launches = b->launches;
+  if (kernel_launches) *kernel_launches = b->launches + 1;  // + the end-of-run error-word mirror
   if (uses_graph) *uses_graph = b->use_graph && b->exec ? 1 : 0;
   return PIM_OK;
 }
