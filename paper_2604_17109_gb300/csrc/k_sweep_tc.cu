@@ -1,6 +1,7 @@
 // Fused PIMI sweep kernel for sm_103a: tcgen05 field GEMM into TMEM, fused decision,
-// spin write-back and energy / best-state tracking, all sweeps of a replica tile inside one
-// CTA.
+// spin write-back and energy / best-state tracking, consecutive sweeps of a replica tile
+// inside one CTA (all of them, or one chunk of them when persistent CTAs share the units
+// through the launch's queue).
 //
 // Per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
 //   fields   D[r, i] = sum_j S[r, j] J[i, j]   (tcgen05.mma kind::f8f6f4, M = 128 replicas,
