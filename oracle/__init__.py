@@ -1,7 +1,8 @@
 """CPU oracle for the PIMI sweep path -- TEST INFRASTRUCTURE ONLY.
 
 Plain, slow, obviously-correct numpy code that restates the paper's update rule step by
-step.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+step (``pimi.py``), and a second plain statement of the anneal in C++17 (``pimi_ref.cpp``,
+loaded through ``cpp.py``) that is pinned to it and timed as the CPU baseline.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  The CUDA library never imports, links or calls anything
 here, and nothing here imports the library.
 """

@@ -10,7 +10,7 @@ What it restates (paper section / equation):
   * success criterion min_{t<=T} H(t) <= target and the trial count
     n = log(eps)/log(1-p) .......................... supplementary CCTS section (Eqs. S)
 
-Readings where the paper leaves a choice (each also listed in the design notes):
+Readings where the paper leaves a choice:
   * Coupling scale c (2/sqrt(N) Max-Cut, 1/sqrt(N) SK) is applied after the
     multiply-accumulate, as the fixed-point section describes: b_t = fl32(beta_t * c) and
     the activation argument is x = b_t * I computed in float64 (exact for integer I).

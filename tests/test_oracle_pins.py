@@ -322,6 +322,73 @@ def test_record_matches_per_state_energies():
     assert np.array_equal(E.argmin(axis=0), out["best_t"])
 
 
+def _first_at_or_below(E, target, t_begin=0):
+    """First step t_begin + k whose recorded energy E[k] is <= target, per replica, or -1."""
+    hit = E <= target
+    return np.where(hit.any(axis=0), hit.argmax(axis=0) + t_begin, -1)
+
+
+def test_first_hit_is_the_first_recorded_energy_at_or_below_the_target():
+    """first_hit = the first t in t_begin .. t_begin + sweeps (the final state s(T) included)
+    whose energy is <= target, or -1: checked against the recorded trajectory for a target
+    every replica meets at t = t_begin, a target that only the final state of some replica
+    meets, a target between those, and one that nothing reaches."""
+    inst = sk_pm1(16, 5)
+    T = 20
+    beta = linear_beta(T)
+    kw = dict(replicas=64, seed=1)
+    rec = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5, record=True, **kw)
+    E = rec["energies"].astype(np.int64)                    # (T + 1, R): s(0) .. s(T)
+    # a replica whose final energy is below every earlier one: its first hit at
+    # target = E[T] is the final state s(T)
+    final_only = np.nonzero(E[T] < E[:T].min(axis=0))[0]
+    assert final_only.size > 0, "no replica improves on its last step; change the seed"
+    targets = {"all at t = 0": int(E[0].max()),
+               "final state only": int(E[T, final_only[0]]),
+               "in between": int(np.median(E)),
+               "never": int(E.min()) - 1}
+    for label, target in targets.items():
+        out = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5, target=target, **kw)
+        want = _first_at_or_below(E, target)
+        assert np.array_equal(out["first_hit"], want), label
+    out = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5,
+                        target=targets["all at t = 0"], **kw)
+    assert np.all(out["first_hit"] == 0)
+    out = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5,
+                        target=targets["final state only"], **kw)
+    assert out["first_hit"][final_only[0]] == T
+    out = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5,
+                        target=targets["never"], **kw)
+    assert np.all(out["first_hit"] == -1)
+    # a hit exactly at the target counts (<=, not <)
+    r0 = 3
+    out = oracle.anneal(inst.J, inst.h, inst.c, beta, eta_power(beta), 0.5, target=int(E[5, r0]),
+                        **kw)
+    assert out["first_hit"][r0] <= 5 and E[out["first_hit"][r0], r0] <= E[5, r0]
+
+
+def test_first_hit_counts_absolute_steps_when_resuming():
+    """A run that starts at t_begin reports first hits as schedule steps t_begin + k, and a
+    resumed run keeps a hit found before the resume."""
+    inst = maxcut_er(20, 2)
+    beta = linear_beta(40)
+    eta = eta_power(beta)
+    kw = dict(replicas=32, seed=9, q=1)
+    part = oracle.anneal(inst.J, inst.h, inst.c, beta, eta, 0.7, sweeps=15, record=True, **kw)
+    rest = oracle.anneal(inst.J, inst.h, inst.c, beta, eta, 0.7, t_begin=15, sweeps=25, prev=part,
+                         record=True, **kw)
+    E_rest = rest["energies"].astype(np.int64)              # s(15) .. s(40)
+    target = int(np.median(E_rest))
+    part_t = oracle.anneal(inst.J, inst.h, inst.c, beta, eta, 0.7, sweeps=15, target=target, **kw)
+    rest_t = oracle.anneal(inst.J, inst.h, inst.c, beta, eta, 0.7, t_begin=15, sweeps=25,
+                           prev=part_t, target=target, **kw)
+    E_all = np.concatenate([part["energies"][:15], E_rest]).astype(np.int64)  # s(0) .. s(40)
+    assert np.array_equal(rest_t["first_hit"], _first_at_or_below(E_all, target))
+    fresh = oracle.anneal(inst.J, inst.h, inst.c, beta, eta, 0.7, t_begin=15, sweeps=25,
+                          init=part["final_state"], target=target, **kw)
+    assert np.array_equal(fresh["first_hit"], _first_at_or_below(E_rest, target, t_begin=15))
+
+
 def test_n_trials_closed_forms():
     """n = log(eps)/log(1-p): p = 1/2, eps = 1e-3 gives log2(1000); p = 1 needs one trial."""
     assert math.isclose(oracle.n_trials(0.5), math.log2(1000), rel_tol=1e-12)
