@@ -457,8 +457,11 @@ int pim_thresholds(pim_instance* inst, uint32_t* out, size_t cap_words, int* ste
  *   cuda_stream      cudaStream_t (NULL = legacy default stream); the call returns after the
  *                    anneal has finished on it.
  * Set-up: the first call on a device looks up that device's address of the array
- * (cudaGetSymbolAddress, with the device current); make that first call before any stream
- * capture.
+ * (cudaGetSymbolAddress, with the device current).  Under CUDA's default lazy module
+ * loading that lookup is also what loads the library's device code on that device, and the
+ * load is where the 16 MiB array is reserved (it may synchronise the device).  So the first
+ * call on each device does allocate: make one warm-up call at start-up, before the
+ * real-time part and before any stream capture; later calls allocate nothing.
  * Sharing: every call uses the same array and leaves the last call's contents in it (the
  * error word is cleared at the start of each call).  Calls whose work overlaps on the GPU
  * would race on the array; this entry point serialises its own calls with a host lock and

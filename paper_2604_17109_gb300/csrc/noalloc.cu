@@ -41,6 +41,7 @@ float g_z[kNoiseLevels];
 
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+int g_err_host = 0;  // error word read back after each call
 
 // Byte offsets of the regions inside the scratch array (each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -204,9 +205,12 @@ PIM_API int pim_anneal_noalloc(int n, const int8_t* J, double scale_c, int steps
   L.stride_words_max = kStrideWords;
   L.err = d_err;
   CKN(launch_sweep_tc(L, npad, nwork, st, true), "fused sweep kernel");
+  // The error word comes back on the caller's stream (a copy on the legacy default stream
+  // would also wait for unrelated work on every other blocking stream of the device).
+  g_err_host = 0;
+  CKN(cudaMemcpyAsync(&g_err_host, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word");
   CKN(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-  int h_err = 0;
-  CKN(cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  const int h_err = g_err_host;
   if (h_err & kDevErrTimeout)
     return fail(PIM_ERR_TIMEOUT, "pim_anneal_noalloc: a device-side bounded wait gave up");
   if (h_err) return fail(PIM_ERR_CUDA, "pim_anneal_noalloc: device error bits 0x%x", h_err);

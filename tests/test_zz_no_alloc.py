@@ -64,6 +64,46 @@ def test_noalloc_matches_regular_entry_point_twice():
             assert np.array_equal(got[key], want[key]), (inst.n, key)
 
 
+def test_noalloc_at_the_maximum_sizes_allocates_nothing():
+    """n = 256 (row sums 255, the table limit), the longest schedule and the most replicas
+    the entry point takes: the tables, the diagonal region and the work list are used up
+    to their last offsets.  After a warm-up call (the first call on a device may load the
+    library's device code), a call leaves the device's free memory unchanged."""
+    torch = pytest.importorskip("torch")
+    inst = sk_pm1(256, 7)
+    assert int(np.abs(inst.J.astype(np.int64)).sum(axis=1).max()) == 255
+    P = pim()
+    T, R, xi, seed, q, target = P.PIM_NOALLOC_MAX_STEPS, P.PIM_NOALLOC_MAX_REPLICAS, 0.5, 21, 2, -3000.0
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    _noalloc(inst, linear_beta(8), eta_power(linear_beta(8)), xi, 4, 0, 0, None)  # warm-up
+    words = ((inst.n + 63) // 64) * 2
+    dev = torch.device("cuda", 0)
+    out = {
+        "best_E": torch.empty((R,), dtype=torch.float64, device=dev),
+        "final_E": torch.empty((R,), dtype=torch.float64, device=dev),
+        "best_t": torch.empty((R,), dtype=torch.int32, device=dev),
+        "first_hit": torch.empty((R,), dtype=torch.int32, device=dev),
+        "best_bits": torch.empty((R, words), dtype=torch.int32, device=dev),
+        "final_bits": torch.empty((R, words), dtype=torch.int32, device=dev),
+    }
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info(dev)[0]
+    P.pim_anneal_noalloc(inst.J, inst.c, beta, eta, xi, R, seed, q, target,
+                         {k: v.data_ptr() for k, v in out.items()})
+    torch.cuda.synchronize()
+    free_after = torch.cuda.mem_get_info(dev)[0]
+    assert free_after == free_before, (free_before, free_after)
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    got = dict(best_E=host["best_E"].astype(np.int64), final_E=host["final_E"].astype(np.int64),
+               best_t=host["best_t"].astype(np.int64), first_hit=host["first_hit"].astype(np.int64),
+               best_state=_unpack(host["best_bits"].view(np.uint32), inst.n),
+               final_state=_unpack(host["final_bits"].view(np.uint32), inst.n))
+    want = run_library(inst, beta, eta, xi, replicas=R, seed=seed, q=q, target=target)
+    for key in ("best_E", "best_t", "first_hit", "final_E", "best_state", "final_state"):
+        assert np.array_equal(got[key], want[key]), key
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum():
     P = pim()
     inst = sk_pm1(20, 0)
