@@ -76,12 +76,12 @@ MIMO_RATE = {"mimo16": 4000.0, "mimo64": 1000.0}  # offered load, requests per s
 #   field to table index 2 (float-to-int, address), threshold lookup 1, key extraction 1,
 #   compare and collect the new spin 2, energy accumulate 1, spin write-back 0.75
 ALU_OPS_PER_SPIN_UPDATE = 5.0 + 2 + 1 + 1 + 2 + 1 + 0.75
-SM_COUNT = 152
-LANES_PER_SM = 128
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one instruction each per cycle
 
 # DRAM bytes (read + write) of the dominant kernel per launch, from ncu captures of these
-# workloads (the summaries under profiles/ name the commands), as fixed + per-pass bytes
-# (passes = sweeps + 1):
+# workloads (dram__bytes_read.sum + dram__bytes_write.sum of one launch), as fixed + per-pass
+# bytes (passes = sweeps + 1).  They are recorded values, not measured by this script; a
+# workload whose kernel changed after its capture has no entry here (traffic reported null):
 #   sk200       sweep_tc_kernel<256,0,queue>, full-size launch: 17.86 MB read + 0.03 MB
 #               written, nothing grows per pass
 #   sk4096      sweep_big_kernel<64,FP8>, 50-sweep capture 18.85 MB = 16.8 MB image (L2-resident
@@ -195,88 +195,79 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------- oracle (CPU)
-def _oracle_sample(w: Workload, budget_s: float, max_instances: int, replicas: int,
-                   sweeps: int, first: int = 0):
-    """Time the oracle as it stands on a bounded sample of the workload: the first
-    `sweeps` sweeps of the first instances with `replicas` replicas each (the same
-    per-replica work per sweep as the workload), until the time budget is spent.
-    Returns (spin updates, seconds, description)."""
-    import oracle
-    beta, eta = _schedule(w.sweeps)
-    done, elapsed = 0, 0.0
-    k = 0
+def _oracle_instances(w: Workload):
+    """Generator of (instance, replicas, xi) for the CPU samples, in workload order."""
     if w.kind == "uneven":
         from workloads import uneven_instance, uneven_sizes
-        sizes = uneven_sizes(w.count, seed=0)[0]
-    if w.kind == "fixed":
-        from workloads import maxcut_er
+        sizes, reps = uneven_sizes(w.count, seed=0)
+        for k in range(w.count):
+            yield uneven_instance(k, sizes[k]), int(reps[k]), (0.7 if k % 2 == 0 else 0.5)
+        return
     if w.kind == "mimo":
         from oracle import mimo as om
-        from workloads import Instance, MIMO_XI, mimo_problem, mimo_scale, mimo_schedule
+        from workloads import Instance, mimo_problem, mimo_scale
         nt = w.n // 4
+        for k in range(w.count):
+            mp = mimo_problem(nt, nt, 16, 15.0, k)
+            xm = om.mmse(mp.H, mp.y, 1.0 / mp.es_n0, 4)
+            Jm, hm = om.di_mimo(mp.H, mp.y, xm, [1, 1])
+            yield Instance("mimo", w.n, Jm, hm, mimo_scale(nt), k), w.replicas, w.xi
+        return
+    from workloads import maxcut_er
+    for k in range(w.count):
+        inst = maxcut_er(w.n, k) if w.kind == "fixed" else _instance(w, k)
+        yield inst, w.replicas, w.xi
+
+
+def _cpu_sample(w: Workload, budget_s: float, threads: int):
+    """The C++ oracle as it stands on a bounded sample of the workload, on `threads` host
+    threads (replicas split over them).  Small n: whole instances of the workload (all their
+    sweeps) with min(R, 32) replicas each, instance after instance until the budget is spent
+    (work per replica is the same as in the workload, so the rate extrapolates linearly to
+    the full replica count).  n > 1024: 3 sweeps of 2 x threads replicas of the first
+    instance.  Returns (spin updates, seconds, description)."""
+    from oracle import cpp
+    cpp.build()
+    if w.kind == "mimo":
+        from workloads import mimo_schedule
         beta, eta = mimo_schedule(w.sweeps)
-        mp = mimo_problem(nt, nt, 16, 15.0, 0)
-        xm = om.mmse(mp.H, mp.y, 1.0 / mp.es_n0, 4)
-        Jm, hm = om.di_mimo(mp.H, mp.y, xm, [1, 1])
-        mimo_inst = Instance("mimo", w.n, Jm, hm, mimo_scale(nt), 0)
-    while k < max_instances:
+    else:
+        beta, eta = _schedule(w.sweeps)
+    done, elapsed, k = 0, 0.0, 0
+    big = w.n > 1024
+    for inst, R, xi in _oracle_instances(w):
+        reps = 2 * threads if big else min(R, 32)
+        sweeps = 3 if big else w.sweeps
+        J = inst.J
+        if J.dtype.kind == "f":
+            import oracle
+            J = oracle.round_bf16(J)
         # instance generation is not oracle work: outside the clock
-        kk = first + k
-        inst = (uneven_instance(kk, sizes[kk % len(sizes)]) if w.kind == "uneven"
-                else mimo_inst if w.kind == "mimo"
-                else maxcut_er(w.n, kk) if w.kind == "fixed" else _instance(w, kk))
         t0 = time.perf_counter()
-        oracle.anneal(inst.J, inst.h, inst.c, beta, eta, w.xi, replicas=replicas, seed=0, q=k,
-                      sweeps=min(sweeps, len(beta)))
+        cpp.anneal(J, inst.h, inst.c, beta, eta, xi, replicas=reps, sweeps=sweeps, seed=0, q=k,
+                   threads=threads)
         elapsed += time.perf_counter() - t0
-        done += inst.n * replicas * sweeps
+        done += inst.n * reps * sweeps
         k += 1
-        if elapsed > budget_s:
+        if big or elapsed > budget_s:
             break
-    return done, elapsed, (f"{k} instance(s) x {replicas} replicas x {sweeps} sweeps of the "
-                      f"{w.name} workload, single thread")
-
-
-def _cpu_plan(w: Workload):
-    """(budget s, max instances, replicas, sweeps) of the CPU-baseline sample."""
-    if w.n <= 256:
-        return 15.0, 8, 16, w.sweeps
-    return 10.0, 1, 4, 20
-
-
-def _cpu_worker(argv):
-    w = WORKLOADS[argv[0]]
-    budget, max_inst, reps, sweeps = float(argv[1]), int(argv[2]), int(argv[3]), int(argv[4])
-    first = int(argv[5]) if len(argv) > 5 else 0
-    n, dt, desc = _oracle_sample(w, budget, max_inst, reps, sweeps, first)
-    print(json.dumps({"updates": n, "seconds": dt, "sample": desc}))
+    if big:
+        desc = (f"3 sweeps of 1 instance x {2 * threads} replicas of the {w.name} workload "
+                f"(C++ oracle, {threads} threads)")
+    else:
+        desc = (f"{k} instance(s) of the {w.name} workload, all {w.sweeps} sweeps, "
+                f"min(R, 32) replicas each (C++ oracle, {threads} threads)")
+    if w.kind == "fixed":
+        desc += "; float32 decisions (the oracle's default datapath)"
+    return done, elapsed, desc
 
 
 def cpu_baseline(w: Workload):
-    """The oracle as it stands on the host's cores: one single-threaded oracle process per
-    core (BLAS threads pinned to 1), concurrently, each on its own instances of the sample;
-    value = the sum of their rates."""
-    budget, max_inst, reps, sweeps = _cpu_plan(w)
-    ncpu = os.cpu_count() or 1
-    workers = max(1, min(ncpu, 4 if w.n >= 4096 else 16))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-worker", w.key,
-                               str(budget), str(max_inst), str(reps), str(sweeps),
-                               str(k * max_inst)],
-                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
-             for k in range(workers)]
-    rates, sample = [], None
-    for p in procs:
-        out, err = p.communicate(timeout=900)
-        if p.returncode != 0:
-            raise RuntimeError(err[-2000:])
-        d = json.loads(out.strip().splitlines()[-1])
-        rates.append(d["updates"] / d["seconds"])
-        sample = sample or d["sample"]
-    return {"value": sum(rates), "unit": METRIC, "cores": workers, "kind": "oracle",
-            "sample": f"{workers} concurrent single-thread processes, each: {sample}",
-            "single_thread_value": rates[0]}
+    """The C++ oracle as it stands on every host core (one thread per core)."""
+    cores = os.cpu_count() or 1
+    updates, seconds, desc = _cpu_sample(w, 15.0, cores)
+    return {"value": updates / seconds, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": desc}
 
 
 # ------------------------------------------------------------------------- distributed
@@ -312,27 +303,29 @@ def _barrier(world: int):
 
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args, w: Workload):
+    """The oracle (plain C++17, one thread per host core) on the same workload, metric and
+    unit as our arm: each step is a bounded sample of the workload (see _cpu_sample)."""
     _, rank, _ = _dist()
     if rank != 0:
         return 0
-    _, _, reps, sweeps = _cpu_plan(w)
-    reps = min(reps, 8)
+    cores = os.cpu_count() or 1
     vals, sample = [], None
     for k in range(args.warmup + args.steps):
-        n, dt, sample = _oracle_sample(w, 0.0, 1, reps, sweeps)
+        n, dt, sample = _cpu_sample(w, 6.0, cores)
         if k >= args.warmup:
-            vals.append(n / dt)
-    value = statistics.mean(vals)
-    per_step_updates = w.n * reps * sweeps
+            vals.append((n, dt))
+    updates = sum(n for n, _ in vals)
+    seconds = sum(dt for _, dt in vals)
+    value = updates / seconds
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per_step_updates / value * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "ms_per_step": seconds / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32" if w.kind != "maxcut_gauss"
+        else "f64/f32", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "instances": w.count,
-                   "replicas": w.replicas, "sweeps": w.sweeps,
-                   "sample_per_step": f"1 instance x {reps} replicas x {sweeps} sweeps"},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                   "replicas": w.replicas, "sweeps": w.sweeps, "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -693,14 +686,16 @@ def run_ours(args, w: Workload):
               "kernel_ms": k_ms,
               "peak_basis": (f"bf16 {peak_kind} burst" if real else
                              f"bf16 {peak_kind} burst x 2 (FP8/BF16 nominal ratio)")}
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     if w.n <= 256:
-        alu_peak = SM_COUNT * LANES_PER_SM * sm_max * 1e6 / 1e12
+        alu_peak = sm_count * LANES_PER_SM * sm_max * 1e6 / 1e12
         alu_achieved = updates_per_step * ALU_OPS_PER_SPIN_UPDATE / (k_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
                     "unit": "Tops/s", "frac": alu_achieved / alu_peak, "traffic": None,
                     "kernel": "sweep_tc_kernel<256>", "kernel_ms": k_ms,
                     "ops_per_spin_update": ALU_OPS_PER_SPIN_UPDATE,
-                    "peak_basis": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
+                    "peak_basis": f"{sm_count} SMs (device attribute) x {LANES_PER_SM} lanes x "
+                                  f"{sm_max:.0f} MHz"}
     elif w.kind == "uneven":
         roofline = dict(tensor, kernel="sweep_mid_kernel (+ fused sweep kernels for n <= 256)")
     elif w.n <= 1024 and n_inst > 1:
@@ -717,7 +712,8 @@ def run_ours(args, w: Workload):
     if traffic is not None and args.sweeps is None and args.instances is None:
         fixed, per_pass = traffic
         roofline["traffic"] = fixed + per_pass * (sweeps + 1)
-        roofline["traffic_basis"] = "ncu dram__bytes_read + write of this kernel, fixed + per pass"
+        roofline["traffic_basis"] = ("recorded ncu dram__bytes_read + write of this kernel "
+                                     "(fixed + per pass), not re-measured in this run")
         if w.n > 256:
             hbm = roofline["traffic"] / (k_ms * 1e-3) / 1e9
             roofline["hbm"] = {"achieved": hbm, "unit": "GB/s",
@@ -755,9 +751,6 @@ def run_ours(args, w: Workload):
 
 
 def main():
-    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-worker":
-        _cpu_worker(sys.argv[2:])
-        return 0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

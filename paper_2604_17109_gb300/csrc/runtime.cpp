@@ -1597,11 +1597,11 @@ int finish_run(pim_instance* const* insts, int count, const int* replicas,
   return PIM_OK;
 }
 
-// Results to host for many instances: one gather launch on st writes every instance's
-// result block into its mapped pinned buffer (one copy command per instance would fill the
-// launch queue behind a long run).  *copied = false when some buffer has no device address
-// (finish_run then copies instance by instance).
-constexpr int kGatherMin = 1;
+// Results to host: one gather launch on st writes every instance's result block into its
+// mapped pinned buffer, whatever the instance count (a single instance included): a copy
+// command per instance would fill the launch queue behind a long run, and copy-engine
+// commands from different streams queue behind each other.  *copied = false when some
+// buffer has no device address; finish_run then copies instance by instance instead.
 
 int gather_results(pim_instance* const* insts, int count, cudaStream_t st, bool* copied) {
   *copied = false;
@@ -1652,7 +1652,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   CK(cudaFreeAsync(d_buf, st), "cudaFreeAsync launch buffer");
   const bool to_host = (flags & PIM_RESULTS_TO_HOST) != 0;
   bool copied = false;
-  if (to_host && count >= kGatherMin && (rc = gather_results(insts, count, st, &copied)) != PIM_OK)
+  if (to_host && (rc = gather_results(insts, count, st, &copied)) != PIM_OK)
     return rc;
   return finish_run(insts, count, replicas, timer, st, to_host, copied);
 }
@@ -1849,7 +1849,7 @@ PIM_API int pim_batch_run(pim_batch* b, int t_begin, int sweeps, uint64_t seed, 
   }
   const bool to_host = (run_flags & PIM_RESULTS_TO_HOST) != 0;
   bool copied = false;
-  if (to_host && count >= kGatherMin &&
+  if (to_host &&
       (rc = gather_results(b->insts.data(), count, st, &copied)) != PIM_OK)
     return rc;
   return finish_run(b->insts.data(), count, b->replicas.data(), b->timer, st, to_host, copied);
