@@ -64,6 +64,9 @@ WORKLOADS = {
     # fixed-point study: Max-Cut N = 100 (config 1) over 20 instances, float32 vs ap_fixed
     "fixed100": Workload("fixed100", "fixed", 100, 20, 64, 1000, 0.7),
     "mimo16": Workload("mimo16", "mimo", 64, 2000, 32, 64, 1.0),
+    # fixed-point MIMO study: BER of 16x16 16-QAM detection vs datapath word length and LUT
+    # levels (ap_fixed<W, 4> couplings and intermediates), 1000 problems
+    "mimofixed16": Workload("mimofixed16", "mimofixed", 64, 1000, 32, 64, 1.0),
     "mimo64": Workload("mimo64", "mimo", 256, 400, 32, 256, 1.0),
 }
 MIMO_RATE = {"mimo16": 4000.0, "mimo64": 1000.0}  # offered load, requests per second
@@ -408,6 +411,91 @@ def run_fixed(args, w: Workload):
     return 0
 
 
+def run_mimo_fixed(args, w: Workload):
+    """Bit-error rate of 16x16 16-QAM detection against the word length W and the tanh LUT
+    levels of the fixed-point datapath (supplementary quantization section; ap_fixed<W, 4>
+    for the couplings Q(c J), the bias and every intermediate; the paper's MIMO design uses
+    <16, 4>), next to the float32 datapath and the MMSE baseline, on the same problems,
+    draws and kernels.  Per problem the replica of lowest best energy is detected.
+    value: spin updates/s of the ap_fixed<16, 4> batch (device-resident)."""
+    world, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2604_17109_gb300 import build as pkg_build
+    from paper_2604_17109_gb300 import pim
+    from workloads import MIMO_XI, bits_from_symbols, mimo_problem, mimo_scale, mimo_schedule
+
+    pkg_build.build()
+    nt = w.n // 4
+    count, R, T = w.count, w.replicas, w.sweeps
+    rng = np.random.default_rng(2000 + rank)
+    snr = rng.uniform(10.0, 25.0, count)
+    probs = [mimo_problem(nt, nt, 16, float(v), rank * count + k) for k, v in enumerate(snr)]
+    staged = [pim.pim_mimo_formulate(p.H, p.y, 16, 1.0 / p.es_n0) for p in probs]
+    beta, eta = mimo_schedule(T)
+    c = mimo_scale(nt)
+    handles = [pim.pim_create(J, h, c) for J, h, _ in staged]
+    bits = np.stack([p.bits for p in probs])
+    ber_mmse = float(np.mean(bits != np.stack([bits_from_symbols(xm, 16) for _, _, xm in staged])))
+    configs = [("float32", None, "tanh", 4)] + \
+              [(f"fixed<{W},4>", (W, 4), "tanh", 4) for W in (6, 8, 10, 12, 14, 16)] + \
+              [(f"fixed<16,4> lut{L}", (16, 4), "lut", L) for L in (4, 8, 16, 32)]
+    stream = torch.cuda.Stream()
+    study, timing = {}, {}
+    ids = list(range(count))
+    with ClockSampler(local) as clocks:
+        for name, fmt, act, L in configs:
+            for hd in handles:
+                if fmt is None:
+                    pim.pim_set_schedule(hd, beta, eta, MIMO_XI, act=act, lut_levels=L)
+                else:
+                    pim.pim_set_schedule_fixed(hd, beta, eta, MIMO_XI, fmt[0], fmt[1], act=act,
+                                               lut_levels=L)
+            for _ in range(max(1, args.warmup)):
+                pim.pim_anneal_batch(handles, R, T, seed=7, instance_ids=ids, stream=stream)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pim.pim_anneal_batch(handles, R, T, seed=7, instance_ids=ids, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            timing[name] = statistics.mean(ms)
+            detected = []
+            for hd, (_, _, xm) in zip(handles, staged):
+                best = pim.pim_energies(hd)["best_E"]
+                s = pim.pim_best_state(hd, w.n)[int(np.argmin(best))]
+                detected.append(bits_from_symbols(pim.pim_mimo_reconstruct(xm, s, 16), 16))
+            study[name] = {"ber": float(np.mean(bits != np.stack(detected))),
+                           "ms_per_batch": timing[name]}
+    for hd in handles:
+        pim.pim_destroy(hd)
+    if rank != 0:
+        return 0
+    updates = count * w.n * R * T
+    ms = timing["fixed<16,4>"]
+    line = {
+        "metric": METRIC, "value": updates / (ms * 1e-3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2/f32 (ap_fixed<16,4> datapath)",
+        "data": "synthetic",
+        "config": {"workload": f"mimo{nt}x{nt}_16qam_{count}req_{R}rep_{T}sweeps_fixed_point_study",
+                   "channel": "i.i.d. Rayleigh CN(0,1), Eb/N0 ~ U[10,25] dB, 16-QAM Gray",
+                   "schedule": "beta=1, eta=sqrt(1/(5 gamma)), gamma 0.01->1, xi=1, c=2/Nr",
+                   "detection": "replica of lowest best energy, its best state"},
+        "study": study, "ber_mmse": ber_mmse,
+        "cpu_baseline": cpu_baseline(dataclasses.replace(w, kind="mimo")),
+        "e2e": None,
+        "gpu_launches": 2 * args.steps * len(configs),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_mimo(args, w: Workload):
     """MIMO detection serving (16-QAM, Rayleigh, Eb/N0 ~ U[10, 25] dB per request).
     value: device-resident throughput of all requests as one batch plan (instances staged
@@ -420,7 +508,6 @@ def run_mimo(args, w: Workload):
     from paper_2604_17109_gb300 import build as pkg_build
     from paper_2604_17109_gb300 import pim
     from workloads import (MIMO_XI, bits_from_symbols, mimo_problem, mimo_scale, mimo_schedule)
-    from oracle import mimo as om  # verification only: MMSE baseline BER
 
     pkg_build.build()
     nt = w.n // 4
@@ -475,9 +562,9 @@ def run_mimo(args, w: Workload):
     finally:
         pim.pim_mimo_server_destroy(srv)
     bits = np.stack([p.bits for p in probs])
-    ber_pimi = om.ber(bits, bits_from_symbols(xh, 16))
-    ber_mmse = om.ber(bits, np.stack([bits_from_symbols(om.mmse(p.H, p.y, r, 4), 16)
-                                      for p, r in zip(probs, regs)]))
+    ber_pimi = float(np.mean(bits != bits_from_symbols(xh, 16)))
+    # the MMSE baseline: the hard-sliced MMSE estimate the library's formulation starts from
+    ber_mmse = float(np.mean(bits != np.stack([bits_from_symbols(xm, 16) for _, _, xm in staged])))
     if rank != 0:
         return 0
     peaks, peak_kind = _peaks()
@@ -671,6 +758,26 @@ def run_ours(args, w: Workload):
                                   "sample": f"{n_plain} instance(s), one warp per replica, "
                                             "n single-spin updates per sweep"}}
 
+    # ---- BF16 field error of the real-coupling kernel (Eq. 2), as a number -------------
+    # fields the kernel forms from 64 random states of instance 0 against float64 fields of
+    # the BF16-rounded and of the original couplings:
+    #   max / mean of |I_gpu - I_64| / max(|I_64|, ||J_i||_1 2^-8)
+    field_error = None
+    if real:
+        from workloads import random_spins
+        S = random_spins(insts[0].n, 64, 5)
+        I_gpu = pim.pim_fields(handles[0], S).astype(np.float64)
+        field_error = {}
+        # round to nearest BF16 (8 significant bits, ties to even) in float64
+        mant, expo = np.frexp(insts[0].J)
+        J_bf16 = np.ldexp(np.rint(mant * 256.0), expo - 8)
+        for label, J in (("vs_bf16_J", J_bf16), ("vs_original_J", insts[0].J)):
+            I64 = S.astype(np.float64) @ J.T
+            floor = np.abs(J).sum(axis=1)[None, :] * 2.0 ** -8
+            err = np.abs(I_gpu - I64) / np.maximum(np.abs(I64), floor)
+            field_error[label] = {"max": float(err.max()), "mean": float(err.mean())}
+        field_error["sample"] = "instance 0, 64 random states, all spins"
+
     for hd in handles:
         pim.pim_destroy(hd)
 
@@ -736,6 +843,7 @@ def run_ours(args, w: Workload):
         "roofline": roofline,
         "tensor_pipe": tensor,
         "tts99": tts,
+        "field_error": field_error,
         "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
@@ -768,6 +876,8 @@ def main():
         return run_reference(args, w)
     if w.kind == "mimo":
         return run_mimo(args, w)
+    if w.kind == "mimofixed":
+        return run_mimo_fixed(args, w)
     if w.kind == "fixed":
         return run_fixed(args, w)
     return run_ours(args, w)

@@ -142,10 +142,21 @@ int pim_set_schedule(pim_instance* inst, int steps, const float* beta, const flo
  *   u = Q(c I)  (normalisation after the multiply-accumulate),  x = Q(beta_t u),
  *   tau = Q(tanh(x)) or Q(L-level staircase(x)),  a = Q(tau + s Q(xi)),
  *   n = Q(Q(eta_t) Q(z)),  s' = +1 iff Q(a + n) >= 0.
- * The paper uses <4,2> for Max-Cut / SK and <16,4> for MIMO.  The decision stays monotone
- * in the noise key, so the same kernels run it from exact key thresholds, built on the host.
- *   total_bits in [2, 32], int_bits in [1, total_bits]; integer couplings only.
- * Errors: PIM_ERR_INVALID, PIM_ERR_UNSUPPORTED (real couplings), PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ * The paper uses <4,2> for Max-Cut / SK and <16,4> for MIMO.
+ * Integer couplings: the decision stays monotone in the noise key, so the same kernels run
+ * it from exact key thresholds, built on the host.
+ * Real couplings (n <= 128, total_bits <= 16; the MIMO pipeline of the paper): the couplings
+ * and bias are stored in the format too, with the scale folded in: J_q = Q(c J), h_q = Q(c h)
+ * (values of order one, as the FPGA holds them); the field I = J_q s + h_q is accumulated
+ * exactly and u = Q(I).  The device holds J_q as two BF16 images whose sum is exact and
+ * evaluates the datapath above on integers in units of 2^-(total_bits - int_bits), with
+ * tau read from a table of Q(tanh(x)) (or the staircase) over every representable x.
+ * Energies and targets of such a run are those of the quantized, scaled problem
+ * -1/2 s^T J_q s - h_q^T s (exact).
+ *   total_bits in [2, 32], int_bits in [1, total_bits].
+ * Errors: PIM_ERR_INVALID, PIM_ERR_UNSUPPORTED (real couplings with n > 128 or
+ *         total_bits > 16, or a row of J_q whose exact sum needs more than 2^24 units),
+ *         PIM_ERR_NOMEM, PIM_ERR_CUDA.
  */
 int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* beta, const float* eta,
                            float xi, int noise_kind, int act_kind, int lut_levels, int total_bits,
@@ -335,6 +346,27 @@ void pim_mimo_server_destroy(pim_mimo_server* server);
 int pim_results_dev(pim_instance* inst, double* best_E, int32_t* best_t, int32_t* first_hit_t,
                     double* final_E, uint32_t* best_bits, uint32_t* final_bits, void* cuda_stream);
 int pim_state_words(const pim_instance* inst);
+
+/*
+ * pim_fields -- diagnostic read-out of the local fields of Eq. 2, I_i = sum_j J_ij s_j + h_i,
+ * exactly as the sweep kernel of a real-coupling instance forms them (J rounded to BF16,
+ * FP32 accumulation in tensor memory, + h in FP32) and feeds them to its Eq. 4 decision.
+ * It runs sweep 0 of the instance's schedule from the given states on the kernel the instance
+ * is routed to (the fused real-valued kernel for n <= 256, the large-N kernel otherwise) with
+ * the kernel's field capture switched on, then returns the captured fields.  This is how the
+ * BF16 field error against a float64 evaluation is measured.
+ *   inst        real-coupling instance (PIM_J_FP32 / PIM_J_FP64) with a schedule.
+ *   replicas    R >= 1 states.
+ *   spins       host int8 R x n of -1/+1: s for each replica.
+ *   fields      host float32 R x n output, row-major (replica, spin).
+ *   flags       0 or PIM_PATH_BIG (no effect for n <= 256).
+ *   cuda_stream cudaStream_t; the call returns when the fields are in `fields`.
+ * The instance's records (pim_energies, ...) afterwards are those of this one-sweep run.
+ * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (no schedule), PIM_ERR_UNSUPPORTED (integer couplings:
+ *         their fields are exact integers), PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ */
+int pim_fields(pim_instance* inst, int replicas, const int8_t* spins, float* fields, int flags,
+               void* cuda_stream);
 
 /* pim_sync -- block until the instance's last anneal has finished.
  * Errors: PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a device-side bounded wait gave up).

@@ -116,4 +116,22 @@ void fixed_thresholds(double c, float beta_t, float eta_t, float xi, int act, in
   }
 }
 
+int32_t fixed_units(double v, int total_bits, int int_bits) {
+  const FixedFormat Q(total_bits, int_bits);
+  return static_cast<int32_t>(std::llround(Q(v) / Q.step));  // exact: Q(v) is on the grid
+}
+
+void fixed_real_tables(int total_bits, int int_bits, int act, int lut_levels, float xi,
+                       const float* z, int32_t* tau, int32_t* qz, int32_t* qxi) {
+  const FixedFormat Q(total_bits, int_bits);
+  const long long half = 1ll << (total_bits - 1);
+  for (long long m = -half; m < half; ++m) {
+    const double x = static_cast<double>(m) * Q.step;
+    const double v = Q(act == 0 ? std::tanh(x) : staircase(x, lut_levels));
+    tau[m + half] = static_cast<int32_t>(std::llround(v / Q.step));
+  }
+  for (int k = 0; k < kNoiseLevels; ++k) qz[k] = fixed_units(static_cast<double>(z[k]), total_bits, int_bits);
+  *qxi = fixed_units(static_cast<double>(xi), total_bits, int_bits);
+}
+
 }  // namespace pim

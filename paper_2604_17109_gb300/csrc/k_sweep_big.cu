@@ -312,6 +312,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         if (warp_active) {
           const uint32_t* tab = nullptr;
           float b = 0.0f, eta = 0.0f;
+          float* dump = nullptr;  // diagnostics: fields of the first sweep (real couplings)
+          if (REAL && P.fields_out != nullptr && t == t_begin && !last && row_valid)
+            dump = P.fields_out + static_cast<size_t>(r) * n + col0;
           if constexpr (REAL) {
             if (!last) {
               b = P.sched_b[t];
@@ -343,6 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
               if constexpr (REAL) {
                 const float hv = __uint_as_float(sH[grp * kSPT + bit]);
                 const float I = __fadd_rn(__uint_as_float(v[e]), hv);
+                if (dump != nullptr && col0 + bit < n) dump[bit] = I;
                 const float term = __fadd_rn(I, hv);
                 eacc += s ? term : -term;
                 if (!last) {

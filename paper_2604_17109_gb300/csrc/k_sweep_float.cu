@@ -10,6 +10,13 @@
 //             delta = (tau + xi s) + eta_t z(key), s' = +1 iff delta >= 0, with the same
 //             Philox draws and 4096 noise levels as the integer path.
 //   energy    H = -1/2 sum_i s_i (I_i + h_i) accumulated in FP32.
+// Fixed-point datapath (P.fix_w > 0, npad 128): the couplings are Q(c J) in
+// ap_fixed<W, W - F> (supplementary quantization section), held as two BF16 images whose sum
+// is exact (high part + low part), so the two MMA chains give the exact field I in FP32
+// (|I| 2^F < 2^24).  The decision then follows the datapath on integers in units of 2^-F:
+//   u = sat(I), x = Q(fl32(beta_t) u), tau = table(x), a = sat(tau + s Q(xi)),
+//   n = sat(trunc(Q(eta_t) Q(z) / 2^F)), s' = +1 iff sat(a + n) >= 0,
+// and the energy is summed exactly in integers.
 #include <cfloat>
 
 #include "kernels.h"
@@ -22,16 +29,34 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTileM = 128;
 
+// Fixed-point decision of one spin (see the header): integers in units of 2^-F.
+__device__ __forceinline__ uint32_t fixed_decide(float I, uint32_t s, float beta, int eta_q,
+                                                 int z_q, int xi_q, int F, int half_range,
+                                                 const int32_t* __restrict__ tau_tab) {
+  const int lo = -half_range, hi = half_range - 1;
+  const int mI = __float2int_rz(__fmul_rn(I, __int_as_float((127 + F) << 23)));  // I 2^F, exact
+  const int mu = min(max(mI, lo), hi);
+  // Q(beta u): the product of a 24-bit and a 16-bit integer is exact in double
+  long long mx = static_cast<long long>(__dmul_rn(static_cast<double>(beta), static_cast<double>(mu)));
+  mx = mx < lo ? lo : (mx > hi ? hi : mx);
+  const int mt = __ldg(tau_tab + (mx + half_range));
+  const int ma = min(max(mt + (s ? xi_q : -xi_q), lo), hi);
+  const int mn = min(max((eta_q * z_q) / (1 << F), lo), hi);  // truncation toward zero
+  const int md = min(max(ma + mn, lo), hi);
+  return md >= 0 ? 1u : 0u;
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L) {
   constexpr int kMaxSlots = NPAD / 32;
   constexpr int kWordsPerThread = kMaxSlots / 2;
   constexpr int kRowBytes = 2 * NPAD;  // bytes of one operand row (K = NPAD BF16 values)
+  constexpr bool kCanFix = NPAD == 128;  // room for the second coupling image
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint8_t* sJ = smem;                                  // NPAD x kRowBytes
-  uint8_t* sA = sJ + NPAD * kRowBytes;                 // 128 x kRowBytes
+  uint8_t* sJ = smem;                                  // NPAD x kRowBytes (x2: high | low part)
+  uint8_t* sA = sJ + (kCanFix ? 2 : 1) * NPAD * kRowBytes;  // 128 x kRowBytes
   float* sZ = reinterpret_cast<float*>(sA + kTileM * kRowBytes);  // 4096
   float* sH = sZ + 4096;                               // NPAD
   float* sPart = sH + NPAD;                            // [2][2][128]
@@ -60,6 +85,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
   const uint32_t bar_j = smem_u32(&bars[1]);
   const float xi = P.xi;
   const int act = P.act, levels = P.lut_levels;
+  const bool fixed = kCanFix && P.fix_w > 0;
+  const int fix_f = P.fix_f, fix_half = fixed ? 1 << (P.fix_w - 1) : 0, fix_xi = P.fix_xi;
+  const float fix_scale = __int_as_float((127 + fix_f) << 23);  // 2^F
 
   if (warp == 0) {
     tmem_alloc(smem_u32(sTmem), NPAD);
@@ -73,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
   }
   for (int k = tid; k < kTileM * kRowBytes / 16; k += kThreads)
     reinterpret_cast<uint4*>(sA)[k] = make_uint4(0, 0, 0, 0);
-  for (int k = tid; k < 4096; k += kThreads) sZ[k] = P.zlev[k];
+  for (int k = tid; k < 4096; k += kThreads) sZ[k] = fixed ? __int_as_float(P.fix_z[k]) : P.zlev[k];
   for (int k = tid; k < NPAD; k += kThreads) sH[k] = (P.hf != nullptr && k < n) ? P.hf[k] : 0.0f;
   tc_fence_before();
   __syncthreads();
@@ -82,10 +110,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
   const uint32_t tmem_warp = tmem + (static_cast<uint32_t>(quad * 32) << 16);
   if (tid == 0) {
     constexpr uint32_t kJBytes = NPAD * kRowBytes;
-    mbar_expect_tx(bar_j, kJBytes);
-    for (uint32_t off = 0; off < kJBytes; off += 16384)
-      bulk_g2s(smem_u32(sJ + off), P.jimg + off, 16384u < kJBytes - off ? 16384u : kJBytes - off,
-               bar_j);
+    mbar_expect_tx(bar_j, fixed ? 2 * kJBytes : kJBytes);
+    for (int part = 0; part < (fixed ? 2 : 1); ++part) {
+      const uint8_t* src = part ? P.jimg_lo : P.jimg;
+      for (uint32_t off = 0; off < kJBytes; off += 16384)
+        bulk_g2s(smem_u32(sJ + part * kJBytes + off), src + off,
+                 16384u < kJBytes - off ? 16384u : kJBytes - off, bar_j);
+    }
   }
 
   uint32_t cur[kWordsPerThread], best[kWordsPerThread];
@@ -97,12 +128,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
     for (int k = 0; k < kMaxSlots; ++k)
       if (k < myc) cur[k >> 1] |= static_cast<uint32_t>(cur_in[static_cast<size_t>(rg) * P.words * 2 + (c0 + k)]) << ((k & 1) * 16);
   }
-  float best_E = FLT_MAX;
+  double best_E = DBL_MAX;  // float32 energies (float mode) or exact ones (fixed mode)
   int best_t = -1, first_hit = -1;
   const bool has_target = P.has_target != 0;
   const double target = P.target_f;
   if (L.cont && row_valid) {
-    best_E = static_cast<float>(P.best_E[rg]);
+    best_E = P.best_E[rg];
     best_t = P.best_t[rg];
     first_hit = P.first_hit[rg];
     const uint16_t* best_in = reinterpret_cast<const uint16_t*>(P.best_bits);
@@ -133,11 +164,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
   const uint32_t idesc = idesc_bf16(kTileM, mma_n);
   const uint32_t sA_addr = smem_u32(sA), sJ_addr = smem_u32(sJ);
   auto issue_fields = [&]() {
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
-      mma_bf16(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
-               sw128_desc(sJ_addr + kb * (NPAD * 128) + ko), idesc, ks > 0 ? 1u : 0u);
-    }
+    for (int part = 0; part < (fixed ? 2 : 1); ++part)  // fixed mode: high part, then low part
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t kb = ks >> 2, ko = (ks & 3) * 32;
+        mma_bf16(tmem, sw128_desc(sA_addr + kb * (kTileM * 128) + ko),
+                 sw128_desc(sJ_addr + part * (NPAD * kRowBytes) + kb * (NPAD * 128) + ko), idesc,
+                 (ks > 0 || part > 0) ? 1u : 0u);
+      }
     mma_commit(bar_mma);
   };
   if (tid == 0) {
@@ -163,10 +196,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
     tc_fence_after();
     const float b = last ? 0.0f : P.sched_b[t];
     const float eta = last ? 0.0f : P.sched_eta[t];
+    const int eta_q = (fixed && !last) ? P.fix_eta[t] : 0;
+    float* dump = (P.fields_out != nullptr && t == t_begin && !last && row_valid)
+                      ? P.fields_out + static_cast<size_t>(rg) * n
+                      : nullptr;
     uint32_t nxt[kWordsPerThread];
 #pragma unroll
     for (int w = 0; w < kWordsPerThread; ++w) nxt[w] = 0;
     float eacc = 0.0f;
+    int ieacc = 0;  // fixed mode: sum_i s_i (I_i + h_i) in units of 2^-F, exact
     if (warp_active) {
 #pragma unroll
       for (int k = 0; k < kMaxSlots; ++k) {
@@ -189,7 +227,20 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
           for (int e = 0; e < 16; ++e) {
             const float hv = sH[c * 16 + e];
             const float I = __fadd_rn(__uint_as_float(v[e]), hv);
+            if (dump != nullptr && c * 16 + e < n) dump[c * 16 + e] = I;
             const uint32_t s = (ob >> e) & 1u;
+            if (fixed) {
+              const int term = __float2int_rz(__fmul_rn(__fadd_rn(I, hv), fix_scale));
+              ieacc += s ? term : -term;
+              if (!last) {
+                const uint32_t word = rw[e >> 1];
+                const uint32_t key = (e & 1) ? (word >> 20) : ((word >> 4) & 0xFFFu);
+                nb |= fixed_decide(I, s, b, eta_q, __float_as_int(sZ[key]), fix_xi, fix_f, fix_half,
+                                   P.fix_tau)
+                      << e;
+              }
+              continue;
+            }
             const float term = __fadd_rn(I, hv);
             eacc += s ? term : -term;
             if (!last) {
@@ -209,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
         }
       }
     }
-    sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = fixed ? __int_as_float(ieacc) : eacc;
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -219,15 +270,17 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
       tc_fence_after();
       issue_fields();
     }
-    const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
-    const float E = -0.5f * etot;
+    const float other = sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    // the quadratic form is even in units of 2^-F: symmetric couplings, zero diagonal
+    const double E = fixed ? -static_cast<double>((ieacc + __float_as_int(other)) / 2) / fix_scale
+                           : static_cast<double>(-0.5f * (eacc + other));
     if (E < best_E) {
       best_E = E;
       best_t = t;
 #pragma unroll
       for (int w = 0; w < kWordsPerThread; ++w) best[w] = cur[w];
     }
-    if (has_target && first_hit < 0 && static_cast<double>(E) <= target) first_hit = t;
+    if (has_target && first_hit < 0 && E <= target) first_hit = t;
     if (last) {
       if (row_valid) {
         uint16_t* cur_out = reinterpret_cast<uint16_t*>(P.cur_bits);
@@ -240,10 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_float_kernel(const Launch L
             best_out[o] = static_cast<uint16_t>(best[k >> 1] >> ((k & 1) * 16));
           }
         if (half == 0) {
-          P.best_E[rg] = static_cast<double>(best_E);
+          P.best_E[rg] = best_E;
           P.best_t[rg] = best_t;
           P.first_hit[rg] = first_hit;
-          P.final_E[rg] = static_cast<double>(E);
+          P.final_E[rg] = E;
         }
       }
     } else {
@@ -270,7 +323,8 @@ cudaError_t launch_float_variant(const Launch& L, int blocks, cudaStream_t st) {
 }  // namespace
 
 int sweep_float_smem_bytes(int npad) {
-  return 1024 + npad * 2 * npad + kTileM * 2 * npad + 4096 * 4 + npad * 4 + 2 * 2 * kTileM * 4 + 64;
+  return 1024 + (npad <= 128 ? 2 : 1) * npad * 2 * npad + kTileM * 2 * npad + 4096 * 4 +
+         npad * 4 + 2 * 2 * kTileM * 4 + 64;
 }
 
 cudaError_t launch_sweep_float(const Launch& L, int npad, int blocks, cudaStream_t st) {

@@ -47,6 +47,20 @@ struct Problem {
   // D = I + dk s, [steps][4 dk].  dk = 0: general table.
   int dk;
   int e5m2;
+  // Diagnostics (real couplings): when set, the kernel writes the FP32 fields
+  // I = sum_j J_ij s_j + h_i of the run's first sweep, [R][n] row-major, as its decision
+  // uses them.
+  float* fields_out;
+  // Real couplings in the fixed-point datapath (fix_w > 0; ap_fixed<fix_w, fix_w - fix_f>,
+  // values held as integers in units of 2^-fix_f): jimg and jimg_lo are the BF16 images of
+  // the high and low parts of Q(c J) (their sum is exact), hf = Q(c h), sched_b = fl32(beta_t)
+  // (c is folded into the couplings), and the decision runs on the integer tables below.
+  const uint8_t* jimg_lo;
+  int fix_w, fix_f;
+  const int32_t* fix_tau;  // [2^fix_w]: Q(act(x)) for x = (m - 2^(fix_w-1)) 2^-fix_f
+  const int32_t* fix_eta;  // [steps]: Q(eta_t)
+  const int32_t* fix_z;    // [4096]: Q(z(key))
+  int fix_xi;              // Q(xi)
 };
 
 // One block copy of a gather launch: `bytes` (a multiple of 16) from src to dst, both

@@ -53,6 +53,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int kMaxN = 8192;        // plain path limit
 constexpr int kMaxNTensor = 256;   // fused kernel limit
+constexpr int kMaxNFixedReal = 128;  // fixed-point real couplings: two coupling images fit in
+                                     // the fused real-valued kernel's shared memory
 constexpr int kMaxImaxTensor = 511;
 constexpr int kMaxImaxDiag = 255;  // |I| < 256: D = I + 256 s keeps the sign of s
 constexpr int kMaxDiagK = 2048;    // widest diagonal of the E5M2 images (table of 4K entries)
@@ -82,8 +84,16 @@ struct Schedule {
   float xi = 0.0f;
   int act = 0, lut = 0;
   int device = 0;
+  // Real couplings in the fixed-point datapath (fix_w > 0): d_bt holds fl32(beta_t) (the
+  // scale c is folded into the quantized couplings) and the decision uses these integer
+  // tables, in units of 2^-(fix_w - fix_i).
+  int fix_w = 0, fix_i = 0;
+  int32_t* d_fix_tau = nullptr;  // [2^fix_w] Q(act(x))
+  int32_t* d_fix_eta = nullptr;  // [steps] Q(eta_t)
+  int32_t* d_fix_z = nullptr;    // [4096] Q(z)
+  int32_t fix_xi = 0;            // Q(xi)
   ~Schedule() {
-    if (d_thr || d_thr_diag || d_thr_dk || d_bt) {
+    if (d_thr || d_thr_diag || d_thr_dk || d_bt || d_fix_tau) {
       int prev = 0;
       cudaGetDevice(&prev);
       cudaSetDevice(device);
@@ -93,6 +103,9 @@ struct Schedule {
       cudaFree(d_bt);
       cudaFree(d_eta);
       cudaFree(d_z);
+      cudaFree(d_fix_tau);
+      cudaFree(d_fix_eta);
+      cudaFree(d_fix_z);
       cudaSetDevice(prev);
     }
   }
@@ -354,6 +367,15 @@ struct pim_instance {
   int dk5 = 0;
   bool real = false;  // real-valued couplings: BF16 operand image, float bias
   float* d_hf = nullptr;
+  // Fixed-point datapath of real couplings (n <= kMaxNFixedReal): the couplings and bias as
+  // given (float64), and the device block built from them for format (fix_w, fix_i):
+  // BF16 images of the high and low parts of Q(c J), then Q(c h) as float32.
+  std::vector<double> host_J, host_h;
+  char* d_fix = nullptr;
+  uint8_t* d_fix_hi = nullptr;
+  uint8_t* d_fix_lo = nullptr;
+  float* d_fix_h = nullptr;
+  int fix_w = 0, fix_i = 0;
   char* d_slab = nullptr;   // J8 | image | bias (one pool block)
   char* d_res = nullptr;    // results (one pool block)
   cudaEvent_t ready = nullptr;  // staging of the inputs done
@@ -769,6 +791,13 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
   if (!p) return fail(PIM_ERR_NOMEM, "pim_create: host allocation failed");
   cudaGetDevice(&p->device);
   p->real = true;
+  if (n <= kMaxNFixedReal) {  // kept for pim_set_schedule_fixed
+    p->host_J.resize(static_cast<size_t>(n) * n);
+    p->host_h.assign(n, 0.0);
+    for (size_t k = 0; k < p->host_J.size(); ++k) p->host_J[k] = at(J, k);
+    if (h)
+      for (int i = 0; i < n; ++i) p->host_h[i] = at(h, i);
+  }
   p->n = n;
   p->npad = n <= 128 ? 128 : (n <= 256 ? 256 : ((n + 127) / 128) * 128);
   p->words = ((n + 63) / 64) * 2;
@@ -1031,16 +1060,131 @@ int build_fixed_schedule(std::shared_ptr<Schedule>& out, int steps, const float*
   return PIM_OK;
 }
 
+double bf16_value(uint16_t bits) {
+  const uint32_t u = static_cast<uint32_t>(bits) << 16;
+  float f;
+  std::memcpy(&f, &u, sizeof f);
+  return static_cast<double>(f);
+}
+
+// Device block of a real instance for the fixed-point datapath ap_fixed<W, I>: the couplings
+// Q(c J) (scale folded in, so the stored values are of order one) as two BF16 images whose
+// sum is exact -- the high part rounds Q(c J) to 8 significant bits, the low part holds the
+// remaining at most 8 bits -- and the bias Q(c h) as float32 (exact).  The MMA then sums
+// integers times 2^-F exactly as long as every row's sum stays below 2^24 units.
+int build_fixed_images(pim_instance* p, int W, int I) {
+  if (p->d_fix && p->fix_w == W && p->fix_i == I) return PIM_OK;
+  const int n = p->n, npad = p->npad;
+  const double step = std::ldexp(1.0, I - W);
+  const size_t nn = static_cast<size_t>(n) * n;
+  std::vector<uint16_t> bits(2 * nn);
+  std::vector<float> hq(npad, 0.0f);
+  for (int i = 0; i < n; ++i) {
+    long long units = 0;
+    for (int j = 0; j < n; ++j) {
+      const int32_t m = fixed_units(p->c * p->host_J[static_cast<size_t>(i) * n + j], W, I);
+      const double v = static_cast<double>(m) * step;
+      const uint16_t hb = bf16_bits_rne(v);
+      const double lv = v - bf16_value(hb);
+      const uint16_t lb = bf16_bits_rne(lv);
+      if (bf16_value(lb) != lv)
+        return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: Q(c J[%d][%d]) needs more than "
+                                         "two BF16 parts", i, j);
+      bits[static_cast<size_t>(i) * n + j] = hb;
+      bits[nn + static_cast<size_t>(i) * n + j] = lb;
+      units += m < 0 ? -m : m;
+    }
+    const int32_t mh = fixed_units(p->c * p->host_h[i], W, I);
+    hq[i] = static_cast<float>(static_cast<double>(mh) * step);
+    units += mh < 0 ? -mh : mh;
+    if (units >= (1ll << 24))
+      return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: row %d of Q(c J) sums to %lld "
+                                       "units of 2^-%d (FP32 accumulation exact below 2^24)",
+                  i, units, W - I);
+  }
+  DeviceCtx* ctx = device_ctx(p->device);
+  if (!ctx) return fail(PIM_ERR_NOMEM, "pim_set_schedule_fixed: device context");
+  const size_t o_lo_bits = align256(nn * 2), o_hi = o_lo_bits + align256(nn * 2);
+  const size_t img = static_cast<size_t>(npad) * npad * 2;
+  const size_t o_lo = o_hi + align256(img), o_h = o_lo + align256(img);
+  void* block = nullptr;
+  CK(pool_alloc(&block, o_h + align256(npad * sizeof(float)), p->device, ctx->upload),
+     "allocating fixed-point images");
+  char* d = static_cast<char*>(block);
+  CK(cudaMemcpyAsync(d, bits.data(), nn * 2, cudaMemcpyHostToDevice, ctx->upload), "upload Q(c J)");
+  CK(cudaMemcpyAsync(d + o_lo_bits, bits.data() + nn, nn * 2, cudaMemcpyHostToDevice, ctx->upload),
+     "upload Q(c J)");
+  CK(cudaMemcpyAsync(d + o_h, hq.data(), npad * sizeof(float), cudaMemcpyHostToDevice, ctx->upload),
+     "upload Q(c h)");
+  CK(staging_after_upload(ctx, p->device), "staging order");
+  CK(launch_stage_bf16_image(reinterpret_cast<const uint16_t*>(d), n, npad,
+                             reinterpret_cast<uint8_t*>(d + o_hi), ctx->staging),
+     "stage high part");
+  CK(launch_stage_bf16_image(reinterpret_cast<const uint16_t*>(d + o_lo_bits), n, npad,
+                             reinterpret_cast<uint8_t*>(d + o_lo), ctx->staging),
+     "stage low part");
+  {
+    std::lock_guard<std::mutex> lk(ctx->stage_mu);
+    CK(cudaEventRecord(p->ready, ctx->staging), "cudaEventRecord");
+    p->ready_seq = ++ctx->stage_seq;
+  }
+  pool_free_after(p->d_fix, p->device, p->done ? p->done->ev : nullptr);
+  p->d_fix = d;
+  p->d_fix_hi = reinterpret_cast<uint8_t*>(d + o_hi);
+  p->d_fix_lo = reinterpret_cast<uint8_t*>(d + o_lo);
+  p->d_fix_h = reinterpret_cast<float*>(d + o_h);
+  p->fix_w = W;
+  p->fix_i = I;
+  return PIM_OK;
+}
+
+// Schedule of the fixed-point datapath for real couplings: fl32(beta_t) per step and the
+// integer tables of the decision (fixed_real_tables), uploaded once.
+int build_fixed_real_schedule(std::shared_ptr<Schedule>& out, int steps, const float* beta,
+                              const float* eta, float xi, int noise, int act, int lut, int W,
+                              int I, int device) {
+  auto s = std::make_shared<Schedule>();
+  s->steps = steps;
+  s->device = device;
+  s->xi = xi;
+  s->act = act;
+  s->lut = lut;
+  s->fix_w = W;
+  s->fix_i = I;
+  std::vector<float> z(kNoiseLevels);
+  noise_levels(noise == PIM_NOISE_GAUSS ? 0 : 1, z.data());
+  std::vector<int32_t> tau(static_cast<size_t>(1) << W), qz(kNoiseLevels), qeta(steps);
+  fixed_real_tables(W, I, act, lut, xi, z.data(), tau.data(), qz.data(), &s->fix_xi);
+  for (int t = 0; t < steps; ++t) qeta[t] = fixed_units(static_cast<double>(eta[t]), W, I);
+  CK(cudaMalloc(&s->d_bt, steps * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_eta, steps * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_z, kNoiseLevels * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_fix_tau, tau.size() * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_fix_eta, steps * 4), "cudaMalloc schedule");
+  CK(cudaMalloc(&s->d_fix_z, kNoiseLevels * 4), "cudaMalloc schedule");
+  CK(cudaMemcpy(s->d_bt, beta, steps * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_eta, eta, steps * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_z, z.data(), kNoiseLevels * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_fix_tau, tau.data(), tau.size() * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_fix_eta, qeta.data(), steps * 4, cudaMemcpyHostToDevice), "upload schedule");
+  CK(cudaMemcpy(s->d_fix_z, qz.data(), kNoiseLevels * 4, cudaMemcpyHostToDevice), "upload schedule");
+  out = s;
+  return PIM_OK;
+}
+
 }  // namespace
 
 PIM_API int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* beta,
                                    const float* eta, float xi, int noise_kind, int act_kind,
                                    int lut_levels, int total_bits, int int_bits) {
   if (!inst) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: instance is NULL");
-  if (inst->real)
-    return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: integer couplings only");
   if (total_bits < 2 || total_bits > 32 || int_bits < 1 || int_bits > total_bits)
     return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: need 2 <= W <= 32, 1 <= I <= W");
+  if (inst->real && inst->n > kMaxNFixedReal)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: real couplings need n <= %d",
+                kMaxNFixedReal);
+  if (inst->real && total_bits > 16)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_set_schedule_fixed: real couplings need W <= 16");
   if (steps < 1 || !beta || !eta) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: bad steps/arrays");
   if (!std::isfinite(xi) || xi < 0.0f) return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: xi must be finite, >= 0");
   if (noise_kind != PIM_NOISE_GAUSS && noise_kind != PIM_NOISE_UNIFORM)
@@ -1053,10 +1197,14 @@ PIM_API int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* b
   for (int t = 0; t < steps; ++t)
     if (!std::isfinite(beta[t]) || beta[t] < 0.0f || !std::isfinite(eta[t]) || eta[t] < 0.0f)
       return fail(PIM_ERR_INVALID, "pim_set_schedule_fixed: beta/eta[%d] must be finite and >= 0", t);
-  const int imax = table_imax(inst);
+  if (inst->real) {
+    const int rc = build_fixed_images(inst, total_bits, int_bits);
+    if (rc != PIM_OK) return rc;
+  }
+  const int imax = inst->real ? -1 : table_imax(inst);
   std::string key = schedule_key(steps, beta, eta, xi, noise_kind, act_kind, lut_levels, inst->c,
                                  imax, inst->device);
-  key += "fixed";
+  key += inst->real ? "fixedreal" : "fixed";
   key.append(reinterpret_cast<const char*>(&total_bits), sizeof total_bits);
   key.append(reinterpret_cast<const char*>(&int_bits), sizeof int_bits);
   std::shared_ptr<Schedule> s;
@@ -1066,8 +1214,12 @@ PIM_API int pim_set_schedule_fixed(pim_instance* inst, int steps, const float* b
     if (it != g_sched_cache.end()) s = it->second.lock();
   }
   if (!s) {
-    const int rc = build_fixed_schedule(s, steps, beta, eta, xi, noise_kind, act_kind, lut_levels,
-                                        inst->c, imax, total_bits, int_bits, inst->device);
+    const int rc = inst->real
+                       ? build_fixed_real_schedule(s, steps, beta, eta, xi, noise_kind, act_kind,
+                                                   lut_levels, total_bits, int_bits, inst->device)
+                       : build_fixed_schedule(s, steps, beta, eta, xi, noise_kind, act_kind,
+                                              lut_levels, inst->c, imax, total_bits, int_bits,
+                                              inst->device);
     if (rc != PIM_OK) return rc;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     g_sched_cache[key] = s;
@@ -1341,6 +1493,17 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
     P.xi = p->sched->xi;
     P.act = p->sched->act;
     P.lut_levels = p->sched->lut;
+    if (p->real && p->sched->fix_w > 0) {
+      P.jimg = p->d_fix_hi;
+      P.jimg_lo = p->d_fix_lo;
+      P.hf = p->d_fix_h;
+      P.fix_w = p->sched->fix_w;
+      P.fix_f = p->sched->fix_w - p->sched->fix_i;
+      P.fix_tau = p->sched->d_fix_tau;
+      P.fix_eta = p->sched->d_fix_eta;
+      P.fix_z = p->sched->d_fix_z;
+      P.fix_xi = p->sched->fix_xi;
+    }
     const double tg = targets ? targets[k] : NAN;
     P.has_target = std::isnan(tg) ? 0 : 1;
     P.target = std::isnan(tg) ? 0 : static_cast<long long>(std::floor(tg));
@@ -1624,7 +1787,7 @@ int gather_results(pim_instance* const* insts, int count, cudaStream_t st, bool*
 
 int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int t_begin,
                 int sweeps, uint64_t seed, const uint32_t* ids, const double* targets,
-                const int8_t* init_spins, int flags, cudaStream_t st) {
+                const int8_t* init_spins, int flags, cudaStream_t st, float* d_fields = nullptr) {
   int rc = check_batch(insts, count, replicas, t_begin, sweeps, targets, flags, true);
   if (rc != PIM_OK) return rc;
   if (init_spins && count != 1) return fail(PIM_ERR_INVALID, "anneal: init spins need one instance");
@@ -1638,6 +1801,7 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
   BatchPlan B;
   const size_t init_bytes = init_spins ? static_cast<size_t>(replicas[0]) * insts[0]->n : 0;
   if ((rc = build_plan(insts, count, replicas, ids, targets, flags, init_bytes, B)) != PIM_OK) return rc;
+  if (d_fields) B.probs[0].fields_out = d_fields;
   char* d_buf = nullptr;
   CK(run_alloc(reinterpret_cast<void**>(&d_buf), B.total, st), "cudaMallocAsync launch buffer");
   std::vector<char> h_buf;
@@ -1672,6 +1836,35 @@ PIM_API int pim_anneal(pim_instance* inst, int replicas, int t_begin, int sweeps
   return anneal_impl(&inst, 1, &replicas, t_begin, sweeps, seed, &instance_id, &target_energy,
                      (flags & PIM_CONTINUE) ? nullptr : init_spins, flags,
                      static_cast<cudaStream_t>(cuda_stream));
+}
+
+PIM_API int pim_fields(pim_instance* inst, int replicas, const int8_t* spins, float* fields,
+                       int flags, void* cuda_stream) {
+  if (!inst || !spins || !fields) return fail(PIM_ERR_INVALID, "pim_fields: NULL argument");
+  if (!inst->real)
+    return fail(PIM_ERR_UNSUPPORTED, "pim_fields: integer couplings give exact integer fields; "
+                                     "the diagnostic serves real couplings");
+  if (replicas < 1) return fail(PIM_ERR_INVALID, "pim_fields: replicas = %d < 1", replicas);
+  if (flags & ~PIM_PATH_BIG) return fail(PIM_ERR_INVALID, "pim_fields: flags may only hold PIM_PATH_BIG");
+  const size_t tot = static_cast<size_t>(replicas) * inst->n;
+  for (size_t k = 0; k < tot; ++k)
+    if (spins[k] != 1 && spins[k] != -1)
+      return fail(PIM_ERR_INVALID, "pim_fields: spins must hold -1/+1");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  float* d_fields = nullptr;
+  CK(run_alloc(reinterpret_cast<void**>(&d_fields), tot * sizeof(float), st), "cudaMallocAsync fields");
+  const uint32_t id = 0;
+  const double no_target = NAN;
+  int rc = anneal_impl(&inst, 1, &replicas, 0, 1, 0, &id, &no_target, spins, flags, st, d_fields);
+  if (rc == PIM_OK) {
+    const cudaError_t e = cudaMemcpyAsync(fields, d_fields, tot * sizeof(float),
+                                          cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "fields to host");
+  }
+  cudaFreeAsync(d_fields, st);
+  if (rc != PIM_OK) return rc;
+  CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  return sync_instance(inst);
 }
 
 PIM_API int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
@@ -2084,6 +2277,7 @@ PIM_API void pim_destroy(pim_instance* inst) {
   cudaEvent_t after = inst->done ? inst->done->ev : inst->ready;
   pool_free_after(inst->d_slab, inst->device, after);
   pool_free_after(inst->d_jf, inst->device, after);
+  pool_free_after(inst->d_fix, inst->device, after);
   inst->done.reset();
   give_event(inst->device, inst->ready);
   inst->sched.reset();

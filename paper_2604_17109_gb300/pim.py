@@ -54,6 +54,7 @@ SIGNATURES = {
     "pim_results_dev": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "pim_state_words": (C.c_int, [C.c_void_p]),
+    "pim_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                         C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -451,3 +452,13 @@ def pim_anneal_noalloc(J: np.ndarray, scale_c: float, beta, eta, xi: float, repl
                                     int(instance_id), tgt, o["best_E"], o["best_t"],
                                     o["first_hit"], o["final_E"], o["best_bits"],
                                     o["final_bits"], _stream(stream)), "pim_anneal_noalloc")
+
+
+def pim_fields(inst, spins: np.ndarray, flags: int = 0, stream=None) -> np.ndarray:
+    """FP32 fields I = J s + h of the states `spins` (R x n, +-1) as the sweep kernel forms
+    them (real couplings); returns float32 R x n."""
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    out = np.empty(s.shape, np.float32)
+    _check(lib().pim_fields(inst, s.shape[0], _ptr(s), _ptr(out), int(flags), _stream(stream)),
+           "pim_fields")
+    return out

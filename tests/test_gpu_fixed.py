@@ -65,3 +65,72 @@ def test_fixed_point_tables_exhaustive(fmt, act):
                                       inst.c, beta[t], 0.5, eta[t], np.broadcast_to(Q, (I.size, 4096)),
                                       fmt[0], fmt[1], act, 4)
             assert np.array_equal(dec > 0, m[None, :] >= M[:, None]), (t, s)
+
+
+# ------------------------------------------------ real couplings (the MIMO datapath)
+def _mimo16(seed):
+    from oracle import mimo as om
+    from workloads import mimo_problem, mimo_scale
+    mp = mimo_problem(16, 16, 16, 12.0, seed)
+    xm = om.mmse(mp.H, mp.y, 1.0 / mp.es_n0, 4)
+    J, h = om.di_mimo(mp.H, mp.y, xm, [1, 1])
+    return J, h, mimo_scale(16)
+
+
+REAL_CASES = [
+    # name, (W, I), act, lut levels, R, sweeps
+    ("mimo16x16", (16, 4), "tanh", 4, 64, 64),
+    ("mimo16x16", (10, 4), "lut", 8, 40, 50),
+    ("mimo16x16", (6, 3), "tanh", 4, 32, 40),
+    ("gauss100_bias", (12, 4), "tanh", 4, 130, 30),
+]
+
+
+@pytest.mark.parametrize("name,fmt,act,L,R,T", REAL_CASES)
+def test_fixed_point_real_couplings_match_oracle(name, fmt, act, L, R, T):
+    """Real couplings in ap_fixed<W, I> (J_q = Q(c J), h_q = Q(c h), every datapath value
+    quantized): the fields are exact, so states, steps and the (exact) energies of the
+    quantized problem equal the oracle's run of the same datapath bit for bit."""
+    from workloads import maxcut_gauss
+    P = pim()
+    if name.startswith("mimo"):
+        J, h, c = _mimo16(5)
+        xi = 1.0
+    else:
+        g = maxcut_gauss(100, 2)
+        J, c = g.J, g.c
+        h = 0.3 * np.random.default_rng(1).standard_normal(100)
+        xi = 0.7
+    beta = linear_beta(T)
+    eta = eta_power(beta)
+    Jq = pimi.quantize(c * J, *fmt)
+    hq = pimi.quantize(c * h, *fmt)
+    target = float(np.median(oracle.energy(Jq, hq, np.ones((1, J.shape[0]), np.int8))) - 1.0)
+    hd = P.pim_create(J, h, c)
+    try:
+        P.pim_set_schedule_fixed(hd, beta, eta, xi, fmt[0], fmt[1], act=act, lut_levels=L)
+        P.pim_anneal(hd, R, T, 9, instance_id=4, target=target)
+        e = P.pim_energies(hd)
+        got = dict(best_E=e["best_E"], best_t=e["best_t"].astype(np.int64),
+                   first_hit=e["first_hit"].astype(np.int64), final_E=e["final_E"],
+                   best_state=P.pim_best_state(hd, J.shape[0]),
+                   final_state=P.pim_final_state(hd, J.shape[0]))
+    finally:
+        P.pim_destroy(hd)
+    want = oracle.anneal(Jq, hq, 1.0, beta, eta, xi, replicas=R, seed=9, q=4, target=target,
+                         act=act, lut_levels=L, fixed=fmt)
+    assert_same(got, want, label=f"{name} fmt={fmt} {act}")
+
+
+def test_fixed_point_real_rejects_large_n():
+    from workloads import maxcut_gauss
+    P = pim()
+    g = maxcut_gauss(200, 0)
+    hd = P.pim_create(g.J, None, g.c)
+    try:
+        beta = linear_beta(4)
+        with pytest.raises(P.PimError) as e:
+            P.pim_set_schedule_fixed(hd, beta, eta_power(beta), 0.7, 16, 4)
+        assert e.value.code == P.PIM_ERR_UNSUPPORTED
+    finally:
+        P.pim_destroy(hd)
