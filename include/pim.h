@@ -229,6 +229,16 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
  * pim_batch_info: kernel launches per run and whether runs replay a graph (1) or not (0).
  * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (instance changed since creation, CONTINUE without
  *         a previous run), PIM_ERR_UNSUPPORTED, PIM_ERR_NOMEM, PIM_ERR_CUDA.
+ *
+ * Autotuning (pim_autotune mode 1, the default): pim_batch_create first times, on the
+ * batch's own staged instances and with result buffers of its own, every shape class it has
+ * not met before on this device -- the fused kernel per (npad, decision path) unit, the
+ * persistent mid-N kernel per unit, and the large-N kernel per (real, npad, replica tiles)
+ * instance sweep at both tile widths (64 and 128 spins) -- a few sweeps each, and keeps the
+ * times in a process-wide cache keyed by device name and class.  The router and the
+ * large-N tile plan of every later run (pim_anneal, pim_anneal_batch, batch plans) use the
+ * measured times where the cache has them and the analytic model elsewhere.  All candidate
+ * kernels give identical results, so tuning changes speed only.
  */
 typedef struct pim_batch pim_batch;
 int pim_batch_create(pim_batch** out, pim_instance* const* insts, int count, const int* replicas,
@@ -237,6 +247,24 @@ int pim_batch_run(pim_batch* batch, int t_begin, int sweeps, uint64_t seed, int 
                   void* cuda_stream);
 int pim_batch_info(const pim_batch* batch, int* kernel_launches, int* uses_graph);
 void pim_batch_destroy(pim_batch* batch);
+
+/*
+ * pim_autotune -- how kernels and large-N tile widths are chosen (process-wide; the paper's
+ * counterpart is the host-side task scheduling it replaces).  mode 0: the analytic cost model
+ * only; mode 1 (default): pim_batch_create measures new shape classes first (see above).
+ * When the environment variable PIM_TUNE_CACHE names a file, measured times are appended
+ * to it and read back by later processes.
+ * Errors: PIM_ERR_INVALID (mode not 0 or 1).
+ *
+ * pim_tune_report -- the measured times, one line per shape class:
+ * "<device>|<kernel>|<a>|<b>|<c>|<d> <microseconds>" with kernel fused (a = npad,
+ * b = 1 diagonal-encoded; us per unit sweep, two CTAs per SM), mid (a = npad, b = decision
+ * path; us per unit sweep, one CTA per SM) or big (a = 1 real, b = npad, c = replica tiles,
+ * d = tile width; us per instance sweep).  Writes at most cap bytes (NUL-terminated) to
+ * out (may be NULL) and the size needed to *needed (may be NULL).
+ */
+int pim_autotune(int mode);
+int pim_tune_report(char* out, size_t cap, size_t* needed);
 
 /*
  * pim_anneal_sequential -- conventional PIM with sequential updates (Eq. 3; Box 1, orange
@@ -291,7 +319,17 @@ int pim_mimo_reconstruct(int nt, int qam, const double* x_mmse, const int8_t* sp
  * so requests that arrive while others run are admitted as slots and memory free up and
  * their work overlaps on the device.  A completion thread selects each request's replica
  * of lowest reported best energy (ties: lowest index), evaluates that state's FP64 energy,
- * reconstructs x_hat and records the latency (submit -> result available).  Every request uses the server's schedule (beta, eta, xi,
+ * reconstructs x_hat and records the latency (submit -> result available).
+ * Device-side request queue (device_queue = 1; n <= 256 spins, replicas <= 128): instead of
+ * batched launches, one persistent kernel (min(SMs, max_batch x max_inflight) CTAs) takes
+ * the requests from a queue in mapped pinned host memory.  The dispatcher formulates a
+ * request, writes its BF16 coupling image, bias and descriptor into the next free slot
+ * (2 x CTAs slots) and publishes it with a release store of the queue's tail; a CTA claims
+ * it from a device counter, runs the whole anneal (all replicas in one CTA) and writes the
+ * results into the slot before a done flag, which the completion thread polls.  The
+ * kernel's wait for requests is bounded: after idle_s without one it ends (no GPU time
+ * spent idling), and the server launches it again for the next request.
+ * Every request uses the server's schedule (beta, eta, xi,
  * scale_c, Gaussian noise, tanh), `replicas`, `sweeps`, `seed`, and its request_id as the
  * instance counter word, so its result does not depend on what it was batched with.
  */
@@ -306,6 +344,9 @@ typedef struct pim_mimo_server_config {
   int max_batch;          /* requests per launch, >= 1 */
   int max_inflight;       /* launches in flight (streams), >= 1 */
   size_t mem_budget;      /* device bytes admitted requests may hold (raised to one request) */
+  int device_queue;       /* 0: host batching as above; 1: device-side request queue (below) */
+  double idle_s;          /* device queue: the serving kernel ends after this long without a
+                             request (> 0; it is relaunched when requests come again) */
 } pim_mimo_server_config;
 typedef struct pim_mimo_server pim_mimo_server;
 int pim_mimo_server_create(pim_mimo_server** out, const pim_mimo_server_config* cfg);
@@ -329,6 +370,11 @@ int pim_mimo_server_replay(pim_mimo_server* server, int count, const double* H_a
                            const double* y_all, const double* reg_all,
                            const double* arrival_us, double* x_hat_all,
                            double* best_energy_all, double* latency_us_all);
+/* Device queue only: waits up to timeout_s for the serving kernel to end with no request
+   left in flight.  PIM_ERR_TIMEOUT: it ended because its bounded wait for requests ran out
+   (idle_s); PIM_OK: it ended on a stop; PIM_PENDING: still running at timeout;
+   PIM_ERR_UNSUPPORTED: the server batches on the host (device_queue = 0). */
+int pim_mimo_server_idle_wait(pim_mimo_server* server, double timeout_s);
 /* Stops admitting, finishes the batches in flight, drops requests still queued and frees
    the server; no other call on the server may run concurrently with it. */
 void pim_mimo_server_destroy(pim_mimo_server* server);

@@ -5,6 +5,8 @@
 
 #include "pim_device.cuh"
 
+struct pim_instance;
+
 namespace pim {
 
 // Byte offset of element (row, k) inside a K-major, 128-byte-swizzled operand image with
@@ -56,6 +58,10 @@ cudaError_t launch_sweep_float(const Launch& L, int npad, int blocks, cudaStream
 int sweep_float_smem_bytes(int npad);
 cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
                                     cudaStream_t st);
+// Persistent serving variant of the real-valued kernel: `blocks` CTAs take requests from Q
+// until it stays empty for Q.idle_ns or Q.stop is set (L: sweeps, round keys, waits).
+cudaError_t launch_serve_float(const Launch& L, const ServeQueue& Q, int npad, int blocks,
+                               cudaStream_t st);
 
 // Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs, each
 // computing nt (64 or 128) output spins; real = BF16 operands and the FP32 decision.
@@ -81,5 +87,11 @@ cudaError_t launch_ref_anneal(const Problem* h_probs, const Problem* d_probs, in
 
 // Sets the thread-local message returned by pim_last_error.
 void set_last_error(const char* msg);
+
+// Device arrays of a real-coupling instance's schedule (b_t = fl32(beta_t c), eta_t, the
+// 4096 noise levels) with its xi and activation, for the serving kernel; PIM_ERR_STATE
+// without a real-valued schedule.
+int schedule_device_arrays(const pim_instance* inst, const float** b_t, const float** eta,
+                           const float** zlev, float* xi, int* act, int* lut_levels);
 
 }  // namespace pim

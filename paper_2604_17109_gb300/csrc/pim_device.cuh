@@ -111,6 +111,27 @@ struct Launch {
   unsigned int* ready;
 };
 
+// Device-side request queue of the persistent serving kernel (real couplings, n <= 256,
+// R <= 128 replicas per request).  The host writes request k into slot k % nslots (its
+// descriptor, with the couplings as a BF16 operand image and the bias, and room for the
+// results, all in mapped pinned host memory) and then publishes it with a release store of
+// tail = k + 1.  Persistent CTAs claim requests in order from the device counter head,
+// run them and release-store done[slot] = k + 1 after the results.  A CTA that finds no
+// request for idle_ns (a bounded wait), or finds stop set, ends; exit_status records why.
+struct ServeQueue {
+  const unsigned int* tail;  // mapped host memory: requests published
+  const unsigned int* stop;  // mapped host memory: non-zero = end when no request is waiting
+  unsigned int* done;        // mapped host memory: [nslots]
+  const char* slots;         // mapped host memory: [nslots] slots of slot_bytes, each
+                             // beginning with its request's Problem descriptor
+  unsigned int* head;        // device memory: requests claimed
+  int* exit_status;          // device memory: 0 running, 1 idle limit reached, 2 stopped
+  const float* zlev;         // device memory: the 4096 noise levels of every request
+  int nslots;
+  unsigned long long slot_bytes;
+  uint64_t idle_ns;
+};
+
 // Launch of the large-N kernel: one instance, all sweeps, cooperative grid of
 // (replica tiles) x (nt-spin column blocks).
 struct BigLaunch {

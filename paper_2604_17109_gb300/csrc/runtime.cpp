@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -556,6 +557,19 @@ int table_imax(const pim_instance* p) {
 
 namespace pim {
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+int schedule_device_arrays(const pim_instance* inst, const float** b_t, const float** eta,
+                           const float** zlev, float* xi, int* act, int* lut_levels) {
+  if (!inst || !inst->real || !inst->sched || !inst->sched->d_bt || inst->sched->fix_w > 0)
+    return PIM_ERR_STATE;
+  *b_t = inst->sched->d_bt;
+  *eta = inst->sched->d_eta;
+  *zlev = inst->sched->d_z;
+  *xi = inst->sched->xi;
+  *act = inst->sched->act;
+  *lut_levels = inst->sched->lut;
+  return PIM_OK;
+}
 }  // namespace pim
 
 // ----------------------------------------------------------------------------------------
@@ -1245,6 +1259,87 @@ struct BigPlan {
 // measured for this kernel on GB300) and its MMA time at the per-SM tensor rate (1889 TFLOP/s
 // BF16, twice that for FP8, over 152 SMs); replica tiles that do not fit the co-resident grid
 // run as further launches, each with its own ~3 us grid barrier per sweep.
+// ---- Autotuning: measured kernel times per shape class -----------------------------------
+// pim_batch_create (mode 1) times, on the batch's own instances, every shape class it has
+// not seen on this device before: the persistent mid-N kernel per (npad, decision path)
+// unit, the fused kernel per unit, and the large-N kernel per (real, npad, replica tiles,
+// NT) instance sweep.  The router and the large-N tile plan use a measured time wherever
+// the cache has one and the analytic model otherwise.  Entries are kept per process and,
+// when PIM_TUNE_CACHE names a file, appended to it and read back by later processes.
+std::mutex g_tune_mu;
+std::map<std::string, double> g_tune;  // key -> microseconds
+bool g_tune_loaded = false;
+std::atomic<int> g_tune_mode{1};
+thread_local int t_force_nt = 0;            // measurement of one large-N tile width
+thread_local bool t_model_routes = false;   // measurement runs: no measured overrides
+
+std::string device_name(int dev) {
+  static std::mutex mu;
+  static std::map<int, std::string> names;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(dev);
+  if (it != names.end()) return it->second;
+  cudaDeviceProp prop{};
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+  for (char& ch : name)
+    if (ch == ' ' || ch == '|') ch = '_';
+  names[dev] = name;
+  return name;
+}
+
+std::string tune_key(const char* what, int a, int b, int c = 0, int d = 0) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "%s|%s|%d|%d|%d|%d", device_name(dev).c_str(), what, a, b, c, d);
+  return buf;
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("PIM_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    char key[200];
+    double us = 0.0;
+    if (std::sscanf(line, "%199s %lf", key, &us) == 2 && us > 0.0) g_tune[key] = us;
+  }
+  std::fclose(f);
+}
+
+bool tune_lookup(const std::string& key, double* us) {
+  if (t_model_routes || g_tune_mode.load() == 0) return false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *us = it->second;
+  return true;
+}
+
+bool tune_known(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  return g_tune.count(key) != 0;
+}
+
+void tune_store(const std::string& key, double us) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  g_tune[key] = us;
+  const char* path = std::getenv("PIM_TUNE_CACHE");
+  if (path && *path) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %.6g\n", key.c_str(), us);
+      std::fclose(f);
+    }
+  }
+}
+
 constexpr double kIngestBytesPerUs = 64e3;
 constexpr double kBf16FlopsPerUs = 1889e6 / 152;
 
@@ -1254,7 +1349,7 @@ int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
   const int tiles_total = (R + 127) / 128;
   BigPlan best;
   for (int nt : {64, 128}) {
-    if (npad % nt) continue;
+    if (npad % nt || (t_force_nt && nt != t_force_nt)) continue;
     const int ncb = npad / nt;
     const int cap = sweep_big_max_blocks(nt, real);
     if (cap < ncb) continue;
@@ -1262,6 +1357,12 @@ int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
     p.nt = nt;
     p.tiles_per_launch = std::min(tiles_total, cap / ncb);
     p.launches = (tiles_total + p.tiles_per_launch - 1) / p.tiles_per_launch;
+    double measured = 0.0;
+    if (tune_lookup(tune_key("big", real ? 1 : 0, npad, tiles_total, nt), &measured)) {
+      p.us_per_sweep = measured;
+      if (best.nt == 0 || p.us_per_sweep < best.us_per_sweep) best = p;
+      continue;
+    }
     const double bytes = 128.0 * 128 + nt * 128.0;
     const double flops = 2.0 * 128 * nt * (128 / eb);
     const double per_kb = std::max(bytes / kIngestBytesPerUs, flops / (kBf16FlopsPerUs * (real ? 1 : 2)));
@@ -1338,6 +1439,22 @@ double mid_unit_us(int npad) {
   return (chunks + 1) * std::max(kEpiUsPerChunk, ingest);
 }
 
+// Decision path a mid-N unit of instance p takes (0 general table, else the diagonal K).
+int mid_path(const pim_instance* p) {
+  if (p->diag && p->sched && p->sched->d_thr_diag) return 256;
+  if (p->d_img5 && p->sched &&
+      (p->dk5 == 256 ? p->sched->d_thr_diag != nullptr : p->sched->dk == p->dk5))
+    return p->dk5;
+  return 0;
+}
+
+// Mid-N unit time of instance p: measured when the cache has it, else the model.
+double mid_unit_us(const pim_instance* p) {
+  double us = 0.0;
+  if (tune_lookup(tune_key("mid", p->npad, mid_path(p)), &us)) return us;
+  return mid_unit_us(p->npad);
+}
+
 int route_batch(pim_instance* const* insts, const int* replicas, int count, int flags,
                 std::vector<int>& route) {
   route.assign(count, kFused);
@@ -1352,6 +1469,14 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
       route[k] = p->n <= kMaxNTensor ? kFused : kBig;
     } else if (p->n <= kMaxNTensor) {
       route[k] = (flags & PIM_PATH_MID) ? kMid : kFused;
+      // measured: a fused unit runs two CTAs per SM, a mid-N unit one, so the per-SM
+      // throughputs compare fused_us / 2 with mid_us
+      double fused_us = 0.0, mid_us = 0.0;
+      if (route[k] == kFused && p->npad <= sweep_mid_max_npad() &&
+          p->sched->imax <= kMaxImaxTensor &&
+          tune_lookup(tune_key("fused", p->npad, p->diag ? 1 : 0), &fused_us) &&
+          tune_lookup(tune_key("mid", p->npad, mid_path(p)), &mid_us) && mid_us < 0.5 * fused_us)
+        route[k] = kMid;
     } else if (p->npad > sweep_mid_max_npad() || (flags & PIM_PATH_BIG)) {
       route[k] = kBig;
     } else {
@@ -1364,7 +1489,7 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
   double mid_total = 0.0, mid_max = 0.0;
   for (int k = 0; k < count; ++k)
     if (route[k] == kMid) {
-      const double u = mid_unit_us(insts[k]->npad);
+      const double u = mid_unit_us(insts[k]);
       mid_total += u * ((replicas[k] + 127) / 128);
       mid_max = std::max(mid_max, u);
     }
@@ -1377,14 +1502,14 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
     const int k = eligible[e];
     BigPlan plan;
     if (plan_big(insts[k]->n, insts[k]->npad, replicas[k], false, &plan) != PIM_OK) continue;
-    const double u = mid_unit_us(insts[k]->npad);
+    const double u = mid_unit_us(insts[k]);
     const double rest_total = mid_total - u * ((replicas[k] + 127) / 128);
     double rest_max = 0.0;
     for (size_t f2 = e + 1; f2 < eligible.size(); ++f2)
-      rest_max = std::max(rest_max, mid_unit_us(insts[eligible[f2]]->npad));
+      rest_max = std::max(rest_max, mid_unit_us(insts[eligible[f2]]));
     for (int j = 0; j < count; ++j)
       if (route[j] == kMid && insts[j]->n <= kMaxNTensor)
-        rest_max = std::max(rest_max, mid_unit_us(insts[j]->npad));
+        rest_max = std::max(rest_max, mid_unit_us(insts[j]));
     const double before = big_total + std::max(mid_max, mid_total / mid_blocks);
     const double after = big_total + plan.us_per_sweep + std::max(rest_max, rest_total / mid_blocks);
     if (after >= before) break;
@@ -1823,6 +1948,138 @@ int anneal_impl(pim_instance* const* insts, int count, const int* replicas, int 
 
 }  // namespace
 
+namespace {
+
+// Device time (ms) of the sweep kernels of `sweeps` sweeps of a clone of `rep` with R
+// replicas, routed by `flags` (the clone shares rep's staged couplings and schedule and has
+// result buffers of its own, so rep's records are untouched).
+int tune_time(pim_instance* rep, int R, int sweeps, int flags, int force_nt, cudaStream_t st,
+              double* ms) {
+  pim_instance tmp = *rep;
+  tmp.d_res = nullptr;
+  tmp.R = tmp.R_cap = 0;
+  tmp.has_results = false;
+  tmp.res_bytes = 0;
+  tmp.h_res = nullptr;
+  tmp.h_res_dev = nullptr;
+  tmp.h_res_cap = 0;
+  tmp.h_res_valid = false;
+  tmp.done.reset();
+  tmp.timer.reset();
+  tmp.ticket = 0;
+  pim_instance* pt = &tmp;
+  t_force_nt = force_nt;
+  t_model_routes = true;
+  int rc = anneal_impl(&pt, 1, &R, 0, sweeps, 0, nullptr, nullptr, nullptr, flags, st);
+  t_force_nt = 0;
+  t_model_routes = false;
+  if (rc == PIM_OK) rc = sync_instance(pt);
+  if (rc == PIM_OK) {
+    float k = 0.0f;
+    const cudaError_t e = cudaEventElapsedTime(&k, tmp.timer->start, tmp.timer->stop);
+    if (e != cudaSuccess) rc = cuda_fail(e, "tuning timer");
+    *ms = k;
+  }
+  free_results(pt);
+  return rc;
+}
+
+// A candidate's time per sweep is the slope between a short and a longer run (each the
+// faster of two, so first-launch costs such as loading the kernel's code drop out), which
+// also removes the per-launch prologue and epilogue from the comparison.
+constexpr int kTuneShort = 8, kTuneLong = 40;
+
+int tune_slope(pim_instance* rep, int R, int flags, int force_nt, cudaStream_t st, double* us) {
+  const int steps = rep->sched->steps;
+  const int s_long = std::min(kTuneLong, steps), s_short = std::min(kTuneShort, s_long / 2);
+  double best[2] = {1e30, 1e30};
+  const int sweeps[2] = {s_short, s_long};
+  for (int pass = 0; pass < 2; ++pass)
+    for (int v = 0; v < 2; ++v) {
+      if (v == 0 && s_short < 1) continue;
+      double ms = 0.0;
+      const int rc = tune_time(rep, R, sweeps[v], flags, force_nt, st, &ms);
+      if (rc != PIM_OK) return rc;
+      best[v] = std::min(best[v], ms);
+    }
+  *us = s_short >= 1 && s_long > s_short ? 1000.0 * (best[1] - best[0]) / (s_long - s_short)
+                                         : 1000.0 * best[1] / s_long;
+  if (!(*us > 0.0)) *us = 1000.0 * best[1] / s_long;
+  return PIM_OK;
+}
+
+// Measures every shape class of the batch that the cache does not hold yet (see the tuning
+// cache above): fused and mid-N unit times for integer n <= 256, mid-N unit and large-N
+// instance sweeps (both tile widths) for integer n <= 1024, large-N sweeps above.
+int tune_batch(pim_instance* const* insts, int count, const int* replicas, cudaStream_t st) {
+  const int sms = device_sms();
+  for (int k = 0; k < count; ++k) {
+    pim_instance* p = insts[k];
+    if (p->sched->steps < 2) continue;
+    double us = 0.0;
+    int rc = PIM_OK;
+    const bool mid_ok = !p->real && p->npad <= sweep_mid_max_npad();
+    if (!p->real && p->n <= kMaxNTensor && p->sched->imax <= kMaxImaxTensor) {
+      const std::string key = tune_key("fused", p->npad, p->diag ? 1 : 0);
+      if (!tune_known(key)) {  // one full wave: two CTAs per SM, one unit each
+        if ((rc = tune_slope(p, 2 * sms * 128, 0, 0, st, &us)) != PIM_OK) return rc;
+        tune_store(key, us);
+      }
+    }
+    if (mid_ok) {
+      const std::string key = tune_key("mid", p->npad, mid_path(p));
+      if (!tune_known(key)) {  // one unit per SM
+        if ((rc = tune_slope(p, sms * 128, PIM_PATH_MID, 0, st, &us)) != PIM_OK) return rc;
+        tune_store(key, us);
+      }
+    }
+    if (p->n > kMaxNTensor) {
+      const int tiles = (replicas[k] + 127) / 128;
+      for (int nt : {64, 128}) {
+        if (p->npad % nt) continue;
+        const std::string key = tune_key("big", p->real ? 1 : 0, p->npad, tiles, nt);
+        if (tune_known(key)) continue;
+        BigPlan plan;
+        t_force_nt = nt;
+        const int prc = plan_big(p->n, p->npad, replicas[k], p->real, &plan);
+        t_force_nt = 0;
+        if (prc != PIM_OK) continue;  // this width cannot be co-resident
+        if ((rc = tune_slope(p, replicas[k], PIM_PATH_BIG, nt, st, &us)) != PIM_OK) return rc;
+        tune_store(key, us);
+      }
+    }
+  }
+  return PIM_OK;
+}
+
+}  // namespace
+
+PIM_API int pim_autotune(int mode) {
+  if (mode != 0 && mode != 1) return fail(PIM_ERR_INVALID, "pim_autotune: mode must be 0 or 1");
+  g_tune_mode = mode;
+  return PIM_OK;
+}
+
+PIM_API int pim_tune_report(char* out, size_t cap, size_t* needed) {
+  std::string text;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    for (const auto& kv : g_tune) {
+      char line[256];
+      std::snprintf(line, sizeof line, "%s %.4g\n", kv.first.c_str(), kv.second);
+      text += line;
+    }
+  }
+  if (needed) *needed = text.size() + 1;
+  if (out && cap > 0) {
+    const size_t n = std::min(cap - 1, text.size());
+    std::memcpy(out, text.data(), n);
+    out[n] = '\0';
+  }
+  return PIM_OK;
+}
+
 PIM_API int pim_anneal(pim_instance* inst, int replicas, int t_begin, int sweeps, uint64_t seed,
                        uint32_t instance_id, const int8_t* init_spins, double target_energy,
                        int flags, void* cuda_stream) {
@@ -1947,6 +2204,9 @@ PIM_API int pim_batch_create(pim_batch** out, pim_instance* const* insts, int co
   if ((e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
     return bail_cuda(e, "cudaStreamCreate");
   if ((rc = prepare_instances(b->insts.data(), count, b->replicas.data(), false, b->cap)) != PIM_OK)
+    return bail(rc);
+  if (g_tune_mode.load() == 1 && !(flags & (PIM_PATH_MID | PIM_PATH_BIG)) &&
+      (rc = tune_batch(b->insts.data(), count, b->replicas.data(), b->cap)) != PIM_OK)
     return bail(rc);
   if ((rc = build_plan(b->insts.data(), count, b->replicas.data(), b->ids.data(), b->targets.data(),
                        flags, 0, b->plan)) != PIM_OK)

@@ -7,9 +7,16 @@
 // thread waits for each batch, selects every request's minimum-energy replica by its FP64
 // energy, reconstructs the symbols and records the request's latency (submit -> result).
 // The Ising solving runs in the library's sweep kernels through the public entry points.
+//
+// Device-queue mode (cfg.device_queue): the dispatcher writes each formulated request into a
+// slot of a queue in mapped pinned host memory and publishes it; a persistent serving kernel
+// (launch_serve_float) claims requests from a device counter and flags each slot done; the
+// completion thread polls the flags.  The kernel ends after idle_s without requests and is
+// launched again by whichever thread next finds requests in flight and the kernel ended.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -43,6 +50,7 @@ struct Request {
   std::vector<double> x_hat;
   double best_E = NAN;
   int status = PIM_PENDING;
+  uint64_t seq = 0;  // device queue: position in the queue (slot seq % nslots)
 };
 
 struct Batch {
@@ -56,6 +64,49 @@ int fail_msg(int code, const char* msg) {
   pim::set_last_error(msg);
   return code;
 }
+
+// BF16 bits of v rounded to nearest (ties to even) from float64 directly: the float64
+// significand is rounded to 8 bits, after which the conversion to float32 is exact.
+uint16_t bf16_rne(double v) {
+  uint64_t d;
+  std::memcpy(&d, &v, sizeof d);
+  d += ((1ull << 44) - 1) + ((d >> 45) & 1);
+  d &= ~((1ull << 45) - 1);
+  double r;
+  std::memcpy(&r, &d, sizeof r);
+  const float f = static_cast<float>(r);
+  uint32_t b;
+  std::memcpy(&b, &f, sizeof b);
+  return static_cast<uint16_t>(b >> 16);
+}
+
+// Layout of one queue slot in the mapped block: descriptor, BF16 coupling image, bias,
+// results (best / final energies, best step, first hit, best and final spin bits).
+struct SlotLayout {
+  size_t desc = 0, img = 0, bias = 0, bestE = 0, finalE = 0, bestT = 0, first = 0, best_bits = 0,
+         cur_bits = 0, bytes = 0;
+  SlotLayout(int npad, int R, int words) {
+    auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+    size_t o = up(sizeof(pim::Problem));
+    img = o;
+    o = up(o + static_cast<size_t>(npad) * npad * 2);
+    bias = o;
+    o = up(o + static_cast<size_t>(npad) * 4);
+    bestE = o;
+    o = up(o + static_cast<size_t>(R) * 8);
+    finalE = o;
+    o = up(o + static_cast<size_t>(R) * 8);
+    bestT = o;
+    o = up(o + static_cast<size_t>(R) * 4);
+    first = o;
+    o = up(o + static_cast<size_t>(R) * 4);
+    best_bits = o;
+    o = up(o + static_cast<size_t>(R) * words * 4);
+    cur_bits = o;
+    o = up(o + static_cast<size_t>(R) * words * 4);
+    bytes = o;
+  }
+};
 
 }  // namespace
 
@@ -77,6 +128,38 @@ struct pim_mimo_server {
   int error = PIM_OK;
   pim_instance* keeper = nullptr;  // holds the schedule so the library keeps it cached
   std::thread dispatcher, completer;
+
+  // ---- device-queue mode ----------------------------------------------------------------
+  bool dq = false;
+  int npad = 0, words = 0, nslots = 0, ctas = 0;
+  SlotLayout lay{128, 1, 2};
+  char* h_block = nullptr;       // mapped pinned: control words | slots
+  char* d_block = nullptr;       // its device address
+  unsigned int* h_tail = nullptr;
+  unsigned int* h_stop = nullptr;
+  unsigned int* h_done = nullptr;
+  size_t slots_off = 0;
+  unsigned int* d_head = nullptr;  // device memory: claimed requests
+  int* d_exit = nullptr;           // device memory: why the kernel ended
+  pim::ServeQueue Q{};
+  pim::Launch L{};
+  pim::Problem proto{};            // descriptor fields shared by every request
+  cudaStream_t kstream = nullptr;
+  cudaEvent_t kdone = nullptr;
+  std::mutex kmu;                  // kernel launches
+  bool kernel_launched = false;
+  int last_exit = 0;               // 1 idle limit, 2 stopped
+  uint64_t published = 0;          // requests written to the queue
+  std::vector<std::shared_ptr<Request>> slot_req;  // in-flight request of each slot
+  std::atomic<uint64_t> in_flight{0};
+
+  char* slot_host(int k) { return h_block + slots_off + static_cast<size_t>(k) * lay.bytes; }
+  char* slot_dev(int k) { return d_block + slots_off + static_cast<size_t>(k) * lay.bytes; }
+  int ensure_kernel();  // launches the serving kernel unless it is running
+  int setup_device_queue();
+  void free_device_queue();
+  void run_dq_dispatcher();
+  void run_dq_completer();
 
   // device bytes one request holds while admitted: BF16 J and image, bias, results
   size_t request_bytes() const {
@@ -220,6 +303,251 @@ void pim_mimo_server::run_completer() {
   }
 }
 
+int pim_mimo_server::setup_device_queue() {
+  if (n > 256 || cfg.replicas > 128)
+    return fail_msg(PIM_ERR_UNSUPPORTED, "pim_mimo_server_create: the device queue serves n <= 256 "
+                                         "spins and at most 128 replicas");
+  if (!(cfg.idle_s > 0.0) || !std::isfinite(cfg.idle_s))
+    return fail_msg(PIM_ERR_INVALID, "pim_mimo_server_create: idle_s must be > 0");
+  dq = true;
+  npad = n <= 128 ? 128 : 256;
+  words = ((n + 63) / 64) * 2;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  ctas = std::max(1, std::min(sms, cfg.max_batch * cfg.max_inflight));
+  nslots = 2 * ctas;
+  lay = SlotLayout(npad, cfg.replicas, words);
+  slots_off = 256 + ((static_cast<size_t>(nslots) * 4 + 255) & ~static_cast<size_t>(255));
+  const size_t bytes = slots_off + static_cast<size_t>(nslots) * lay.bytes;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h_block), bytes, cudaHostAllocMapped) != cudaSuccess)
+    return fail_msg(PIM_ERR_NOMEM, "pim_mimo_server_create: mapped queue allocation failed");
+  std::memset(h_block, 0, bytes);
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&d_block), h_block, 0) != cudaSuccess)
+    return fail_msg(PIM_ERR_UNSUPPORTED, "pim_mimo_server_create: mapped memory has no device address");
+  h_tail = reinterpret_cast<unsigned int*>(h_block);
+  h_stop = h_tail + 1;
+  h_done = reinterpret_cast<unsigned int*>(h_block + 256);
+  if (cudaMalloc(reinterpret_cast<void**>(&d_head), 256) != cudaSuccess ||
+      cudaMemset(d_head, 0, 256) != cudaSuccess)
+    return fail_msg(PIM_ERR_NOMEM, "pim_mimo_server_create: device queue counters");
+  d_exit = reinterpret_cast<int*>(d_head + 1);
+  if (cudaStreamCreateWithFlags(&kstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&kdone, cudaEventDisableTiming) != cudaSuccess)
+    return fail_msg(PIM_ERR_CUDA, "pim_mimo_server_create: serving stream");
+  const float *bt = nullptr, *eta_d = nullptr, *z = nullptr;
+  float xi = 0.0f;
+  int act = 0, lut = 0;
+  if (pim::schedule_device_arrays(keeper, &bt, &eta_d, &z, &xi, &act, &lut) != PIM_OK)
+    return fail_msg(PIM_ERR_STATE, "pim_mimo_server_create: no real-valued schedule");
+  proto = pim::Problem{};
+  proto.n = n;
+  proto.npad = npad;
+  proto.words = words;
+  proto.R = cfg.replicas;
+  proto.sched_b = bt;
+  proto.sched_eta = eta_d;
+  proto.zlev = z;
+  proto.xi = xi;
+  proto.act = act;
+  proto.lut_levels = lut;
+  Q.tail = reinterpret_cast<const unsigned int*>(d_block);
+  Q.stop = reinterpret_cast<const unsigned int*>(d_block) + 1;
+  Q.done = reinterpret_cast<unsigned int*>(d_block + 256);
+  Q.slots = d_block + slots_off;
+  Q.slot_bytes = lay.bytes;
+  Q.head = d_head;
+  Q.exit_status = d_exit;
+  Q.zlev = z;
+  Q.nslots = nslots;
+  Q.idle_ns = static_cast<uint64_t>(cfg.idle_s * 1e9);
+  L = pim::Launch{};
+  L.t_begin = 0;
+  L.sweeps = cfg.sweeps;
+  L.key_lo = static_cast<uint32_t>(cfg.seed);
+  L.key_hi = static_cast<uint32_t>(cfg.seed >> 32);
+  pim::philox_round_keys(cfg.seed, L.round_keys);
+  L.err = d_exit + 1;
+  slot_req.assign(nslots, nullptr);
+  return PIM_OK;
+}
+
+void pim_mimo_server::free_device_queue() {
+  if (kstream) cudaStreamSynchronize(kstream);
+  if (kdone) cudaEventDestroy(kdone);
+  if (kstream) cudaStreamDestroy(kstream);
+  if (d_head) cudaFree(d_head);
+  if (h_block) cudaFreeHost(h_block);
+  kdone = nullptr;
+  kstream = nullptr;
+  d_head = nullptr;
+  h_block = nullptr;
+}
+
+int pim_mimo_server::ensure_kernel() {
+  std::lock_guard<std::mutex> lk(kmu);
+  if (kernel_launched) {
+    const cudaError_t q = cudaEventQuery(kdone);
+    if (q == cudaErrorNotReady) return PIM_OK;  // still serving
+    if (q != cudaSuccess) return PIM_ERR_CUDA;
+    int why[2] = {0, 0};  // exit reason, device error bits
+    if (cudaMemcpy(why, d_exit, sizeof why, cudaMemcpyDeviceToHost) != cudaSuccess) return PIM_ERR_CUDA;
+    last_exit = why[0];
+    kernel_launched = false;
+    if (why[1] & pim::kDevErrTimeout) {
+      pim::set_last_error("serving kernel: a device-side bounded wait gave up");
+      return PIM_ERR_TIMEOUT;
+    }
+  }
+  if (cudaMemsetAsync(d_exit, 0, 2 * sizeof(int), kstream) != cudaSuccess) return PIM_ERR_CUDA;
+  if (pim::launch_serve_float(L, Q, npad, ctas, kstream) != cudaSuccess) return PIM_ERR_CUDA;
+  if (cudaEventRecord(kdone, kstream) != cudaSuccess) return PIM_ERR_CUDA;
+  kernel_launched = true;
+  return PIM_OK;
+}
+
+void pim_mimo_server::run_dq_dispatcher() {
+  cudaSetDevice(device);
+  const size_t nn = static_cast<size_t>(n) * n;
+  for (;;) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&]() { return stop || !queue.empty(); });
+      if (stop) break;
+      r = queue.front();
+      queue.pop_front();
+    }
+    r->J.assign(nn, 0.0);
+    r->h.assign(n, 0.0);
+    r->xm.assign(2 * cfg.nt, 0.0);
+    int rc = pim::mimo_formulate(cfg.nt, cfg.nr, cfg.qam, r->H.data(), r->y.data(), r->reg,
+                                 r->J.data(), r->h.data(), r->xm.data());
+    std::unique_lock<std::mutex> lk(mu);
+    if (rc != PIM_OK) {
+      r->status = rc;
+      r->t_done = Clock::now();
+      latencies_us.push_back(std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count());
+      ++completed;
+      cv_done.notify_all();
+      continue;
+    }
+    const int slot = static_cast<int>(published % nslots);
+    cv_work.wait(lk, [&]() { return stop || !slot_req[slot]; });  // the slot's last request is read
+    if (stop) break;
+    // the position first: the completion thread matches the slot's done flag against it as
+    // soon as the request is in the slot table (the flag still holds the slot's previous
+    // request's position + 1 until this one is done)
+    r->seq = published;
+    slot_req[slot] = r;
+    lk.unlock();
+    // the request into its slot: BF16 coupling image (K-major, 128-byte swizzle), bias and
+    // descriptor, then the release store that publishes it
+    char* base = slot_host(slot);
+    uint16_t* img = reinterpret_cast<uint16_t*>(base + lay.img);
+    std::memset(img, 0, static_cast<size_t>(npad) * npad * 2);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        img[pim::sw128_offset(i, 2 * j, npad) / 2] = bf16_rne(r->J[static_cast<size_t>(i) * n + j]);
+    float* bias = reinterpret_cast<float*>(base + lay.bias);
+    for (int i = 0; i < npad; ++i) bias[i] = i < n ? static_cast<float>(r->h[i]) : 0.0f;
+    pim::Problem P = proto;
+    char* dev = slot_dev(slot);
+    P.jimg = reinterpret_cast<const uint8_t*>(dev + lay.img);
+    P.hf = reinterpret_cast<const float*>(dev + lay.bias);
+    P.best_E = reinterpret_cast<double*>(dev + lay.bestE);
+    P.final_E = reinterpret_cast<double*>(dev + lay.finalE);
+    P.best_t = reinterpret_cast<int32_t*>(dev + lay.bestT);
+    P.first_hit = reinterpret_cast<int32_t*>(dev + lay.first);
+    P.best_bits = reinterpret_cast<uint32_t*>(dev + lay.best_bits);
+    P.cur_bits = reinterpret_cast<uint32_t*>(dev + lay.cur_bits);
+    P.q = r->id;
+    std::memcpy(base + lay.desc, &P, sizeof P);
+    std::atomic_thread_fence(std::memory_order_release);
+    lk.lock();
+    ++published;
+    __atomic_store_n(h_tail, static_cast<unsigned int>(published), __ATOMIC_RELEASE);
+    ++in_flight;
+    peak_bytes = std::max(peak_bytes, static_cast<size_t>(in_flight.load()) * lay.bytes);
+    ++batches;
+    lk.unlock();
+    rc = ensure_kernel();
+    if (rc != PIM_OK) {
+      std::lock_guard<std::mutex> g(mu);
+      error = rc;
+    }
+    cv_done.notify_all();
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  dispatcher_done = true;
+  cv_done.notify_all();
+}
+
+void pim_mimo_server::run_dq_completer() {
+  cudaSetDevice(device);
+  const int R = cfg.replicas;
+  std::vector<int8_t> s(n);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_done.wait(lk, [&]() { return in_flight.load() > 0 || dispatcher_done; });
+      if (in_flight.load() == 0 && dispatcher_done) break;
+    }
+    bool progress = false;
+    for (int slot = 0; slot < nslots; ++slot) {
+      std::shared_ptr<Request> r;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r = slot_req[slot];
+      }
+      if (!r || __atomic_load_n(h_done + slot, __ATOMIC_ACQUIRE) != static_cast<unsigned int>(r->seq + 1))
+        continue;
+      const char* base = slot_host(slot);
+      const double* bestE = reinterpret_cast<const double*>(base + lay.bestE);
+      const uint32_t* bits = reinterpret_cast<const uint32_t*>(base + lay.best_bits);
+      // the replica of lowest reported energy (ties -> lowest index), then its FP64 energy
+      int best = 0;
+      for (int q = 1; q < R; ++q)
+        if (bestE[q] < bestE[best]) best = q;
+      for (int i = 0; i < n; ++i)
+        s[i] = ((bits[static_cast<size_t>(best) * words + (i >> 5)] >> (i & 31)) & 1u) ? 1 : -1;
+      double e = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double f = 0.0;
+        const double* Ji = r->J.data() + static_cast<size_t>(i) * n;
+        for (int j = 0; j < n; ++j) f += Ji[j] * s[j];
+        e -= s[i] * (0.5 * f + r->h[i]);
+      }
+      r->best_E = e;
+      r->x_hat.assign(2 * cfg.nt, 0.0);
+      pim::mimo_reconstruct(cfg.nt, cfg.qam, r->xm.data(), s.data(), r->x_hat.data());
+      const auto now = Clock::now();
+      std::lock_guard<std::mutex> lk(mu);
+      r->status = PIM_OK;
+      r->t_done = now;
+      latencies_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+      ++completed;
+      ++batched;
+      slot_req[slot].reset();
+      --in_flight;
+      progress = true;
+      cv_work.notify_all();
+      cv_done.notify_all();
+    }
+    if (!progress) {
+      // requests in flight but the kernel ended (its wait for requests ran out just before
+      // they were published): launch it again
+      if (in_flight.load() > 0) {
+        const int rc = ensure_kernel();
+        if (rc != PIM_OK) {
+          std::lock_guard<std::mutex> lk(mu);
+          error = rc;
+        }
+      }
+      std::this_thread::yield();
+    }
+  }
+}
+
 PIM_API int pim_mimo_server_create(pim_mimo_server** out, const pim_mimo_server_config* cfg) {
   if (!out || !cfg) return fail_msg(PIM_ERR_INVALID, "pim_mimo_server_create: NULL argument");
   *out = nullptr;
@@ -254,15 +582,22 @@ PIM_API int pim_mimo_server_create(pim_mimo_server** out, const pim_mimo_server_
     if (rc == PIM_OK)
       rc = pim_set_schedule(s->keeper, cfg->sweeps, cfg->beta, cfg->eta, cfg->xi, PIM_NOISE_GAUSS,
                             PIM_ACT_TANH, 0);
+    if (rc == PIM_OK && cfg->device_queue) rc = s->setup_device_queue();
     if (rc != PIM_OK) {
+      s->free_device_queue();
       if (s->keeper) pim_destroy(s->keeper);
       for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
       delete s;
       return rc;
     }
   }
-  s->dispatcher = std::thread([s]() { s->run_dispatcher(); });
-  s->completer = std::thread([s]() { s->run_completer(); });
+  if (s->dq) {
+    s->dispatcher = std::thread([s]() { s->run_dq_dispatcher(); });
+    s->completer = std::thread([s]() { s->run_dq_completer(); });
+  } else {
+    s->dispatcher = std::thread([s]() { s->run_dispatcher(); });
+    s->completer = std::thread([s]() { s->run_completer(); });
+  }
   *out = s;
   return PIM_OK;
 }
@@ -362,6 +697,34 @@ PIM_API int pim_mimo_server_replay(pim_mimo_server* s, int count, const double* 
   return status;
 }
 
+PIM_API int pim_mimo_server_idle_wait(pim_mimo_server* s, double timeout_s) {
+  if (!s) return fail_msg(PIM_ERR_INVALID, "pim_mimo_server_idle_wait: server is NULL");
+  if (!s->dq) return fail_msg(PIM_ERR_UNSUPPORTED, "pim_mimo_server_idle_wait: no device queue");
+  const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+  for (;;) {
+    if (s->in_flight.load() == 0) {
+      std::lock_guard<std::mutex> lk(s->kmu);
+      if (!s->kernel_launched) break;
+      const cudaError_t q = cudaEventQuery(s->kdone);
+      if (q == cudaSuccess) {
+        int why = 0;
+        if (cudaMemcpy(&why, s->d_exit, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return fail_msg(PIM_ERR_CUDA, "pim_mimo_server_idle_wait: reading the exit status");
+        s->last_exit = why;
+        s->kernel_launched = false;
+        break;
+      }
+      if (q != cudaErrorNotReady) return fail_msg(PIM_ERR_CUDA, "pim_mimo_server_idle_wait: cudaEventQuery");
+    }
+    if (Clock::now() > deadline) return PIM_PENDING;
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  if (s->last_exit == 1)
+    return fail_msg(PIM_ERR_TIMEOUT, "pim_mimo_server_idle_wait: the serving kernel's wait for "
+                                     "requests ran out (idle limit)");
+  return PIM_OK;
+}
+
 PIM_API void pim_mimo_server_destroy(pim_mimo_server* s) {
   if (!s) return;
   {
@@ -370,7 +733,12 @@ PIM_API void pim_mimo_server_destroy(pim_mimo_server* s) {
     s->cv_work.notify_all();
   }
   if (s->dispatcher.joinable()) s->dispatcher.join();
+  if (s->dq) {
+    // no new requests: the kernel finishes what it claimed and ends once the queue is empty
+    __atomic_store_n(s->h_stop, 1u, __ATOMIC_RELEASE);
+  }
   if (s->completer.joinable()) s->completer.join();
+  s->free_device_queue();
   for (auto& q : s->queue)
     if (q->inst) pim_destroy(q->inst);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);

@@ -55,6 +55,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "pim_state_words": (C.c_int, [C.c_void_p]),
     "pim_fields": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "pim_autotune": (C.c_int, [C.c_int]),
+    "pim_tune_report": (C.c_int, [C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     "pim_anneal_sequential": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                         C.c_uint32, C.c_void_p, C.c_double, C.c_int, C.c_void_p]),
     "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
@@ -72,6 +74,7 @@ SIGNATURES = {
     "pim_mimo_server_replay": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pim_mimo_server_destroy": (None, [C.c_void_p]),
+    "pim_mimo_server_idle_wait": (C.c_int, [C.c_void_p, C.c_double]),
     "pim_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_int]),
     "pim_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
@@ -250,16 +253,19 @@ class MimoServerConfig(C.Structure):
     _fields_ = [("nt", C.c_int), ("nr", C.c_int), ("qam", C.c_int), ("replicas", C.c_int),
                 ("sweeps", C.c_int), ("beta", C.c_void_p), ("eta", C.c_void_p), ("xi", C.c_float),
                 ("scale_c", C.c_double), ("seed", C.c_uint64), ("max_batch", C.c_int),
-                ("max_inflight", C.c_int), ("mem_budget", C.c_size_t)]
+                ("max_inflight", C.c_int), ("mem_budget", C.c_size_t),
+                ("device_queue", C.c_int), ("idle_s", C.c_double)]
 
 
 def pim_mimo_server_create(nt, nr, qam, replicas, beta, eta, xi, scale_c, seed=0, max_batch=64,
-                           max_inflight=4, mem_budget=1 << 30) -> int:
+                           max_inflight=4, mem_budget=1 << 30, device_queue=False,
+                           idle_s=0.05) -> int:
     beta = np.ascontiguousarray(beta, dtype=np.float32)
     eta = np.ascontiguousarray(eta, dtype=np.float32)
     cfg = MimoServerConfig(int(nt), int(nr), int(qam), int(replicas), int(beta.size),
                            beta.ctypes.data, eta.ctypes.data, float(xi), float(scale_c), int(seed),
-                           int(max_batch), int(max_inflight), int(mem_budget))
+                           int(max_batch), int(max_inflight), int(mem_budget),
+                           1 if device_queue else 0, float(idle_s))
     out = C.c_void_p()
     _check(lib().pim_mimo_server_create(C.byref(out), C.byref(cfg)), "pim_mimo_server_create")
     return out.value
@@ -462,3 +468,26 @@ def pim_fields(inst, spins: np.ndarray, flags: int = 0, stream=None) -> np.ndarr
     _check(lib().pim_fields(inst, s.shape[0], _ptr(s), _ptr(out), int(flags), _stream(stream)),
            "pim_fields")
     return out
+
+
+def pim_autotune(mode: int) -> None:
+    """0: analytic cost model only; 1: batch plans measure new shape classes first."""
+    _check(lib().pim_autotune(int(mode)), "pim_autotune")
+
+
+def pim_tune_report() -> str:
+    """The measured kernel times, one line per shape class."""
+    need = C.c_size_t()
+    _check(lib().pim_tune_report(None, 0, C.byref(need)), "pim_tune_report")
+    buf = C.create_string_buffer(need.value)
+    _check(lib().pim_tune_report(buf, need.value, None), "pim_tune_report")
+    return buf.value.decode()
+
+
+def pim_mimo_server_idle_wait(server: int, timeout_s: float) -> int:
+    """Device queue: PIM_ERR_TIMEOUT when the serving kernel ended on its idle limit, PIM_OK
+    when it ended on a stop, PIM_PENDING while it runs (returned, not raised)."""
+    rc = lib().pim_mimo_server_idle_wait(server, float(timeout_s))
+    if rc in (PIM_OK, PIM_PENDING, PIM_ERR_TIMEOUT):
+        return rc
+    return _check(rc, "pim_mimo_server_idle_wait")

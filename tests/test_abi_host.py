@@ -108,3 +108,14 @@ def test_validation_finds_first_asymmetry_and_range_errors(pim, n):
             pim.pim_create(K)
         assert e.value.code == pim.PIM_ERR_INVALID
         assert re.search(rf"\|J\[{i}\]\[{j}\]\| = {17 if _ % 2 else 128} > 16", str(e.value)), str(e.value)
+
+
+def test_autotune_mode_and_report_on_the_host(pim):
+    """pim_autotune takes modes 0 and 1 only; the tuning report is text (empty when nothing
+    was measured and no cache file is named)."""
+    with pytest.raises(pim.PimError) as e:
+        pim.pim_autotune(2)
+    assert e.value.code == pim.PIM_ERR_INVALID
+    pim.pim_autotune(0)
+    pim.pim_autotune(1)
+    assert isinstance(pim.pim_tune_report(), str)

@@ -166,3 +166,81 @@ def test_memory_admission_bounds_admitted_bytes():
     assert one["completed"] == 0
     assert st["completed"] == 12 and st["mean_batch"] == 1.0
     assert st["p99_us"] >= st["p50_us"] > 0
+
+
+# ------------------------------------------------ device-side request queue
+def test_device_queue_equals_host_batching():
+    """The persistent serving kernel fed from the device queue gives every request the same
+    detected symbols and energy as host-side batched launches (same couplings, draws and
+    decisions), for requests arriving all at once and one by one."""
+    P = pim()
+    nt, T = 16, 64
+    probs = _problems(nt, 40, seed0=100)
+    H = np.stack([p.H for p in probs])
+    y = np.stack([p.y for p in probs])
+    regs = [_reg(p) for p in probs]
+    s1 = _server(P, nt, T, max_batch=8, max_inflight=3)
+    try:
+        x1, e1, _ = P.pim_mimo_server_replay(s1, H, y, regs, np.zeros(len(probs)), nt)
+    finally:
+        P.pim_mimo_server_destroy(s1)
+    # 16 serving CTAs and 32 slots; then one CTA and two slots, so every request reuses a slot
+    for batch, inflight in ((8, 2), (1, 1)):
+        s2 = _server(P, nt, T, max_batch=batch, max_inflight=inflight, device_queue=True, idle_s=0.5)
+        try:
+            x2, e2, lat = P.pim_mimo_server_replay(s2, H, y, regs, np.zeros(len(probs)), nt)
+            st = P.pim_mimo_server_stats(s2)
+            single = []
+            for k in (3, 17):
+                t = P.pim_mimo_server_submit(s2, probs[k].H, probs[k].y, regs[k], k)
+                single.append(P.pim_mimo_server_result(s2, t, nt))
+        finally:
+            P.pim_mimo_server_destroy(s2)
+        assert st["completed"] == len(probs)
+        bad = np.nonzero(np.any(x1 != x2, axis=1) | (e1 != e2))[0]
+        assert bad.size == 0, (batch, inflight, bad)
+        assert np.all(lat > 0)
+        for (xs, es, _), k in zip(single, (3, 17)):
+            assert np.array_equal(xs, x1[k]) and es == e1[k]
+
+
+def test_device_queue_idle_wait_runs_out_and_the_kernel_comes_back():
+    """With no request for idle_s the serving kernel's bounded wait runs out: it ends and the
+    host sees PIM_ERR_TIMEOUT; the next requests launch it again and are served."""
+    P = pim()
+    nt, T = 16, 64
+    probs = _problems(nt, 6, seed0=200)
+    ref = []
+    s1 = _server(P, nt, T, max_batch=4, max_inflight=1)
+    try:
+        for k, p in enumerate(probs):
+            ref.append(P.pim_mimo_server_result(s1, P.pim_mimo_server_submit(s1, p.H, p.y, _reg(p), k), nt))
+    finally:
+        P.pim_mimo_server_destroy(s1)
+    s2 = _server(P, nt, T, max_batch=4, max_inflight=1, device_queue=True, idle_s=0.05)
+    try:
+        got = []
+        for k, p in enumerate(probs[:3]):
+            got.append(P.pim_mimo_server_result(s2, P.pim_mimo_server_submit(s2, p.H, p.y, _reg(p), k), nt))
+        assert P.pim_mimo_server_idle_wait(s2, 5.0) == P.PIM_ERR_TIMEOUT
+        for k, p in enumerate(probs[3:], start=3):
+            got.append(P.pim_mimo_server_result(s2, P.pim_mimo_server_submit(s2, p.H, p.y, _reg(p), k), nt))
+        assert P.pim_mimo_server_idle_wait(s2, 5.0) == P.PIM_ERR_TIMEOUT
+    finally:
+        P.pim_mimo_server_destroy(s2)
+    for (x, e, _), (xr, er, _) in zip(got, ref):
+        assert np.array_equal(x, xr) and e == er
+
+
+def test_device_queue_limits():
+    P = pim()
+    with pytest.raises(P.PimError) as e:
+        _server(P, 65, 8, max_batch=1, max_inflight=1, device_queue=True)  # n = 260 spins
+    assert e.value.code == P.PIM_ERR_UNSUPPORTED
+    s = _server(P, 4, 8, max_batch=1, max_inflight=1)
+    try:
+        with pytest.raises(P.PimError) as e:
+            P.pim_mimo_server_idle_wait(s, 0.01)
+        assert e.value.code == P.PIM_ERR_UNSUPPORTED
+    finally:
+        P.pim_mimo_server_destroy(s)
