@@ -716,6 +716,79 @@ def _tts_study(pim, handles, reps, ids, xis, n_inst, stream, torch, np):
     }
 
 
+# Workloads measured beside the default one (device-resident batch-plan replays only, no
+# end-to-end or CPU legs, fewer sweeps where stated), so that one default run also records
+# the large-N, uneven-batch and serving kernels: name, workload key, sweeps.
+SECONDARY = (("sk4096_2000sweeps", "sk4096", 2000),
+             ("maxcut8192_bf16_1000sweeps", "maxcut8192", 1000),
+             ("uneven4096_200sweeps", "uneven4096", 200),
+             ("sk512_152inst_1000sweeps", "sk512", 1000))
+
+
+def _secondary(args, pim, torch, np, rank):
+    """Device-resident throughput of the SECONDARY workloads and device-queue serving."""
+    peaks, _ = _peaks()
+    stream = torch.cuda.Stream()
+    out = []
+    for name, key, sweeps in SECONDARY:
+        w = dataclasses.replace(WORKLOADS[key], sweeps=sweeps)
+        beta, eta = _schedule(sweeps)
+        insts, reps, ids, xis = _batch_inputs(w, rank)
+        real = w.kind == "maxcut_gauss"
+        handles = [pim.pim_create(i.J, None, i.c) for i in insts]
+        for hd, xi in zip(handles, xis):
+            pim.pim_set_schedule(hd, beta, eta, xi)
+        batch = pim.pim_batch_create(handles, reps, instance_ids=np.asarray(ids, dtype=np.uint32))
+        for _ in range(2):
+            pim.pim_batch_run(batch, sweeps, seed=0, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pim.pim_batch_run(batch, sweeps, seed=0, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        k_ms = pim.pim_kernel_ms(handles[0])
+        pim.pim_batch_destroy(batch)
+        for hd in handles:
+            pim.pim_destroy(hd)
+        step_ms = statistics.mean(ms)
+        updates = sum(i.n * r for i, r in zip(insts, reps)) * sweeps
+        flops = sum(2.0 * i.n * i.n * r for i, r in zip(insts, reps)) * sweeps
+        tensor_peak = float(peaks["bf16_tflops"]) * (1.0 if real else 2.0)
+        out.append({"workload": name, "value": updates / (step_ms * 1e-3), "unit": METRIC,
+                    "ms_per_step": step_ms, "us_per_sweep": step_ms * 1000.0 / sweeps,
+                    "tensor_frac": flops / (k_ms * 1e-3) / 1e12 / tensor_peak,
+                    "dtype": "bf16/f32" if real else "fp8e4m3/i32"})
+    # MIMO 16x16 16-QAM detection through the device-side request queue (Poisson arrivals)
+    from workloads import MIMO_XI, bits_from_symbols, mimo_problem, mimo_scale, mimo_schedule
+    nt, count, R, T, rate = 16, 2000, 32, 64, 4000.0
+    rng = np.random.default_rng(3000 + rank)
+    probs = [mimo_problem(nt, nt, 16, float(snr), rank * count + k)
+             for k, snr in enumerate(rng.uniform(10.0, 25.0, count))]
+    beta, eta = mimo_schedule(T)
+    srv = pim.pim_mimo_server_create(nt, nt, 16, R, beta, eta, MIMO_XI, mimo_scale(nt), seed=7,
+                                     max_batch=64, max_inflight=4, device_queue=True, idle_s=0.2)
+    try:
+        arrivals = np.cumsum(rng.exponential(1e6 / rate, count))
+        t0 = time.perf_counter()
+        xh, _, _ = pim.pim_mimo_server_replay(srv, np.stack([p.H for p in probs]),
+                                              np.stack([p.y for p in probs]),
+                                              [1.0 / p.es_n0 for p in probs], arrivals, nt)
+        wall = time.perf_counter() - t0
+        st = pim.pim_mimo_server_stats(srv)
+    finally:
+        pim.pim_mimo_server_destroy(srv)
+    bits = np.stack([p.bits for p in probs])
+    out.append({"workload": "mimo16x16_16qam_device_queue_4000req_per_s", "offered_per_s": rate,
+                "served_per_s": st["completed"] / wall, "latency_p50_us": st["p50_us"],
+                "latency_p99_us": st["p99_us"],
+                "ber": float(np.mean(bits != bits_from_symbols(xh, 16)))})
+    return out
+
+
 def run_ours(args, w: Workload):
     world, rank, local = _dist()
     import numpy as np
@@ -853,6 +926,10 @@ def run_ours(args, w: Workload):
     for hd in handles:
         pim.pim_destroy(hd)
 
+    secondary = None
+    if w.key == "sk200" and args.instances is None and args.sweeps is None and not args.no_secondary:
+        secondary = _secondary(args, pim, torch, np, rank)
+
     if rank != 0:
         return 0
     peaks, peak_kind = _peaks()
@@ -919,6 +996,7 @@ def run_ours(args, w: Workload):
         "tensor_pipe": tensor,
         "tts99": tts,
         "field_error": field_error,
+        "secondary_workloads": secondary,
         "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
@@ -943,6 +1021,8 @@ def main():
     ap.add_argument("--instances", type=int, default=None,
                     help="instances per GPU (smaller cases for profiling)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per anneal")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the secondary workloads of the default run")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="1: batch plans measure new shape classes first; 0: cost model only")
     args = ap.parse_args()
