@@ -8,8 +8,8 @@
 // Per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
 //   fields   D[r, i] = sum_j S[r, j] J[i, j] for the CTA's 128 replicas and NT spins: the
 //            K dimension (all N spins) streams through a shared-memory ring filled by
-//            cp.async.bulk (spins of the tile from the global spin image, rows of J from the
-//            coupling image), consumed by tcgen05.mma into TMEM.
+//            cp.async.bulk (spins of the tile from the global spin image, two K-blocks per
+//            copy, rows of J from the coupling image), consumed by tcgen05.mma into TMEM.
 //   decision 16 epilogue warps (4 TMEM lane quadrants x 4 column groups); each thread owns
 //            one replica and NT/4 spins for the whole anneal, keeps their old / new / best
 //            bits in registers, draws the Philox blocks and decides: integer couplings by
@@ -40,6 +40,11 @@ constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr int kSmemBudget = 227 * 1024;
 
 // Shared-memory plan of one kernel variant: NT output spins per CTA, FP8 or BF16 operands.
+// K-blocks per ring stage.  A bulk copy costs about 0.16 us of the producer's time whatever
+// its size (up to 16 KB measured), so a stage moves two K-blocks of the tile's spins in one
+// copy (the spin image is tile-major for that) instead of one copy per K-block.
+constexpr int KPS = 2;
+
 template <int NT, bool REAL>
 struct BigCfg {
   static constexpr int kEB = REAL ? 2 : 1;       // operand element bytes
@@ -47,12 +52,13 @@ struct BigCfg {
   static constexpr int kChunks = kSPT / 16;      // 16-spin chunks per thread
   static constexpr int kABytes = 128 * 128;      // one K-block of the spin tile (128 rows x 128 B)
   static constexpr int kBBytes = NT * 128;       // one K-block of the coupling rows
+  static constexpr int kKPS = KPS;               // K-blocks per ring stage
   static constexpr int kAux = REAL ? 4096 * 4 : kTabWords * 4;  // noise levels | step table
   static constexpr int kFixed = 1024 + kAux + 4 * 128 * 4 + NT * 4 + 256;
-  static constexpr int kFit = (kSmemBudget - kFixed) / (kABytes + kBBytes);
-  static constexpr int kStages = kFit < 8 ? kFit : 8;  // K-block ring depth
-  static constexpr int kSmem = kFixed + kStages * (kABytes + kBBytes);
-  static_assert(kStages >= 3, "ring too shallow");
+  static constexpr int kFit = (kSmemBudget - kFixed) / (kKPS * (kABytes + kBBytes));
+  static constexpr int kStages = kFit < 8 ? kFit : 8;  // ring depth
+  static constexpr int kSmem = kFixed + kStages * kKPS * (kABytes + kBBytes);
+  static_assert(kStages >= 2, "ring too shallow");
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
@@ -115,11 +121,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint8_t* sA = smem;                               // kStages x kABytes
-  uint8_t* sB = sA + kStages * kABytes;             // kStages x kBBytes
-  uint32_t* sTab = reinterpret_cast<uint32_t*>(sB + kStages * kBBytes);  // [kTabWords] (integer)
+  constexpr int kKPS = C::kKPS;
+  uint8_t* sA = smem;                               // kStages x kKPS x kABytes
+  uint8_t* sB = sA + kStages * kKPS * kABytes;      // kStages x kKPS x kBBytes
+  uint32_t* sTab = reinterpret_cast<uint32_t*>(sB + kStages * kKPS * kBBytes);  // [kTabWords]
   float* sZ = reinterpret_cast<float*>(sTab);       // [4096] noise levels (real)
-  EAcc* sRed = reinterpret_cast<EAcc*>(sB + kStages * kBBytes + C::kAux);  // [4 groups][128 rows]
+  EAcc* sRed = reinterpret_cast<EAcc*>(sB + kStages * kKPS * kBBytes + C::kAux);  // [4][128 rows]
   uint32_t* sH = reinterpret_cast<uint32_t*>(sRed + 4 * 128);  // [NT] bias: int32 or float bits
   uint64_t* bars = reinterpret_cast<uint64_t*>(sH + NT);       // full[S], empty[S], done
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
@@ -207,17 +214,21 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
   const bool has_target = P.has_target != 0;
 
   // Spin image s(t) for this CTA's block (rows of the tile, its NT spins): FP8 or BF16 +-1.
+  // The image is tile-major, [replica tile][K-block][128 rows x 128 B with the 128-byte
+  // swizzle], so consecutive K-blocks of one tile are contiguous (one copy per ring stage).
+  const size_t tile_bytes = static_cast<size_t>(kblocks) * kABytes;
   auto write_image = [&](uint8_t* img, uint32_t bits) {
     if (!epi || col0 >= npad) return;
+    uint8_t* base = img + static_cast<size_t>(rt) * tile_bytes;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
       const uint32_t b16 = (bits >> (16 * c)) & 0xFFFFu;
       const int k = col0 + 16 * c;
       if constexpr (REAL) {
-        *reinterpret_cast<uint4*>(img + sw128_offset(rl, 2 * k, rpad)) = bf16x8_from_bits(b16 & 0xFFu);
-        *reinterpret_cast<uint4*>(img + sw128_offset(rl, 2 * k + 16, rpad)) = bf16x8_from_bits(b16 >> 8);
+        *reinterpret_cast<uint4*>(base + sw128_offset(row, 2 * k, 128)) = bf16x8_from_bits(b16 & 0xFFu);
+        *reinterpret_cast<uint4*>(base + sw128_offset(row, 2 * k + 16, 128)) = bf16x8_from_bits(b16 >> 8);
       } else {
-        *reinterpret_cast<uint4*>(img + sw128_offset(rl, k, rpad)) = fp8x16_from_bits(b16);
+        *reinterpret_cast<uint4*>(base + sw128_offset(row, k, 128)) = fp8x16_from_bits(b16);
       }
     }
   };
@@ -231,17 +242,21 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     // Producer (thread 0): stream the K blocks of image `img` (spins of the tile) and of the
     // coupling rows of the column block into the ring.  A stage is refilled once the MMAs
     // that read it have completed (its empty barrier).
+    // A stage holds kKPS consecutive K-blocks: the tile's spins of all of them in one copy
+    // (the image is tile-major), the coupling rows in one copy per K-block.
     auto produce = [&](const uint8_t* img) -> bool {
-      const uint8_t* a_src = img + static_cast<size_t>(rt) * 128 * 128;
+      const uint8_t* a_src = img + static_cast<size_t>(rt) * tile_bytes;
       const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * NT * 128;
-      for (int kb = 0; kb < kblocks; ++kb) {
+      for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+        const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
         const uint32_t s = loads % kStages, use = loads / kStages;
         if (use > 0 && !mbar_wait_fast(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
-        mbar_expect_tx(bar_full0 + 8 * s, kABytes + kBBytes);
-        bulk_g2s(smem_u32(sA + s * kABytes), a_src + static_cast<size_t>(kb) * rpad * 128, kABytes,
-                 bar_full0 + 8 * s);
-        bulk_g2s(smem_u32(sB + s * kBBytes), b_src + static_cast<size_t>(kb) * npad * 128, kBBytes,
-                 bar_full0 + 8 * s);
+        mbar_expect_tx(bar_full0 + 8 * s, nk * (kABytes + kBBytes));
+        bulk_g2s(smem_u32(sA + s * kKPS * kABytes), a_src + static_cast<size_t>(kb0) * kABytes,
+                 nk * kABytes, bar_full0 + 8 * s);
+        for (int j = 0; j < nk; ++j)
+          bulk_g2s(smem_u32(sB + (s * kKPS + j) * kBBytes),
+                   b_src + static_cast<size_t>(kb0 + j) * npad * 128, kBBytes, bar_full0 + 8 * s);
         ++loads;
       }
       return true;
@@ -250,18 +265,22 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     // never waits for an MMA to finish, only for data.  Each MMA consumes 32 bytes of K
     // (32 FP8 or 16 BF16 values).
     auto multiply = [&]() -> bool {
-      for (int kb = 0; kb < kblocks; ++kb) {
+      for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+        const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
         const uint32_t s = mmas % kStages, use = mmas / kStages;
         if (!mbar_wait_fast(bar_full0 + 8 * s, use & 1, L.wait_ns)) return false;
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+        for (int j = 0; j < nk; ++j) {
+          const uint32_t a0 = smem_u32(sA + (s * kKPS + j) * kABytes);
+          const uint32_t b0 = smem_u32(sB + (s * kKPS + j) * kBBytes);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
-          if constexpr (REAL)
-            mma_bf16(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
-          else
-            mma_e4m3(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t acc = (kb0 + j > 0 || ks > 0) ? 1u : 0u;
+            if constexpr (REAL)
+              mma_bf16(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
+            else
+              mma_e4m3(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
+          }
         }
         mma_commit(bar_empty0 + 8 * s);
         ++mmas;

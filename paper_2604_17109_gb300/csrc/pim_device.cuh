@@ -136,7 +136,8 @@ struct ServeQueue {
 // (replica tiles) x (nt-spin column blocks).
 struct BigLaunch {
   Problem P;
-  uint8_t* s_img[2];       // FP8 spin images [npad/128][rpad][128 B] (A operand), ping-pong
+  uint8_t* s_img[2];       // spin images (A operand), ping-pong: tile-major,
+                           // [rpad/128][K-blocks][128 rows x 128 B, 128-byte swizzle]
   float* energy;           // [3][rpad] rotating per-replica energy accumulators (zeroed);
                            // int32 for integer couplings, float for real couplings
   int nt;                  // output spins per CTA (64 or 128)
