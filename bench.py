@@ -87,14 +87,14 @@ LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one instruction each per cyc
 # workload whose kernel changed after its capture has no entry here (traffic reported null):
 #   sk200       sweep_tc_kernel<256,0,queue>, full-size launch: 17.86 MB read + 0.03 MB
 #               written, nothing grows per pass
-#   sk4096      sweep_big_kernel<64,FP8>, 50-sweep capture 18.85 MB = 16.8 MB image (L2-resident
+#   sk4096      sweep_big_kernel<64,FP8>, 50-sweep capture 19.17 MB = 16.8 MB image (L2-resident
 #               afterwards) + misc, and one 32 KB threshold table per pass
-#   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.194 GB = the 134 MB image
+#   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.156 GB = the 134 MB image
 #               streamed from HBM every pass (it exceeds L2)
 DRAM_TRAFFIC = {
     "sk200": (17.862e6 + 0.027e6, 0.0),
-    "sk4096": (18.848e6 - 51 * 32768.0, 32768.0),
-    "maxcut8192": (0.0, 7.194e9 / 51),
+    "sk4096": (19.171e6 - 51 * 32768.0, 32768.0),
+    "maxcut8192": (0.0, 7.156e9 / 51),
 }
 
 

@@ -81,12 +81,17 @@ typedef enum pim_flags {
   PIM_PATH_BIG = 8,     /* put every instance with n > 256 on the large-N cooperative kernel
                            (same decisions; for tests and tuning).  Without either flag the
                            library picks the kernel of each instance from its cost model. */
-  PIM_RESULTS_TO_HOST = 16 /* after the run, copy every instance's results (all of what
+  PIM_RESULTS_TO_HOST = 16, /* after the run, copy every instance's results (all of what
                            pim_energies, pim_best_state and pim_final_state return) into
                            library-owned pinned host memory on the same stream, so those
                            getters wait for the run and read host memory instead of issuing
                            a synchronous copy each.  Costs R * (24 + 8 * words) bytes of
                            device-to-host traffic per instance and run. */
+  PIM_PATH_BIG_FP8 = 32 /* on the large-N kernel, stream FP8 E4M3 couplings every sweep even
+                           where the coupling-resident E2M1 variant applies (integer couplings
+                           in {0, +-1, +-2, +-3, +-4, +-6}, 256 < n <= 4096); same decisions,
+                           for tests and tuning.  Without it the library picks the variant
+                           from its cost model or measured times. */
 } pim_flags;
 
 typedef struct pim_instance pim_instance;
@@ -96,7 +101,10 @@ typedef struct pim_instance pim_instance;
  * Defines the problem of Eq. 1 / Eq. 2 (Ising Hamiltonian and local field).
  *   out      receives the new handle (set to NULL on failure).
  *   n        number of spins, 1 <= n <= 8192; the fused kernels serve n <= 256, the
- *            large-N kernel n > 256 (integer and real couplings alike).
+ *            large-N kernel n > 256 (integer and real couplings alike).  For integer J with
+ *            256 < n <= 4096 and every entry in {0, +-1, +-2, +-3, +-4, +-6} the instance
+ *            also keeps an E2M1 (FP4) copy of J, n_pad^2 / 2 bytes, for the large-N
+ *            kernel's coupling-resident variant (exact: those integers are E2M1 values).
  *   j_type   element type of J (pim_j_type).
  *   J        host, row-major n x n; must be symmetric with a zero diagonal.
  *   h        host bias, n entries: int32 when j_type == PIM_J_INT8, else the float type
@@ -218,7 +226,7 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
  *                 schedule and replica counts while it exists (pim_batch_run checks).
  *   replicas      count entries >= 1; instance_ids (NULL = 0..count-1) and targets (NULL
  *                 or NaN = none) as in pim_anneal_batch.
- *   flags         0, PIM_PATH_MID or PIM_PATH_BIG.
+ *   flags         0, PIM_PATH_MID or PIM_PATH_BIG, each optionally with PIM_PATH_BIG_FP8.
  * pim_batch_run runs sweeps t_begin .. t_begin+sweeps-1 of every instance, asynchronously on
  * `cuda_stream`: the first run with given (t_begin, sweeps, seed, run_flags) captures the
  * batch's launches into a CUDA graph (later changes update the instantiated graph in

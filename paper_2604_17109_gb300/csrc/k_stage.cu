@@ -39,6 +39,49 @@ cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag,
   return cudaGetLastError();
 }
 
+// E2M1 coupling image of the coupling-resident large-N variant (column block width 64):
+// [npad/64 column blocks][npad/256 K-blocks][64 rows x 128 B], each row holding 256 packed
+// E2M1 values (element j in nibble j % 2 of byte j / 2, low nibble first) with the 128-byte
+// swizzle, so one column block's couplings are contiguous.  Couplings are integers in
+// {0, +-1, +-2, +-3, +-4, +-6} (checked by the host), all exact in E2M1 (sign, 2-bit
+// exponent, 1-bit mantissa).  One thread per 16-byte chunk (32 couplings).
+__device__ __forceinline__ uint32_t e2m1_code(int v) {
+  const int a = v < 0 ? -v : v;
+  const uint32_t mag = a == 1 ? 2u : a == 2 ? 4u : a == 3 ? 5u : a == 4 ? 6u : a == 6 ? 7u : 0u;
+  return mag | (v < 0 && mag ? 8u : 0u);
+}
+
+__global__ void stage_fp4_image_kernel(const int8_t* __restrict__ J, int n, int npad,
+                                       uint8_t* __restrict__ img) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t chunks = static_cast<uint32_t>(npad) * npad / 32u;
+  if (q >= chunks) return;
+  const int kb4 = npad / 256;
+  const uint32_t block = q / 512u, within = q % 512u;
+  const int cb = block / kb4, kb = block % kb4;
+  const int r = within / 8, pc = within % 8;
+  const int i = cb * 64 + r;
+  const int j0 = kb * 256 + ((pc ^ (r & 7)) * 32);
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  if (i < n) {
+    const int8_t* row = J + static_cast<size_t>(i) * n;
+    for (int e = 0; e < 32; ++e) {
+      const int j = j0 + e;
+      const uint32_t code = j < n ? e2m1_code(row[j]) : 0u;
+      w[e >> 3] |= code << (4 * (e & 7));
+    }
+  }
+  reinterpret_cast<uint4*>(img)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+cudaError_t launch_stage_fp4_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+                                   cudaStream_t st) {
+  if (npad % 256) return cudaErrorInvalidValue;
+  const uint32_t chunks = static_cast<uint32_t>(npad) * npad / 32u;
+  stage_fp4_image_kernel<<<(chunks + 255) / 256, 256, 0, st>>>(d_J, n, npad, d_img);
+  return cudaGetLastError();
+}
+
 __global__ void stage_f32_kernel(const int8_t* __restrict__ J, int n, float* __restrict__ jf) {
   const size_t k = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k < static_cast<size_t>(n) * n) jf[k] = static_cast<float>(J[k]);

@@ -25,6 +25,10 @@ __host__ __device__ inline uint32_t sw128_offset(int row, int k, int rows) {
 cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
                                    cudaStream_t st, bool e5m2 = false);
 cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st);
+// E2M1 image of the coupling-resident large-N variant, npad x npad / 2 bytes (npad a
+// multiple of 256; couplings in {0, +-1, +-2, +-3, +-4, +-6}).
+cudaError_t launch_stage_fp4_image(const int8_t* d_J, int n, int npad, uint8_t* d_img,
+                                   cudaStream_t st);
 
 // Decision thresholds for all steps: tau [steps][2*imax+1], eta [steps], z [4096].
 cudaError_t launch_thresholds(const float* d_tau, const float* d_eta, const float* d_z,
@@ -64,10 +68,26 @@ cudaError_t launch_serve_float(const Launch& L, const ServeQueue& Q, int npad, i
                                cudaStream_t st);
 
 // Large-N kernel (n > 256): cooperative launch of `blocks` = (rpad/128) * ncb CTAs, each
-// computing nt (64 or 128) output spins; real = BF16 operands and the FP32 decision.
-cudaError_t launch_sweep_big(const BigLaunch& L, int nt, bool real, int blocks, cudaStream_t st);
-int sweep_big_max_blocks(int nt, bool real);  // co-resident CTAs on the current device (0 on error)
-int sweep_big_stages(int nt, bool real);      // depth of the K-block ring
+// computing nt (64 or 128) output spins.  Operand variants (op):
+//   kBigFp8   FP8 E4M3 spins and couplings, both streamed every sweep (integer couplings);
+//   kBigBf16  BF16 spins and couplings, FP32 decision (real couplings);
+//   kBigFp4   coupling-resident: the CTA's 64 coupling rows stay in shared memory as packed
+//             E2M1 for the whole launch and only E2M1 spins stream (integer couplings in
+//             {0, +-1, +-2, +-3, +-4, +-6}, npad <= 4096, nt = 64).
+enum BigOp : int { kBigFp8 = 0, kBigBf16 = 1, kBigFp4 = 2 };
+// Shared-memory plan of a variant: ring depth, whether the step's threshold table is staged
+// in shared memory, dynamic shared-memory bytes.  ok = false when the variant does not fit.
+struct BigSmem {
+  bool ok = false;
+  int stages = 0;
+  int tab_smem = 0;
+  int bytes = 0;
+};
+BigSmem sweep_big_smem(int nt, int op, int npad, int stride_words);
+// L.stages / L.tab_smem must hold sweep_big_smem's plan for (nt, op, P.npad, P.stride_words).
+cudaError_t launch_sweep_big(const BigLaunch& L, int nt, int op, int blocks, cudaStream_t st);
+// Co-resident CTAs on the current device for that plan (0 on error or when it does not fit).
+int sweep_big_max_blocks(int nt, int op, int npad, int stride_words);
 
 // Persistent mid-N kernel (integer couplings, npad <= 1024): `blocks` CTAs take the units
 // of L.work from the counter L.next (zeroed by the launch).

@@ -10,11 +10,14 @@ enum : int {
   kDevErrTimeout = 1,      // a bounded mbarrier wait gave up
   kDevErrFieldRange = 2,   // a field fell outside the threshold table (cannot happen for
                            // a valid instance; checked so a bad table never reads out of range)
+  kDevErrLayout = 4,       // dynamic shared memory not 1024-byte aligned where the kernel's
+                           // layout has no room for the alignment pad (the kernel did nothing)
 };
 
 // Per-instance parameters of one launch.  All pointers are device pointers.
 struct Problem {
   const uint8_t* jimg;     // FP8 E4M3 couplings, npad x npad, 128B-swizzled K-major image
+  const uint8_t* jimg4;    // E2M1 image of the coupling-resident large-N variant, or null
   const float* jf;         // float32 row-major n x n (plain path)
   const int8_t* j8;        // int8 row-major n x n (sequential path)
   const int32_t* h;        // int32 bias or nullptr
@@ -137,11 +140,16 @@ struct ServeQueue {
 struct BigLaunch {
   Problem P;
   uint8_t* s_img[2];       // spin images (A operand), ping-pong: tile-major,
-                           // [rpad/128][K-blocks][128 rows x 128 B, 128-byte swizzle]
+                           // [rpad/128][K-blocks][128 rows x 128 B, 128-byte swizzle];
+                           // a 128-byte row holds 128 FP8, 64 BF16 or 256 E2M1 spins
+  const uint8_t* j4;       // E2M1 coupling image of the coupling-resident variant (else null)
+  int stages;              // K-block ring depth and threshold-table placement of the
+  int tab_smem;            //   variant's shared-memory plan
   float* energy;           // [3][rpad] rotating per-replica energy accumulators (zeroed);
                            // int32 for integer couplings, float for real couplings
   int nt;                  // output spins per CTA (64 or 128)
-  unsigned int* bar;       // grid barrier {arrivals, generation, abort} (zeroed)
+  unsigned int* bar;       // grid barrier: 64-bit monotone arrival counter with an abort
+                           // bit (zeroed, 8-byte aligned)
   int rbase;               // first replica of this launch
   int rpad;                // replica rows of this launch (multiple of 128)
   int ncb;                 // column blocks = npad / nt

@@ -54,6 +54,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int kMaxN = 8192;        // plain path limit
 constexpr int kMaxNTensor = 256;   // fused kernel limit
+constexpr int kMaxNpadFp4 = 4096;  // coupling-resident large-N variant: 64 x npad / 2 bytes
+                                   // of E2M1 couplings per CTA fit in shared memory
 constexpr int kMaxNFixedReal = 128;  // fixed-point real couplings: two coupling images fit in
                                      // the fused real-valued kernel's shared memory
 constexpr int kMaxImaxTensor = 511;
@@ -366,6 +368,9 @@ struct pim_instance {
   // diagonal-encoded path.
   uint8_t* d_img5 = nullptr;
   int dk5 = 0;
+  // 256 < n, npad <= 4096, couplings in {0, +-1, +-2, +-3, +-4, +-6}: the E2M1 image of the
+  // coupling-resident large-N variant (column-block-major, npad x npad / 2 bytes).
+  uint8_t* d_img4 = nullptr;
   bool real = false;  // real-valued couplings: BF16 operand image, float bias
   float* d_hf = nullptr;
   // Fixed-point datapath of real couplings (n <= kMaxNFixedReal): the couplings and bias as
@@ -645,9 +650,9 @@ std::pair<int, int> first_asymmetry(const T* a, int n) {
 // when some |entry| in 9..16 is odd (9, 11, 13, 15 have no exact E5M2 encoding).  Byte
 // arithmetic with 16-bit partial sums (|v| <= 128, 256 of them fit) so that the loop
 // vectorises.
-bool abs_row_sum_i8(const int8_t* row, int n, int* sum, bool* not_e5m2) {
+bool abs_row_sum_i8(const int8_t* row, int n, int* sum, bool* not_e5m2, bool* not_e2m1) {
   int s = 0;
-  uint8_t out = 0, odd = 0;
+  uint8_t out = 0, odd = 0, nf4 = 0;
   for (int j0 = 0; j0 < n; j0 += 256) {
     const int j1 = std::min(n, j0 + 256);
     uint16_t part = 0;
@@ -658,11 +663,13 @@ bool abs_row_sum_i8(const int8_t* row, int n, int* sum, bool* not_e5m2) {
       part += a;
       out |= static_cast<uint8_t>(static_cast<uint8_t>(u + 16) > 32);
       odd |= static_cast<uint8_t>((a > 8) & a);
+      nf4 |= static_cast<uint8_t>((a > 6) | (a == 5));  // E2M1 integers: 0..4 and 6
     }
     s += part;
   }
   *sum = s;
   *not_e5m2 = (odd & 1) != 0;
+  *not_e2m1 = nf4 != 0;
   return out != 0;
 }
 
@@ -896,14 +903,14 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   // row sums of |J| + |h| (the field bound); then the symmetry check.
   std::vector<long long> rowsum(n, 0);
   std::vector<int> bad(n, -1);
-  std::vector<uint8_t> no_e5m2(n, 0);
+  std::vector<uint8_t> no_e5m2(n, 0), no_e2m1(n, 0);
   parallel_for(n, [&](int i0, int i1) {
     for (int i = i0; i < i1; ++i) {
       const int8_t* row = J8 + static_cast<size_t>(i) * n;
       long long s = h32 ? std::llabs(static_cast<long long>(h32[i])) : 0;
       int sum = 0;
-      bool ne = false;
-      if (abs_row_sum_i8(row, n, &sum, &ne) || row[i] != 0) {
+      bool ne = false, nf4 = false;
+      if (abs_row_sum_i8(row, n, &sum, &ne, &nf4) || row[i] != 0) {
         for (int j = 0; j < n; ++j) {  // locate the first offending entry of the row
           const int v = row[j];
           if ((i == j && v != 0) || v < -16 || v > 16) {
@@ -914,6 +921,7 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
       }
       rowsum[i] = s + sum;
       no_e5m2[i] = ne ? 1 : 0;
+      no_e2m1[i] = nf4 ? 1 : 0;
     }
   }, 64, static_cast<size_t>(n) * n);
   long long imax = 0;
@@ -956,14 +964,17 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   if (!ctx) return bail(cudaErrorMemoryAllocation, "device context");
   const size_t nn = static_cast<size_t>(n) * n;
   const size_t img = static_cast<size_t>(p->npad) * p->npad;
-  bool e5m2_exact = true;
+  bool e5m2_exact = true, e2m1_exact = true;
   for (int i = 0; i < n; ++i) e5m2_exact &= no_e5m2[i] == 0;
+  for (int i = 0; i < n; ++i) e2m1_exact &= no_e2m1[i] == 0;
   if (n > kMaxNTensor && p->npad <= sweep_mid_max_npad() && !p->has_h && e5m2_exact)
     p->dk5 = table_imax(p) <= kMaxImaxDiag ? 256 : wide_diag_k(table_imax(p));
+  const bool fp4 = n > kMaxNTensor && p->npad <= kMaxNpadFp4 && e2m1_exact;
   const size_t o_img = align256(nn), o_h = o_img + align256(img);
   const size_t o_img5 = o_h + align256(n * sizeof(int32_t));
+  const size_t o_img4 = o_img5 + (p->dk5 ? align256(img) : 0);
   void* slab = nullptr;
-  if ((e = pool_alloc(&slab, o_img5 + (p->dk5 ? align256(img) : 0), p->device, ctx->upload)) != cudaSuccess)
+  if ((e = pool_alloc(&slab, o_img4 + (fp4 ? align256(img / 2) : 0), p->device, ctx->upload)) != cudaSuccess)
     return bail(e, "allocating J");
   p->d_slab = static_cast<char*>(slab);
   p->d_J8 = reinterpret_cast<int8_t*>(p->d_slab);
@@ -986,6 +997,11 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->dk5, p->d_img5, ctx->staging, true)) !=
         cudaSuccess)
       return bail(e, "stage E5M2 J image");
+  }
+  if (fp4) {
+    p->d_img4 = reinterpret_cast<uint8_t*>(p->d_slab + o_img4);
+    if ((e = launch_stage_fp4_image(p->d_J8, n, p->npad, p->d_img4, ctx->staging)) != cudaSuccess)
+      return bail(e, "stage E2M1 J image");
   }
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
@@ -1248,17 +1264,19 @@ namespace {
 // Tile plan of the large-N kernel for one instance.
 struct BigPlan {
   int nt = 0;                // output spins per CTA (64 or 128)
+  int op = kBigFp8;          // operand variant (BigOp)
   int tiles_per_launch = 0;  // 128-replica tiles per cooperative launch
   int launches = 0;
   double us_per_sweep = 0.0;  // model estimate
 };
 
-// Per-sweep time model of the large-N kernel.  Every CTA streams npad * bytes / 128
-// K-blocks of (128 x 128 B spins + nt x 128 B couplings); a K-block costs the larger of its
-// ingest time at the per-SM bulk-copy rate (about 64 GB/s per SM when all SMs stream, as
-// measured for this kernel on GB300) and its MMA time at the per-SM tensor rate (1889 TFLOP/s
-// BF16, twice that for FP8, over 152 SMs); replica tiles that do not fit the co-resident grid
-// run as further launches, each with its own ~3 us grid barrier per sweep.
+// Per-sweep time model of the large-N kernel.  Every CTA streams K-blocks of 128 x 128 B
+// spins (128 FP8, 64 BF16 or 256 E2M1 spins per row) plus, unless they are resident, nt x
+// 128 B of couplings; a K-block costs the larger of its ingest time at the per-SM bulk-copy
+// rate (about 64 GB/s per SM when all SMs stream, as measured for this kernel on GB300) and
+// its MMA time at the per-SM tensor rate (1889 TFLOP/s BF16, twice that for FP8, four times
+// for FP4, over 152 SMs); replica tiles that do not fit the co-resident grid run as further
+// launches, each with its own ~3 us grid barrier per sweep.
 // ---- Autotuning: measured kernel times per shape class -----------------------------------
 // pim_batch_create (mode 1) times, on the batch's own instances, every shape class it has
 // not seen on this device before: the persistent mid-N kernel per (npad, decision path)
@@ -1271,6 +1289,7 @@ std::map<std::string, double> g_tune;  // key -> microseconds
 bool g_tune_loaded = false;
 std::atomic<int> g_tune_mode{1};
 thread_local int t_force_nt = 0;            // measurement of one large-N tile width
+thread_local int t_force_op = -1;           //   and operand variant
 thread_local bool t_model_routes = false;   // measurement runs: no measured overrides
 
 std::string device_name(int dev) {
@@ -1343,30 +1362,36 @@ void tune_store(const std::string& key, double us) {
 constexpr double kIngestBytesPerUs = 64e3;
 constexpr double kBf16FlopsPerUs = 1889e6 / 152;
 
-int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
-  const int eb = real ? 2 : 1;
-  const int kblocks = npad * eb / 128;
+int plan_big(int n, int npad, int R, bool real, bool fp4, int stride_words, BigPlan* out) {
   const int tiles_total = (R + 127) / 128;
+  const int base = real ? kBigBf16 : kBigFp8;
+  const std::pair<int, int> cands[3] = {{64, base}, {128, base}, {64, kBigFp4}};
   BigPlan best;
-  for (int nt : {64, 128}) {
-    if (npad % nt || (t_force_nt && nt != t_force_nt)) continue;
+  for (const auto& cand : cands) {
+    const int nt = cand.first, op = cand.second;
+    if (op == kBigFp4 && !fp4) continue;
+    if (npad % nt || (t_force_nt && nt != t_force_nt) || (t_force_op >= 0 && op != t_force_op))
+      continue;
     const int ncb = npad / nt;
-    const int cap = sweep_big_max_blocks(nt, real);
+    const int cap = sweep_big_max_blocks(nt, op, npad, stride_words);
     if (cap < ncb) continue;
     BigPlan p;
     p.nt = nt;
+    p.op = op;
     p.tiles_per_launch = std::min(tiles_total, cap / ncb);
     p.launches = (tiles_total + p.tiles_per_launch - 1) / p.tiles_per_launch;
     double measured = 0.0;
-    if (tune_lookup(tune_key("big", real ? 1 : 0, npad, tiles_total, nt), &measured)) {
+    if (tune_lookup(tune_key("big", op, npad, tiles_total, nt), &measured)) {
       p.us_per_sweep = measured;
       if (best.nt == 0 || p.us_per_sweep < best.us_per_sweep) best = p;
       continue;
     }
-    const double bytes = 128.0 * 128 + nt * 128.0;
-    const double flops = 2.0 * 128 * nt * (128 / eb);
-    const double per_kb = std::max(bytes / kIngestBytesPerUs, flops / (kBf16FlopsPerUs * (real ? 1 : 2)));
-    p.us_per_sweep = p.launches * (kblocks * per_kb + 3.0);
+    const int spins_per_kb = op == kBigFp4 ? 256 : (real ? 64 : 128);
+    const double rate = kBf16FlopsPerUs * (op == kBigFp4 ? 4 : (real ? 1 : 2));
+    const double bytes = 128.0 * 128 + (op == kBigFp4 ? 0.0 : nt * 128.0);
+    const double flops = 2.0 * 128 * nt * spins_per_kb;
+    const double per_kb = std::max(bytes / kIngestBytesPerUs, flops / rate);
+    p.us_per_sweep = p.launches * ((npad / spins_per_kb) * per_kb + 3.0);
     if (best.nt == 0 || p.us_per_sweep < best.us_per_sweep) best = p;
   }
   if (best.nt == 0)
@@ -1378,18 +1403,25 @@ int plan_big(int n, int npad, int R, bool real, BigPlan* out) {
 // Large-N anneal of one instance: the replicas are split into groups of tiles that fit the
 // co-resident grid (each group is an independent cooperative launch); per launch scratch
 // (two spin images, energy accumulators, barrier words) comes from the stream-ordered pool.
+// Bytes of one large-N spin image of rpad replica rows.
+size_t big_image_bytes(int rpad, int npad, int op) {
+  const size_t cells = static_cast<size_t>(rpad) * npad;
+  return op == kBigFp4 ? cells / 2 : (op == kBigBf16 ? 2 * cells : cells);
+}
+
 int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t seed, bool cont,
                int* d_err, char* scratch, int* launches, cudaStream_t st) {
   BigPlan plan;
-  const int rc = plan_big(P.n, P.npad, P.R, real, &plan);
+  const int rc = plan_big(P.n, P.npad, P.R, real, P.jimg4 != nullptr, P.stride_words, &plan);
   if (rc != PIM_OK) return rc;
+  const BigSmem smem = sweep_big_smem(plan.nt, plan.op, P.npad, P.stride_words);
+  if (!smem.ok) return fail(PIM_ERR_UNSUPPORTED, "anneal: large-N variant does not fit");
   const int ncb = P.npad / plan.nt;
   const int tiles_total = (P.R + 127) / 128;
-  const int eb = real ? 2 : 1;
   for (int tile0 = 0; tile0 < tiles_total; tile0 += plan.tiles_per_launch) {
     const int tiles = std::min(plan.tiles_per_launch, tiles_total - tile0);
     const int rpad = tiles * 128;
-    const size_t img_bytes = static_cast<size_t>(rpad) * P.npad * eb;
+    const size_t img_bytes = big_image_bytes(rpad, P.npad, plan.op);
     const size_t energy_bytes = sizeof(float) * 3 * rpad;
     const size_t bytes = 2 * img_bytes + energy_bytes + 256;
     char* d = scratch;
@@ -1400,6 +1432,9 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
     L.P = P;
     L.s_img[0] = reinterpret_cast<uint8_t*>(d);
     L.s_img[1] = reinterpret_cast<uint8_t*>(d + img_bytes);
+    L.j4 = plan.op == kBigFp4 ? P.jimg4 : nullptr;
+    L.stages = smem.stages;
+    L.tab_smem = smem.tab_smem;
     L.energy = reinterpret_cast<float*>(d + 2 * img_bytes);
     L.bar = reinterpret_cast<unsigned int*>(d + 2 * img_bytes + energy_bytes);
     L.nt = plan.nt;
@@ -1413,7 +1448,7 @@ int launch_big(const Problem& P, bool real, int t_begin, int sweeps, uint64_t se
     L.err = d_err;
     L.wait_ns = g_wait_ns.load();
     L.inject = g_inject.load();
-    CK(launch_sweep_big(L, plan.nt, real, tiles * ncb, st), "large-N sweep kernel");
+    CK(launch_sweep_big(L, plan.nt, plan.op, tiles * ncb, st), "large-N sweep kernel");
     if (!scratch) CK(cudaFreeAsync(d, st), "cudaFreeAsync large-N scratch");
     if (launches) ++*launches;
   }
@@ -1501,7 +1536,10 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
   for (size_t e = 0; e < eligible.size(); ++e) {
     const int k = eligible[e];
     BigPlan plan;
-    if (plan_big(insts[k]->n, insts[k]->npad, replicas[k], false, &plan) != PIM_OK) continue;
+    const bool fp4 = insts[k]->d_img4 != nullptr && !(flags & PIM_PATH_BIG_FP8);
+    if (plan_big(insts[k]->n, insts[k]->npad, replicas[k], false, fp4, insts[k]->sched->stride_words,
+                 &plan) != PIM_OK)
+      continue;
     const double u = mid_unit_us(insts[k]);
     const double rest_total = mid_total - u * ((replicas[k] + 127) / 128);
     double rest_max = 0.0;
@@ -1543,7 +1581,8 @@ int check_batch(pim_instance* const* insts, int count, const int* replicas, int 
                 int sweeps, const double* targets, int flags, bool check_steps) {
   if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
   if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
-  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG | PIM_RESULTS_TO_HOST))
+  if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG | PIM_RESULTS_TO_HOST |
+                PIM_PATH_BIG_FP8))
     return fail(PIM_ERR_INVALID, "anneal: unknown flags");
   const bool cont = (flags & PIM_CONTINUE) != 0;
   const bool ref = (flags & PIM_PATH_FP32REF) != 0;
@@ -1592,6 +1631,7 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
     pim_instance* p = insts[k];
     Problem& P = B.probs[k];
     P.jimg = p->d_img;
+    P.jimg4 = (flags & PIM_PATH_BIG_FP8) ? nullptr : p->d_img4;
     P.jf = p->d_jf;
     P.j8 = p->d_J8;
     P.h = p->d_h;
@@ -1665,10 +1705,11 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
   for (int k = 0; k < count && !ref; ++k) {
     if (B.route[k] == kBig) {
       BigPlan plan;
-      const int rc = plan_big(insts[k]->n, insts[k]->npad, replicas[k], insts[k]->real, &plan);
+      const Problem& P = B.probs[k];
+      const int rc = plan_big(P.n, P.npad, P.R, insts[k]->real, P.jimg4 != nullptr, P.stride_words, &plan);
       if (rc != PIM_OK) return rc;
-      const size_t rpad = static_cast<size_t>(plan.tiles_per_launch) * 128;
-      B.big_scratch = std::max(B.big_scratch, 2 * rpad * insts[k]->npad * (insts[k]->real ? 2 : 1) +
+      const int rpad = plan.tiles_per_launch * 128;
+      B.big_scratch = std::max(B.big_scratch, 2 * big_image_bytes(rpad, P.npad, plan.op) +
                                                   sizeof(float) * 3 * rpad + 256);
       continue;
     }
@@ -2035,16 +2076,24 @@ int tune_batch(pim_instance* const* insts, int count, const int* replicas, cudaS
     }
     if (p->n > kMaxNTensor) {
       const int tiles = (replicas[k] + 127) / 128;
-      for (int nt : {64, 128}) {
-        if (p->npad % nt) continue;
-        const std::string key = tune_key("big", p->real ? 1 : 0, p->npad, tiles, nt);
+      const int base = p->real ? kBigBf16 : kBigFp8;
+      const std::pair<int, int> cands[3] = {{64, base}, {128, base}, {64, kBigFp4}};
+      for (const auto& cand : cands) {
+        const int nt = cand.first, op = cand.second;
+        if (p->npad % nt || (op == kBigFp4 && !p->d_img4)) continue;
+        const std::string key = tune_key("big", op, p->npad, tiles, nt);
         if (tune_known(key)) continue;
         BigPlan plan;
         t_force_nt = nt;
-        const int prc = plan_big(p->n, p->npad, replicas[k], p->real, &plan);
+        t_force_op = op;
+        const int prc = plan_big(p->n, p->npad, replicas[k], p->real, p->d_img4 != nullptr,
+                                 p->sched->stride_words, &plan);
+        if (prc == PIM_OK)  // else this variant cannot be co-resident
+          rc = tune_slope(p, replicas[k], PIM_PATH_BIG, nt, st, &us);
         t_force_nt = 0;
-        if (prc != PIM_OK) continue;  // this width cannot be co-resident
-        if ((rc = tune_slope(p, replicas[k], PIM_PATH_BIG, nt, st, &us)) != PIM_OK) return rc;
+        t_force_op = -1;
+        if (prc != PIM_OK) continue;
+        if (rc != PIM_OK) return rc;
         tune_store(key, us);
       }
     }

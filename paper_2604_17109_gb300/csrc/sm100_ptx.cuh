@@ -284,4 +284,52 @@ __device__ __forceinline__ float staircase(float x, int levels) {
   return -1.0f + 2.0f * k / (levels - 1);
 }
 
+// ---- Block-scaled FP4 (kind::mxf4): packed E2M1 operands, UE8M0 scale factors in TMEM ----
+// Instruction descriptor: A and B E2M1 (format code 1 at bits 7-9 / 10-12), N >> 3 at bits
+// 17-22, UE8M0 scale type (bit 23), M >> 4 at bits 24-28; dense, K = 64 per MMA, scale
+// factor ids 0.  The FP32 accumulator type is implied.
+__device__ __forceinline__ uint32_t idesc_mxf4(int m, int n) {
+  return (1u << 7) | (1u << 10) | (static_cast<uint32_t>(n >> 3) << 17) | (1u << 23) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+// D (+)= (A x 2^(sfa-127)) (B x 2^(sfb-127))^T over K = 64 packed E2M1 values (32 bytes of
+// each K-major row), scale factors read from tensor memory at sfa / sfb (one per 32 K).
+__device__ __forceinline__ void mma_mxf4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], "
+      "[%5], p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+
+// Stores the 32-bit word x into 32 consecutive columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t x) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(x)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Eight spins (low 8 bits) -> eight packed E2M1 values, element k in nibble k (low nibble
+// first): +1 = 0x2, -1 = 0xA.  The spread moves bit k to bit 4k + 3 (the sign bit of
+// nibble k).
+__device__ __forceinline__ uint32_t e2m1x8_from_bits(uint32_t b) {
+  uint32_t x = b & 0xFFu;
+  x = (x | (x << 12)) & 0x000F000Fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  x = (x | (x << 3)) & 0x11111111u;
+  return 0xAAAAAAAAu ^ (x << 3);
+}
+
 }  // namespace pim

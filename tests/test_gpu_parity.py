@@ -16,8 +16,10 @@ from gpu_helpers import assert_same, collect, oracle_run, pim, run_library
 pytestmark = pytest.mark.gpu
 
 # library's choice, plain FP32 path (PIM_PATH_FP32REF), persistent mid-N kernel for every
-# integer n <= 1024 (PIM_PATH_MID), large-N kernel for every n > 256 (PIM_PATH_BIG)
-PATHS = [0, 2, 4, 8]
+# integer n <= 1024 (PIM_PATH_MID), large-N kernel for every n > 256 (PIM_PATH_BIG: the
+# coupling-resident E2M1 variant where the couplings allow it), large-N kernel with FP8
+# couplings streamed every sweep (PIM_PATH_BIG | PIM_PATH_BIG_FP8)
+PATHS = [0, 2, 4, 8, 8 | 32]
 
 CASES = [
     # kind, n, replicas, sweeps, seed
@@ -43,6 +45,12 @@ CASES = [
     ("maxcut", 300, 64, 12, 18),
     ("sk2", 600, 130, 10, 16),
     ("sk9", 400, 96, 10, 17),
+    # coupling-resident E2M1 variant: every E2M1 integer magnitude (1, 2, 3, 4, 6); 9
+    # K-blocks of 256 spins (odd: the last ring stage holds one) with the threshold table in
+    # shared memory; npad 3072 (12 K-blocks)
+    ("sk12346", 700, 130, 8, 19),
+    ("sk", 2100, 70, 4, 20),
+    ("maxcut", 3000, 40, 3, 21),
 ]
 
 
@@ -56,6 +64,14 @@ def _inst(kind, n, seed):
         i = np.arange(0, n - 1, 7)
         J[i, i + 1] = J[i + 1, i] = 9 * J[i, i + 1]
         return Instance("sk", n, J, base.h, base.c, seed)
+    if kind == "sk12346":
+        base = sk_pm1(n, seed)
+        rng = np.random.default_rng(seed)
+        mult = rng.choice(np.array([1, 2, 3, 4, 6], np.int8), size=(n, n))
+        mult = np.triu(mult, 1)
+        mult = mult + mult.T
+        J = (base.J.astype(np.int16) * mult).astype(np.int8)
+        return Instance("sk", n, J, base.h, base.c / 3, seed)
     return sk_pm1(n, seed) if kind == "sk" else maxcut_er(n, seed)
 
 
@@ -340,8 +356,10 @@ def test_large_n_bias_and_resume(flags):
         P.pim_destroy(hd)
 
 
-def test_sk4096_sampled_replicas():
-    """SK N = 4096, 256 replicas: sampled replicas bit for bit against the oracle, every
+@pytest.mark.parametrize("flags", [0, 8 | 32])
+def test_sk4096_sampled_replicas(flags):
+    """SK N = 4096, 256 replicas (the library's choice: the coupling-resident E2M1 variant;
+    and FP8 couplings streamed): sampled replicas bit for bit against the oracle, every
     replica's reported energies against its reported states."""
     P = pim()
     inst = sk_pm1(4096, 0)
@@ -351,13 +369,13 @@ def test_sk4096_sampled_replicas():
     hd = P.pim_create(inst.J, None, inst.c)
     try:
         P.pim_set_schedule(hd, beta, eta, 0.5)
-        P.pim_anneal(hd, 256, T, 3, instance_id=1)
+        P.pim_anneal(hd, 256, T, 3, instance_id=1, flags=flags)
         got = collect(hd, 4096)
     finally:
         P.pim_destroy(hd)
     rows = [0, 77, 128, 255]
     want = oracle_run(inst, beta, eta, 0.5, replica_ids=rows, seed=3, q=1)
-    assert_same(got, want, rows=rows, label="sk4096")
+    assert_same(got, want, rows=rows, label=f"sk4096 path={flags}")
     assert np.array_equal(oracle.energy(inst.J, inst.h, got["final_state"]), got["final_E"])
     assert np.array_equal(oracle.energy(inst.J, inst.h, got["best_state"]), got["best_E"])
 
