@@ -80,6 +80,7 @@ MIMO_RATE = {"mimo16": 4000.0, "mimo64": 1000.0}  # offered load, requests per s
 #   compare and collect the new spin 2, energy accumulate 1, spin write-back 0.75
 ALU_OPS_PER_SPIN_UPDATE = 5.0 + 2 + 1 + 1 + 2 + 1 + 0.75
 LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one instruction each per cycle
+FP4_BF16_NOMINAL = 13.5 / 2.25  # dense E2M1 / BF16 tensor rates (nominal, per GPU)
 
 # DRAM bytes (read + write) of the dominant kernel per launch, from ncu captures of these
 # workloads (dram__bytes_read.sum + dram__bytes_write.sum of one launch), as fixed + per-pass
@@ -87,14 +88,14 @@ LANES_PER_SM = 128  # 4 schedulers x 32 lanes issue one instruction each per cyc
 # workload whose kernel changed after its capture has no entry here (traffic reported null):
 #   sk200       sweep_tc_kernel<256,0,queue>, full-size launch: 17.86 MB read + 0.03 MB
 #               written, nothing grows per pass
-#   sk4096      sweep_big_kernel<64,FP8>, 50-sweep capture 19.17 MB = 16.8 MB image (L2-resident
-#               afterwards) + misc, and one 32 KB threshold table per pass
-#   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.156 GB = the 134 MB image
+#   sk4096      sweep_big_kernel<64, E2M1 coupling-resident>, 50-sweep capture 8.86 MB = the
+#               8 MB E2M1 coupling image once + misc, and one 32 KB threshold table per pass
+#   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.137 GB = the 134 MB image
 #               streamed from HBM every pass (it exceeds L2)
 DRAM_TRAFFIC = {
     "sk200": (17.862e6 + 0.027e6, 0.0),
-    "sk4096": (19.171e6 - 51 * 32768.0, 32768.0),
-    "maxcut8192": (0.0, 7.156e9 / 51),
+    "sk4096": (8.857e6 - 51 * 32768.0, 32768.0),
+    "maxcut8192": (0.0, 7.137e9 / 51),
 }
 
 
@@ -751,17 +752,23 @@ def _secondary(args, pim, torch, np, rank):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         k_ms = pim.pim_kernel_ms(handles[0])
+        route0 = pim.pim_batch_route(batch, 0)
         pim.pim_batch_destroy(batch)
         for hd in handles:
             pim.pim_destroy(hd)
         step_ms = statistics.mean(ms)
         updates = sum(i.n * r for i, r in zip(insts, reps)) * sweeps
         flops = sum(2.0 * i.n * i.n * r for i, r in zip(insts, reps)) * sweeps
-        tensor_peak = float(peaks["bf16_tflops"]) * (1.0 if real else 2.0)
+        e2m1 = route0.get("operand") == "e2m1_resident"
+        fp8_peak = float(peaks["bf16_tflops"]) * 2.0
+        tensor_peak = float(peaks["bf16_tflops"]) * (1.0 if real else (FP4_BF16_NOMINAL if e2m1 else 2.0))
+        achieved = flops / (k_ms * 1e-3) / 1e12
         out.append({"workload": name, "value": updates / (step_ms * 1e-3), "unit": METRIC,
                     "ms_per_step": step_ms, "us_per_sweep": step_ms * 1000.0 / sweeps,
-                    "tensor_frac": flops / (k_ms * 1e-3) / 1e12 / tensor_peak,
-                    "dtype": "bf16/f32" if real else "fp8e4m3/i32"})
+                    "tensor_frac": achieved / tensor_peak,
+                    "tensor_frac_of_fp8_peak": None if real else achieved / fp8_peak,
+                    "kernel_of_instance_0": route0,
+                    "dtype": "bf16/f32" if real else ("e2m1/i32" if e2m1 else "fp8e4m3/i32")})
     # MIMO 16x16 16-QAM detection through the device-side request queue (Poisson arrivals)
     from workloads import MIMO_XI, bits_from_symbols, mimo_problem, mimo_scale, mimo_schedule
     nt, count, R, T, rate = 16, 2000, 32, 64, 4000.0
@@ -830,6 +837,7 @@ def run_ours(args, w: Workload):
         step()
     torch.cuda.synchronize()
     info = pim.pim_batch_info(batch)
+    route0 = pim.pim_batch_route(batch, 0)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -935,13 +943,19 @@ def run_ours(args, w: Workload):
     peaks, peak_kind = _peaks()
     clk = clocks.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    tensor_peak = float(peaks["bf16_tflops"]) * (1.0 if real else 2.0)
+    e2m1 = route0.get("operand") == "e2m1_resident"
+    ratio = 1.0 if real else (FP4_BF16_NOMINAL if e2m1 else 2.0)
+    tensor_peak = float(peaks["bf16_tflops"]) * ratio
     tensor_achieved = flops_per_step / (k_ms * 1e-3) / 1e12
     tensor = {"bound": "tensor", "achieved": tensor_achieved, "peak": tensor_peak,
               "unit": "TFLOP/s", "frac": tensor_achieved / tensor_peak, "traffic": None,
               "kernel_ms": k_ms,
               "peak_basis": (f"bf16 {peak_kind} burst" if real else
-                             f"bf16 {peak_kind} burst x 2 (FP8/BF16 nominal ratio)")}
+                             f"bf16 {peak_kind} burst x {ratio:g} "
+                             f"({'E2M1' if e2m1 else 'FP8'}/BF16 nominal ratio)")}
+    if e2m1:
+        fp8_peak = float(peaks["bf16_tflops"]) * 2.0
+        tensor["frac_of_fp8_peak"] = tensor_achieved / fp8_peak
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     if w.n <= 256:
         alu_peak = sm_count * LANES_PER_SM * sm_max * 1e6 / 1e12
@@ -957,13 +971,23 @@ def run_ours(args, w: Workload):
     elif w.n <= 1024 and n_inst > 1:
         roofline = dict(tensor, kernel="sweep_mid_kernel")
     else:
-        roofline = dict(tensor, kernel=f"sweep_big_kernel<{'BF16' if real else 'FP8'}>")
-        # every replica tile streams the whole coupling image from L2 each sweep; HBM sees it
-        # once per sweep when it does not fit L2 (the tiles meet in L2)
-        l2_bytes = sum(i.n * i.n * (2 if real else 1) * ((r + 127) // 128)
-                       for i, r in zip(insts, reps)) * sweeps
-        roofline["coupling_l2_to_sm"] = {"achieved": l2_bytes / (k_ms * 1e-3) / 1e9,
-                                         "unit": "GB/s"}
+        nt, operand = route0.get("tile_width", 0), route0.get("operand", "?")
+        roofline = dict(tensor, kernel=f"sweep_big_kernel<{nt}, {operand}>")
+        # bytes every CTA streams from L2 per sweep: its replica tile's spins and, unless
+        # they are resident, its column block's couplings (all K); HBM sees a streamed
+        # coupling image once per sweep when it does not fit L2 (the tiles meet in L2)
+        spin_b = 0.5 if e2m1 else (2 if real else 1)
+        coup_b = 0.0 if e2m1 else (2 if real else 1)
+        l2_bytes = 0.0
+        for i, r in zip(insts, reps):
+            npad = -(-i.n // 256) * 256
+            ctas = ((r + 127) // 128) * (npad // max(nt, 1))
+            l2_bytes += ctas * (128 * npad * spin_b + nt * npad * coup_b)
+        l2_bytes *= sweeps
+        roofline["operands_l2_to_sm"] = {"achieved": l2_bytes / (k_ms * 1e-3) / 1e9,
+                                         "unit": "GB/s",
+                                         "basis": "spins of the tile (+ streamed coupling rows) "
+                                                  "per CTA per sweep"}
     traffic = DRAM_TRAFFIC.get(w.key)
     if traffic is not None and args.sweeps is None and args.instances is None:
         fixed, per_pass = traffic
@@ -984,12 +1008,13 @@ def run_ours(args, w: Workload):
                           else "analytic cost model"),
               "tuning": pim.pim_tune_report().strip().splitlines() if args.autotune else [],
               "launch": "batch plan replayed as one CUDA graph" if info["uses_graph"]
-                        else "batch plan, direct launches"}
+                        else "batch plan, direct launches",
+              "kernel_of_instance_0": route0}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16/f32" if real else "fp8e4m3/i32",
+        "dtype": "bf16/f32" if real else ("e2m1/i32" if e2m1 else "fp8e4m3/i32"),
         "data": "synthetic",
         "config": config,
         "roofline": roofline,

@@ -235,14 +235,20 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
  * Results are read with the per-instance getters.  A batch whose launches cannot be
  * captured runs them directly instead (pim_batch_info reports which).
  * pim_batch_info: kernel launches per run and whether runs replay a graph (1) or not (0).
+ * pim_batch_route: the kernel instance `index` runs on -- *kernel 0 fused (n <= 256), 1
+ * persistent mid-N, 2 large-N -- and, for the large-N kernel, its tile width (64 or 128
+ * output spins per CTA) and operand variant (0 FP8 E4M3 streamed, 1 BF16 streamed, 2 E2M1
+ * with the couplings resident in shared memory); both 0 / -1 otherwise.  Any output pointer
+ * may be NULL.
  * Errors: PIM_ERR_INVALID, PIM_ERR_STATE (instance changed since creation, CONTINUE without
  *         a previous run), PIM_ERR_UNSUPPORTED, PIM_ERR_NOMEM, PIM_ERR_CUDA.
  *
  * Autotuning (pim_autotune mode 1, the default): pim_batch_create first times, on the
  * batch's own staged instances and with result buffers of its own, every shape class it has
  * not met before on this device -- the fused kernel per (npad, decision path) unit, the
- * persistent mid-N kernel per unit, and the large-N kernel per (real, npad, replica tiles)
- * instance sweep at both tile widths (64 and 128 spins) -- a few sweeps each, and keeps the
+ * persistent mid-N kernel per unit, and the large-N kernel per (operand variant, npad,
+ * replica tiles) instance sweep at both tile widths (64 and 128 spins; the E2M1
+ * coupling-resident variant at 64) -- a few sweeps each, and keeps the
  * times in a process-wide cache keyed by device name and class.  The router and the
  * large-N tile plan of every later run (pim_anneal, pim_anneal_batch, batch plans) use the
  * measured times where the cache has them and the analytic model elsewhere.  All candidate
@@ -254,6 +260,7 @@ int pim_batch_create(pim_batch** out, pim_instance* const* insts, int count, con
 int pim_batch_run(pim_batch* batch, int t_begin, int sweeps, uint64_t seed, int run_flags,
                   void* cuda_stream);
 int pim_batch_info(const pim_batch* batch, int* kernel_launches, int* uses_graph);
+int pim_batch_route(const pim_batch* batch, int index, int* kernel, int* tile_width, int* operand);
 void pim_batch_destroy(pim_batch* batch);
 
 /*
@@ -267,8 +274,8 @@ void pim_batch_destroy(pim_batch* batch);
  * pim_tune_report -- the measured times, one line per shape class:
  * "<device>|<kernel>|<a>|<b>|<c>|<d> <microseconds>" with kernel fused (a = npad,
  * b = 1 diagonal-encoded; us per unit sweep, two CTAs per SM), mid (a = npad, b = decision
- * path; us per unit sweep, one CTA per SM) or big (a = 1 real, b = npad, c = replica tiles,
- * d = tile width; us per instance sweep).  Writes at most cap bytes (NUL-terminated) to
+ * path; us per unit sweep, one CTA per SM) or big (a = operand variant 0 FP8, 1 BF16, 2
+ * E2M1, b = npad, c = replica tiles, d = tile width; us per instance sweep).  Writes at most cap bytes (NUL-terminated) to
  * out (may be NULL) and the size needed to *needed (may be NULL).
  */
 int pim_autotune(int mode);

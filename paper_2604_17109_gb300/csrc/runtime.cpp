@@ -2364,6 +2364,28 @@ PIM_API int pim_batch_info(const pim_batch* b, int* kernel_launches, int* uses_g
   return PIM_OK;
 }
 
+PIM_API int pim_batch_route(const pim_batch* b, int index, int* kernel, int* tile_width,
+                            int* operand) {
+  if (!b) return fail(PIM_ERR_INVALID, "pim_batch_route: batch is NULL");
+  if (index < 0 || index >= static_cast<int>(b->insts.size()))
+    return fail(PIM_ERR_INVALID, "pim_batch_route: index %d out of range", index);
+  const int route = b->plan.route[index];
+  int nt = 0, op = -1;
+  if (route == kBig) {
+    const Problem& P = b->plan.probs[index];
+    BigPlan plan;
+    const int rc = plan_big(P.n, P.npad, P.R, b->insts[index]->real, P.jimg4 != nullptr,
+                            P.stride_words, &plan);
+    if (rc != PIM_OK) return rc;
+    nt = plan.nt;
+    op = plan.op;
+  }
+  if (kernel) *kernel = route;
+  if (tile_width) *tile_width = nt;
+  if (operand) *operand = op;
+  return PIM_OK;
+}
+
 PIM_API void pim_batch_destroy(pim_batch* b) {
   if (!b) return;
   for (pim_instance* p : b->insts)

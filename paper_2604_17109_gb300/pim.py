@@ -80,6 +80,8 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p, C.c_int]),
     "pim_batch_run": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]),
     "pim_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pim_batch_route": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]),
     "pim_batch_destroy": (None, [C.c_void_p]),
     "pim_anneal_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
                                      C.c_void_p, C.c_float, C.c_int, C.c_uint64, C.c_uint32,
@@ -337,6 +339,22 @@ def pim_batch_run(batch: int, sweeps: int, seed: int, t_begin: int = 0, run_flag
                   stream=None) -> None:
     _check(lib().pim_batch_run(batch, int(t_begin), int(sweeps), int(seed), int(run_flags),
                                _stream(stream)), "pim_batch_run")
+
+
+BIG_OPERANDS = {0: "fp8", 1: "bf16", 2: "e2m1_resident"}
+KERNELS = {0: "fused", 1: "mid", 2: "large"}
+
+
+def pim_batch_route(batch: int, index: int) -> dict:
+    """Kernel of instance `index` of the batch; for the large-N kernel also its tile width
+    and operand variant."""
+    k, nt, op = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().pim_batch_route(batch, index, C.byref(k), C.byref(nt), C.byref(op)),
+           "pim_batch_route")
+    out = {"kernel": KERNELS[k.value]}
+    if k.value == 2:
+        out.update(tile_width=nt.value, operand=BIG_OPERANDS[op.value])
+    return out
 
 
 def pim_batch_info(batch: int) -> dict:
