@@ -271,3 +271,39 @@ def test_mid_batch_mixes_diagonal_and_general_units():
     finally:
         for hd in handles:
             P.pim_destroy(hd)
+
+
+def test_batch_route_reports_kernel_and_large_n_variant():
+    """pim_batch_route: fused for n <= 256; the E2M1 coupling-resident large-N variant for
+    integer couplings in {0, +-1, +-2, +-3, +-4, +-6} (FP8 with PIM_PATH_BIG_FP8, and for a
+    coupling magnitude E2M1 cannot hold); BF16 for real couplings."""
+    from workloads import Instance, maxcut_gauss
+    P = pim()
+    sk = sk_pm1(1100, 5)
+    J9 = sk.J.astype(np.int8).copy()
+    J9[0, 1] = J9[1, 0] = 5
+    insts = [sk_pm1(100, 4), sk, Instance("sk", 1100, J9, sk.h, sk.c, 5), maxcut_gauss(600, 6)]
+    beta = linear_beta(4)
+    handles = [P.pim_create(i.J, None, i.c) for i in insts]
+    try:
+        for hd in handles:
+            P.pim_set_schedule(hd, beta, eta_power(beta), 0.5)
+        for flags, want in ((P.PIM_PATH_BIG, ["fused", "e2m1_resident", "fp8", "bf16"]),
+                            (P.PIM_PATH_BIG | P.PIM_PATH_BIG_FP8, ["fused", "fp8", "fp8", "bf16"])):
+            b = P.pim_batch_create(handles, [128] * 4, flags=flags)
+            try:
+                got = [P.pim_batch_route(b, k) for k in range(4)]
+            finally:
+                P.pim_batch_destroy(b)
+            assert got[0] == {"kernel": "fused"}
+            assert [g.get("operand", "fused") for g in got] == want
+            assert all(g["kernel"] == "large" and g["tile_width"] in (64, 128) for g in got[1:])
+        with pytest.raises(P.PimError):
+            b = P.pim_batch_create(handles, [128] * 4)
+            try:
+                P.pim_batch_route(b, 4)
+            finally:
+                P.pim_batch_destroy(b)
+    finally:
+        for hd in handles:
+            P.pim_destroy(hd)
