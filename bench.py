@@ -68,6 +68,9 @@ WORKLOADS = {
     # levels (ap_fixed<W, 4> couplings and intermediates), 1000 problems
     "mimofixed16": Workload("mimofixed16", "mimofixed", 64, 1000, 32, 64, 1.0),
     "mimo64": Workload("mimo64", "mimo", 256, 400, 32, 256, 1.0),
+    # correction-set study: BER of 16x16 16-QAM detection with T = [I, I] (n = 64) and
+    # T = [2I, I, I] (n = 96) on the same problems, and of 4x4 against exhaustive ML
+    "mimodepth16": Workload("mimodepth16", "mimodepth", 64, 1000, 32, 64, 1.0),
 }
 MIMO_RATE = {"mimo16": 4000.0, "mimo64": 1000.0}  # offered load, requests per second
 
@@ -406,6 +409,113 @@ def run_fixed(args, w: Workload):
         "cpu_baseline": cpu_baseline(w),
         "e2e": None,
         "gpu_launches": 2 * args.steps * len(configs),
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _ml_detect(H, y, levels: int):
+    """Exhaustive maximum-likelihood detection (all levels^(2 nt) QAM vectors), the
+    reference detector of the small-system study."""
+    import itertools
+    import numpy as np
+    nt = H.shape[1]
+    pam = np.arange(-levels + 1, levels, 2, dtype=np.float64)
+    pts = (pam[:, None] + 1j * pam[None, :]).ravel()
+    U = pts[np.array(list(itertools.product(range(pts.size), repeat=nt)))]
+    return U[int(np.argmin(np.sum(np.abs(y[None, :] - U @ H.T) ** 2, axis=1)))]
+
+
+def run_mimo_depth(args, w: Workload):
+    """Bit-error rate of 16-QAM detection with the two correction sets the paper prints
+    (supplementary DI-MIMO sections): T = [I, I] (corrections {-2, 0, 2}, n = 4 nt) and
+    T = [2I, I, I] (corrections {-4, .., 4}, n = 6 nt), on the same problems, schedule and
+    draws (float32 datapath, replica of lowest best energy detected), beside the MMSE
+    estimate they start from.  16x16: 1000 problems, Eb/N0 ~ U[10, 25] dB, 64 and 128
+    sweeps.  4x4 at 10 and 15 dB: also exhaustive ML.  value: spin updates/s of the 16x16
+    depth-2 batch (device-resident)."""
+    world, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2604_17109_gb300 import build as pkg_build
+    from paper_2604_17109_gb300 import pim
+    from workloads import MIMO_XI, bits_from_symbols, mimo_problem, mimo_scale, mimo_schedule
+
+    pkg_build.build()
+    stream = torch.cuda.Stream()
+    R = w.replicas
+
+    def detect(probs, depth, T):
+        staged = [pim.pim_mimo_formulate(p.H, p.y, 16, 1.0 / p.es_n0, depth=depth) for p in probs]
+        n = staged[0][0].shape[0]
+        beta, eta = mimo_schedule(T)
+        nt = probs[0].H.shape[1]
+        handles = [pim.pim_create(J, h, mimo_scale(nt)) for J, h, _ in staged]
+        for hd in handles:
+            pim.pim_set_schedule(hd, beta, eta, MIMO_XI)
+        ids = list(range(len(probs)))
+        pim.pim_anneal_batch(handles, R, T, seed=7, instance_ids=ids, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pim.pim_anneal_batch(handles, R, T, seed=7, instance_ids=ids, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        bits = []
+        for hd, (_, _, xm) in zip(handles, staged):
+            best = pim.pim_energies(hd)["best_E"]
+            s = pim.pim_best_state(hd, n)[int(np.argmin(best))]
+            bits.append(bits_from_symbols(pim.pim_mimo_reconstruct(xm, s, 16, depth=depth), 16))
+        for hd in handles:
+            pim.pim_destroy(hd)
+        mmse = [bits_from_symbols(xm, 16) for _, _, xm in staged]
+        return np.stack(bits), np.stack(mmse), statistics.mean(ms), n
+
+    study = {}
+    with ClockSampler(local) as clocks:
+        rng = np.random.default_rng(3000 + rank)
+        snr = rng.uniform(10.0, 25.0, w.count)
+        probs = [mimo_problem(16, 16, 16, float(v), rank * w.count + k) for k, v in enumerate(snr)]
+        truth = np.stack([p.bits for p in probs])
+        ms_main = None
+        for depth in (2, 3):
+            for T in (w.sweeps, 2 * w.sweeps):
+                det, mmse, ms, n = detect(probs, depth, T)
+                if depth == 2 and T == w.sweeps:
+                    ms_main = ms
+                study[f"16x16 depth{depth} T{T}"] = {"n": n, "ber": float(np.mean(truth != det)),
+                                                     "ms_per_batch": ms}
+        study["16x16 mmse"] = {"ber": float(np.mean(truth != mmse))}
+        for ebn0 in (10.0, 15.0):
+            small = [mimo_problem(4, 4, 16, ebn0, 10_000 + rank * 1000 + k) for k in range(300)]
+            truth4 = np.stack([p.bits for p in small])
+            ml = np.stack([bits_from_symbols(_ml_detect(p.H, p.y, 4), 16) for p in small])
+            row = {"ml": float(np.mean(truth4 != ml))}
+            for depth in (2, 3):
+                det, mmse, _, n = detect(small, depth, w.sweeps)
+                row[f"pimi_depth{depth}"] = float(np.mean(truth4 != det))
+            row["mmse"] = float(np.mean(truth4 != mmse))
+            study[f"4x4 {ebn0:g} dB (300 problems)"] = row
+    if rank != 0:
+        return 0
+    updates = w.count * w.n * R * w.sweeps
+    line = {
+        "metric": METRIC, "value": updates / (ms_main * 1e-3), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_main, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": f"mimo16x16_16qam_{w.count}req_{R}rep_correction_set_study",
+                   "channel": "i.i.d. Rayleigh CN(0,1), 16-QAM Gray",
+                   "schedule": "beta=1, eta=sqrt(1/(5 gamma)), gamma 0.01->1, xi=1, c=2/Nr",
+                   "detection": "replica of lowest best energy, its best state"},
+        "study": study,
+        "cpu_baseline": cpu_baseline(dataclasses.replace(w, kind="mimo")),
+        "e2e": None,
+        "gpu_launches": 2 * max(1, args.steps) * 4,  # timed 16x16 batches: init + sweep kernel
         "clocks": clocks.summary(),
     }
     print(json.dumps(line))
@@ -1060,6 +1170,8 @@ def main():
         return run_mimo(args, w)
     if w.kind == "mimofixed":
         return run_mimo_fixed(args, w)
+    if w.kind == "mimodepth":
+        return run_mimo_depth(args, w)
     if w.kind == "fixed":
         return run_fixed(args, w)
     return run_ours(args, w)

@@ -317,12 +317,22 @@ int pim_anneal_sequential(pim_instance* inst, int replicas, int t_begin, int swe
  *   1 / (Es/N0)).
  * pim_mimo_reconstruct -- x_hat = slice(x_mmse + T s) for spins s (n int8 +-1), nt complex
  *   out (reconstruction section).
- * Errors: PIM_ERR_INVALID (sizes, constellation, non-positive-definite MMSE system).
+ * pim_mimo_formulate_depth / pim_mimo_reconstruct_depth -- the same with the correction
+ *   set chosen by `depth` (spins per real symbol component): 2 = T = [I, I] (corrections
+ *   {-2, 0, 2}), 3 = T = [2I, I, I] (corrections {-4, .., 4}), 0 = the constellation's
+ *   default above; n = depth * 2 nt.  The paper prints both sets and leaves the choice per
+ *   constellation open ("higher-order constellations require larger sets").
+ * Errors: PIM_ERR_INVALID (sizes, constellation, depth, non-positive-definite MMSE system).
  */
 int pim_mimo_formulate(int nt, int nr, int qam, const double* H, const double* y,
                        double mmse_reg, double* J, double* h, double* x_mmse);
 int pim_mimo_reconstruct(int nt, int qam, const double* x_mmse, const int8_t* spins,
                          double* x_hat);
+int pim_mimo_formulate_depth(int nt, int nr, int qam, int depth, const double* H,
+                             const double* y, double mmse_reg, double* J, double* h,
+                             double* x_mmse);
+int pim_mimo_reconstruct_depth(int nt, int qam, int depth, const double* x_mmse,
+                               const int8_t* spins, double* x_hat);
 
 /*
  * MIMO-detection server -- the real-time request loop of the supplementary "Kernel

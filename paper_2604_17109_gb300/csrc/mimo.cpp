@@ -19,7 +19,14 @@ int mimo_spins_per_component(int qam) {
   return 0;
 }
 
-static double weight_of_block(int qam, int b) { return (qam == 64 && b == 0) ? 2.0 : 1.0; }
+int mimo_depth(int qam, int depth) {
+  if (mimo_spins_per_component(qam) == 0) return 0;
+  if (depth == 0) return mimo_spins_per_component(qam);
+  return depth == 2 || depth == 3 ? depth : 0;
+}
+
+// Weight of spin block b in T: [I, I] (depth 2) or [2I, I, I] (depth 3).
+static double weight_of_block(int depth, int b) { return (depth == 3 && b == 0) ? 2.0 : 1.0; }
 
 static int pam_levels(int qam) { return qam == 4 ? 2 : (qam == 16 ? 4 : 8); }
 
@@ -80,8 +87,8 @@ static bool mmse_solve(int nt, int nr, const cd* H, const cd* y, double reg, cd*
 }
 
 int mimo_formulate(int nt, int nr, int qam, const double* H_ri, const double* y_ri, double reg,
-                   double* J_out, double* h_out, double* xm_ri) {
-  const int ncopy = mimo_spins_per_component(qam);
+                   double* J_out, double* h_out, double* xm_ri, int depth) {
+  const int ncopy = mimo_depth(qam, depth);
   const int two_nt = 2 * nt, n = ncopy * two_nt;
   const int L = pam_levels(qam);
   std::vector<cd> H(static_cast<size_t>(nr) * nt), y(nr), z(nt), gram;
@@ -123,22 +130,23 @@ int mimo_formulate(int nt, int nr, int qam, const double* H_ri, const double* y_
   //   J[k][l] = -2 w_b w_c G[m][m'] (k != l),  h[k] = 2 w_b g[m]
   for (int k = 0; k < n; ++k) {
     const int bk = k / two_nt, mk = k % two_nt;
-    const double wk = weight_of_block(qam, bk);
+    const double wk = weight_of_block(ncopy, bk);
     for (int l = 0; l < n; ++l) {
       const int bl = l / two_nt, ml = l % two_nt;
       J_out[static_cast<size_t>(k) * n + l] =
-          k == l ? 0.0 : -2.0 * wk * weight_of_block(qam, bl) * G[mk * two_nt + ml];
+          k == l ? 0.0 : -2.0 * wk * weight_of_block(ncopy, bl) * G[mk * two_nt + ml];
     }
     h_out[k] = 2.0 * wk * g[mk];
   }
   return PIM_OK;
 }
 
-void mimo_reconstruct(int nt, int qam, const double* xm_ri, const int8_t* spins, double* x_ri) {
-  const int ncopy = mimo_spins_per_component(qam), two_nt = 2 * nt, L = pam_levels(qam);
+void mimo_reconstruct(int nt, int qam, const double* xm_ri, const int8_t* spins, double* x_ri,
+                      int depth) {
+  const int ncopy = mimo_depth(qam, depth), two_nt = 2 * nt, L = pam_levels(qam);
   for (int m = 0; m < two_nt; ++m) {
     double d = 0.0;
-    for (int b = 0; b < ncopy; ++b) d += weight_of_block(qam, b) * spins[b * two_nt + m];
+    for (int b = 0; b < ncopy; ++b) d += weight_of_block(ncopy, b) * spins[b * two_nt + m];
     const int c = m % nt;
     const double base = m < nt ? xm_ri[2 * c] : xm_ri[2 * c + 1];
     x_ri[2 * c + (m < nt ? 0 : 1)] = slice_pam(base + d, L);

@@ -763,3 +763,23 @@ PIM_API int pim_mimo_reconstruct(int nt, int qam, const double* x_mmse, const in
   pim::mimo_reconstruct(nt, qam, x_mmse, spins, x_hat);
   return PIM_OK;
 }
+
+PIM_API int pim_mimo_formulate_depth(int nt, int nr, int qam, int depth, const double* H,
+                                     const double* y, double mmse_reg, double* J, double* h,
+                                     double* x_mmse) {
+  if (nt < 1 || nr < nt || !H || !y || !J || !h || !x_mmse || !(mmse_reg > 0.0) ||
+      pim::mimo_depth(qam, depth) == 0)
+    return fail_msg(PIM_ERR_INVALID, "pim_mimo_formulate_depth: bad arguments");
+  const int rc = pim::mimo_formulate(nt, nr, qam, H, y, mmse_reg, J, h, x_mmse, depth);
+  if (rc != PIM_OK)
+    return fail_msg(rc, "pim_mimo_formulate_depth: MMSE system not positive definite");
+  return PIM_OK;
+}
+
+PIM_API int pim_mimo_reconstruct_depth(int nt, int qam, int depth, const double* x_mmse,
+                                       const int8_t* spins, double* x_hat) {
+  if (nt < 1 || !x_mmse || !spins || !x_hat || pim::mimo_depth(qam, depth) == 0)
+    return fail_msg(PIM_ERR_INVALID, "pim_mimo_reconstruct_depth: bad arguments");
+  pim::mimo_reconstruct(nt, qam, x_mmse, spins, x_hat, depth);
+  return PIM_OK;
+}

@@ -63,6 +63,11 @@ SIGNATURES = {
     "pim_mimo_formulate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pim_mimo_reconstruct": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pim_mimo_formulate_depth": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                           C.c_void_p]),
+    "pim_mimo_reconstruct_depth": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
     "pim_mimo_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_void_p]),
     "pim_mimo_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                          C.c_uint32, C.POINTER(C.c_uint64)]),
@@ -228,27 +233,37 @@ def spins_per_component(qam: int) -> int:
     return {4: 2, 16: 2, 64: 3}[qam]
 
 
-def pim_mimo_formulate(H, y, qam: int, mmse_reg: float):
-    """(J n x n, h n, x_mmse nt complex) of the DI-MIMO instance of (H, y)."""
+def pim_mimo_formulate(H, y, qam: int, mmse_reg: float, depth: int = 0):
+    """(J n x n, h n, x_mmse nt complex) of the DI-MIMO instance of (H, y); depth 0 = the
+    constellation's correction set, 2 = T = [I, I], 3 = T = [2I, I, I]."""
     H = np.asarray(H)
     nr, nt = H.shape
-    n = spins_per_component(qam) * 2 * nt
+    n = (depth or spins_per_component(qam)) * 2 * nt
     J = np.empty((n, n), np.float64)
     h = np.empty(n, np.float64)
     xm = np.empty(2 * nt, np.float64)
     Hri, yri = _complex_ri(H), _complex_ri(y)
-    _check(lib().pim_mimo_formulate(nt, nr, int(qam), _ptr(Hri), _ptr(yri), float(mmse_reg),
-                                    _ptr(J), _ptr(h), _ptr(xm)), "pim_mimo_formulate")
+    if depth:
+        _check(lib().pim_mimo_formulate_depth(nt, nr, int(qam), int(depth), _ptr(Hri), _ptr(yri),
+                                              float(mmse_reg), _ptr(J), _ptr(h), _ptr(xm)),
+               "pim_mimo_formulate_depth")
+    else:
+        _check(lib().pim_mimo_formulate(nt, nr, int(qam), _ptr(Hri), _ptr(yri), float(mmse_reg),
+                                        _ptr(J), _ptr(h), _ptr(xm)), "pim_mimo_formulate")
     return J, h, xm.view(np.complex128)
 
 
-def pim_mimo_reconstruct(x_mmse, spins, qam: int) -> np.ndarray:
+def pim_mimo_reconstruct(x_mmse, spins, qam: int, depth: int = 0) -> np.ndarray:
     xm = _complex_ri(x_mmse)
     nt = xm.size // 2
     s = np.ascontiguousarray(spins, dtype=np.int8)
     out = np.empty(2 * nt, np.float64)
-    _check(lib().pim_mimo_reconstruct(nt, int(qam), _ptr(xm), _ptr(s), _ptr(out)),
-           "pim_mimo_reconstruct")
+    if depth:
+        _check(lib().pim_mimo_reconstruct_depth(nt, int(qam), int(depth), _ptr(xm), _ptr(s),
+                                                _ptr(out)), "pim_mimo_reconstruct_depth")
+    else:
+        _check(lib().pim_mimo_reconstruct(nt, int(qam), _ptr(xm), _ptr(s), _ptr(out)),
+               "pim_mimo_reconstruct")
     return out.view(np.complex128)
 
 

@@ -107,3 +107,28 @@ def test_library_formulation_matches_oracle(nt, nr, qam):
         s = np.where(rng.random(J.shape[0]) < 0.5, -1, 1).astype(np.int8)
         assert np.array_equal(P.pim_mimo_reconstruct(xm, s, qam),
                               om.reconstruct(xo, s, WEIGHTS[qam], LEVELS[qam]))
+
+
+@pytest.mark.parametrize("nt,nr,qam,depth", [(4, 4, 16, 3), (8, 8, 4, 3), (4, 6, 64, 2), (16, 16, 16, 2)])
+def test_library_formulation_with_explicit_depth_matches_oracle(nt, nr, qam, depth):
+    """Either correction set on any constellation: T = [I, I] (depth 2) or [2I, I, I]
+    (depth 3)."""
+    from paper_2604_17109_gb300 import build
+    build.build()
+    from paper_2604_17109_gb300 import pim as P
+    weights = (1.0, 1.0) if depth == 2 else (2.0, 1.0, 1.0)
+    p = mimo_problem(nt, nr, qam, 12.0, 5)
+    J, h, xm = P.pim_mimo_formulate(p.H, p.y, qam, 0.1, depth=depth)
+    assert J.shape == (depth * 2 * nt, depth * 2 * nt)
+    xo = om.mmse(p.H, p.y, 0.1, LEVELS[qam])
+    Jo, ho = om.di_mimo(p.H, p.y, xo, weights)
+    assert np.array_equal(xm, xo)
+    assert np.abs(J - Jo).max() <= 1e-12 * np.abs(Jo).max()
+    assert np.abs(h - ho).max() <= 1e-12 * max(1.0, np.abs(ho).max())
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        s = np.where(rng.random(J.shape[0]) < 0.5, -1, 1).astype(np.int8)
+        assert np.array_equal(P.pim_mimo_reconstruct(xm, s, qam, depth=depth),
+                              om.reconstruct(xo, s, weights, LEVELS[qam]))
+    with pytest.raises(P.PimError):
+        P.pim_mimo_formulate(p.H, p.y, qam, 0.1, depth=4)
