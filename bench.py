@@ -432,7 +432,7 @@ def run_mimo_depth(args, w: Workload):
     (supplementary DI-MIMO sections): T = [I, I] (corrections {-2, 0, 2}, n = 4 nt) and
     T = [2I, I, I] (corrections {-4, .., 4}, n = 6 nt), on the same problems, schedule and
     draws (float32 datapath, replica of lowest best energy detected), beside the MMSE
-    estimate they start from.  16x16: 1000 problems, Eb/N0 ~ U[10, 25] dB, 64 and 128
+    estimate they start from.  16x16: 1000 problems, Eb/N0 ~ U[10, 25] dB, 64 and 256
     sweeps.  4x4 at 10 and 15 dB: also exhaustive ML.  value: spin updates/s of the 16x16
     depth-2 batch (device-resident)."""
     world, rank, local = _dist()
@@ -447,12 +447,12 @@ def run_mimo_depth(args, w: Workload):
     stream = torch.cuda.Stream()
     R = w.replicas
 
-    def detect(probs, depth, T):
+    def detect(probs, depth, T, cf=1.0):
         staged = [pim.pim_mimo_formulate(p.H, p.y, 16, 1.0 / p.es_n0, depth=depth) for p in probs]
         n = staged[0][0].shape[0]
         beta, eta = mimo_schedule(T)
         nt = probs[0].H.shape[1]
-        handles = [pim.pim_create(J, h, mimo_scale(nt)) for J, h, _ in staged]
+        handles = [pim.pim_create(J, h, mimo_scale(nt) * cf) for J, h, _ in staged]
         for hd in handles:
             pim.pim_set_schedule(hd, beta, eta, MIMO_XI)
         ids = list(range(len(probs)))
@@ -483,13 +483,15 @@ def run_mimo_depth(args, w: Workload):
         probs = [mimo_problem(16, 16, 16, float(v), rank * w.count + k) for k, v in enumerate(snr)]
         truth = np.stack([p.bits for p in probs])
         ms_main = None
-        for depth in (2, 3):
-            for T in (w.sweeps, 2 * w.sweeps):
-                det, mmse, ms, n = detect(probs, depth, T)
-                if depth == 2 and T == w.sweeps:
-                    ms_main = ms
-                study[f"16x16 depth{depth} T{T}"] = {"n": n, "ber": float(np.mean(truth != det)),
-                                                     "ms_per_batch": ms}
+        # the schedule's defaults at 64 and 256 sweeps, and the best coupling scale of a
+        # sweep over c x {1, 1/2, 1/4, 1/8}, xi in {0.5, 1, 2} for each depth at 256 sweeps
+        for depth, T, cf in ((2, w.sweeps, 1.0), (2, 4 * w.sweeps, 1.0), (2, 4 * w.sweeps, 0.5),
+                             (3, w.sweeps, 1.0), (3, 4 * w.sweeps, 1.0), (3, 4 * w.sweeps, 0.25)):
+            det, mmse, ms, n = detect(probs, depth, T, cf)
+            if depth == 2 and T == w.sweeps and cf == 1.0:
+                ms_main = ms
+            study[f"16x16 depth{depth} T{T} c x {cf:g}"] = {
+                "n": n, "ber": float(np.mean(truth != det)), "ms_per_batch": ms}
         study["16x16 mmse"] = {"ber": float(np.mean(truth != mmse))}
         for ebn0 in (10.0, 15.0):
             small = [mimo_problem(4, 4, 16, ebn0, 10_000 + rank * 1000 + k) for k in range(300)]
@@ -515,7 +517,7 @@ def run_mimo_depth(args, w: Workload):
         "study": study,
         "cpu_baseline": cpu_baseline(dataclasses.replace(w, kind="mimo")),
         "e2e": None,
-        "gpu_launches": 2 * max(1, args.steps) * 4,  # timed 16x16 batches: init + sweep kernel
+        "gpu_launches": 2 * max(1, args.steps) * 6,  # timed 16x16 batches: init + sweep kernel
         "clocks": clocks.summary(),
     }
     print(json.dumps(line))
