@@ -1047,8 +1047,17 @@ def run_ours(args, w: Workload):
         pim.pim_destroy(hd)
 
     secondary = None
+    probes = None
     if w.key == "sk200" and args.instances is None and args.sweeps is None and not args.no_secondary:
         secondary = _secondary(args, pim, torch, np, rank)
+        # measured rates of the units the kernels are bound by (own probe kernels)
+        probes = {"tensor_tflops": {k: pim.pim_probe_tensor(k, 20000) for k in ("bf16", "fp8", "e2m1")},
+                  "bulk_copy_ingest_gbs_per_sm": {
+                      "32KB_own_region": pim.pim_probe_ingest(32768, 4000, shared=False),
+                      "16KB_own_region": pim.pim_probe_ingest(16384, 8000, shared=False),
+                      "32KB_same_region_all_sms": pim.pim_probe_ingest(32768, 4000, shared=True)},
+                  "basis": "one CTA per SM; M=128 N=256 tcgen05.mma back to back on shared-memory "
+                           "operands / cp.async.bulk through a 4-stage ring from L2, no compute"}
 
     if rank != 0:
         return 0
@@ -1134,6 +1143,7 @@ def run_ours(args, w: Workload):
         "tts99": tts,
         "field_error": field_error,
         "secondary_workloads": secondary,
+        "probes": probes,
         "cpu_baseline": cpu_baseline(w),
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,

@@ -282,6 +282,25 @@ int pim_autotune(int mode);
 int pim_tune_report(char* out, size_t cap, size_t* needed);
 
 /*
+ * Measurement probes (no anneal; they synchronise the device): the rates of the units the
+ * sweep kernels are bound by on the current GPU, for the roofline fractions the benchmark
+ * reports beside the prescribed peaks.
+ * pim_probe_tensor -- one CTA per SM issues `iters` tcgen05.mma of M = 128, N = 256 back to
+ *   back on shared-memory operands into one TMEM accumulator; *tflops = dense rate over all
+ *   SMs.  kind 0: FP8 E4M3 (kind::f8f6f4, K = 32), 1: BF16 (kind::f16, K = 16), 2: E2M1
+ *   block-scaled with unit scale factors (kind::mxf4, K = 64) -- the operand kinds of the
+ *   sweep kernels.  Keep iters x 1 MFLOP within a second of work (e.g. 20000).
+ * pim_probe_ingest -- one CTA per SM streams `iters` cp.async.bulk copies of `bytes` (a
+ *   multiple of 16, at most 32768) from an L2-resident source through a 4-stage ring, no
+ *   compute; *gbs_per_sm = bytes per nanosecond of the slowest SM.  shared 0: each SM reads
+ *   its own 256 KB; shared 1: all SMs read the same 256 KB.
+ * Errors: PIM_ERR_INVALID (arguments), PIM_ERR_NOMEM, PIM_ERR_CUDA, PIM_ERR_TIMEOUT (a
+ *   bounded wait of the probe gave up).
+ */
+int pim_probe_tensor(int kind, int iters, double* tflops);
+int pim_probe_ingest(int bytes, int iters, int shared, double* gbs_per_sm);
+
+/*
  * pim_anneal_sequential -- conventional PIM with sequential updates (Eq. 3; Box 1, orange
  * path), the baseline of the fully parallel loop, on integer couplings.
  *   Sweep k (schedule entry k) updates spins i = 0 .. n-1 one after another, each from the

@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libpimi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["runtime.cpp", "host_tables.cpp", "mimo.cpp", "serve.cpp", "k_stage.cu", "k_ref.cu", "k_sweep_tc.cu",
            "k_sweep_big.cu", "k_sweep_mid.cu", "k_sweep_float.cu", "k_sequential.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "k_probe.cu"]
 
 
 def _nvcc() -> str:

@@ -87,6 +87,8 @@ SIGNATURES = {
     "pim_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pim_batch_route": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int)]),
+    "pim_probe_tensor": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "pim_probe_ingest": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "pim_batch_destroy": (None, [C.c_void_p]),
     "pim_anneal_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
                                      C.c_void_p, C.c_float, C.c_int, C.c_uint64, C.c_uint32,
@@ -370,6 +372,26 @@ def pim_batch_route(batch: int, index: int) -> dict:
     if k.value == 2:
         out.update(tile_width=nt.value, operand=BIG_OPERANDS[op.value])
     return out
+
+
+TENSOR_KINDS = {"fp8": 0, "bf16": 1, "e2m1": 2}
+
+
+def pim_probe_tensor(kind: str, iters: int = 20000) -> float:
+    """Measured dense tcgen05 rate (TFLOP/s, all SMs) of one operand kind."""
+    out = C.c_double()
+    if kind not in TENSOR_KINDS:
+        raise PimError(PIM_ERR_INVALID, "pim_probe_tensor", f"unknown kind {kind!r}")
+    _check(lib().pim_probe_tensor(TENSOR_KINDS[kind], int(iters), C.byref(out)), "pim_probe_tensor")
+    return out.value
+
+
+def pim_probe_ingest(nbytes: int = 32768, iters: int = 4000, shared: bool = False) -> float:
+    """Measured cp.async.bulk ingest of one SM from L2 (GB/s) while every SM streams."""
+    out = C.c_double()
+    _check(lib().pim_probe_ingest(int(nbytes), int(iters), 1 if shared else 0, C.byref(out)),
+           "pim_probe_ingest")
+    return out.value
 
 
 def pim_batch_info(batch: int) -> dict:
