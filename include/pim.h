@@ -87,11 +87,11 @@ typedef enum pim_flags {
                            getters wait for the run and read host memory instead of issuing
                            a synchronous copy each.  Costs R * (24 + 8 * words) bytes of
                            device-to-host traffic per instance and run. */
-  PIM_PATH_BIG_FP8 = 32 /* on the large-N kernel, stream FP8 E4M3 couplings every sweep even
-                           where the coupling-resident E2M1 variant applies (integer couplings
-                           in {0, +-1, +-2, +-3, +-4, +-6}, 256 < n <= 4096); same decisions,
-                           for tests and tuning.  Without it the library picks the variant
-                           from its cost model or measured times. */
+  PIM_PATH_FP8 = 32     /* FP8 E4M3 operands only: no E2M1 coupling-resident variant of the
+                           large-N kernel, which applies to integer couplings in {0, +-1, +-2,
+                           +-3, +-4, +-6} with 256 < n <= 4096; same decisions, for tests and
+                           tuning.  Without it the library picks the variant from its cost
+                           model or measured times. */
 } pim_flags;
 
 typedef struct pim_instance pim_instance;
@@ -226,7 +226,7 @@ int pim_anneal_batch(pim_instance* const* insts, int count, const int* replicas,
  *                 schedule and replica counts while it exists (pim_batch_run checks).
  *   replicas      count entries >= 1; instance_ids (NULL = 0..count-1) and targets (NULL
  *                 or NaN = none) as in pim_anneal_batch.
- *   flags         0, PIM_PATH_MID or PIM_PATH_BIG, each optionally with PIM_PATH_BIG_FP8.
+ *   flags         0, PIM_PATH_MID or PIM_PATH_BIG, each optionally with PIM_PATH_FP8.
  * pim_batch_run runs sweeps t_begin .. t_begin+sweeps-1 of every instance, asynchronously on
  * `cuda_stream`: the first run with given (t_begin, sweeps, seed, run_flags) captures the
  * batch's launches into a CUDA graph (later changes update the instantiated graph in

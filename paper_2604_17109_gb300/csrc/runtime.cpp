@@ -1536,7 +1536,7 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
   for (size_t e = 0; e < eligible.size(); ++e) {
     const int k = eligible[e];
     BigPlan plan;
-    const bool fp4 = insts[k]->d_img4 != nullptr && !(flags & PIM_PATH_BIG_FP8);
+    const bool fp4 = insts[k]->d_img4 != nullptr && !(flags & PIM_PATH_FP8);
     if (plan_big(insts[k]->n, insts[k]->npad, replicas[k], false, fp4, insts[k]->sched->stride_words,
                  &plan) != PIM_OK)
       continue;
@@ -1562,6 +1562,7 @@ int route_batch(pim_instance* const* insts, const int* replicas, int count, int 
 // fused 0-5, mid-N general path 6, mid-N diagonal-encoded 7
 constexpr int kGroups = 8, kMidGroup = 6, kMidDiagGroup = 7;
 
+
 // Launch description of one batch: problem descriptors, the unit lists of each kernel group
 // (fused: npad 128 | 256 x diagonal-encoded | general bias | real-valued; persistent mid-N),
 // the large-N instances, and the layout of the one device buffer that holds them.
@@ -1582,7 +1583,7 @@ int check_batch(pim_instance* const* insts, int count, const int* replicas, int 
   if (!insts || count < 1 || !replicas) return fail(PIM_ERR_INVALID, "anneal: empty batch");
   if (sweeps < 0 || t_begin < 0) return fail(PIM_ERR_INVALID, "anneal: negative t_begin/sweeps");
   if (flags & ~(PIM_CONTINUE | PIM_PATH_FP32REF | PIM_PATH_MID | PIM_PATH_BIG | PIM_RESULTS_TO_HOST |
-                PIM_PATH_BIG_FP8))
+                PIM_PATH_FP8))
     return fail(PIM_ERR_INVALID, "anneal: unknown flags");
   const bool cont = (flags & PIM_CONTINUE) != 0;
   const bool ref = (flags & PIM_PATH_FP32REF) != 0;
@@ -1631,7 +1632,7 @@ int build_plan(pim_instance* const* insts, int count, const int* replicas, const
     pim_instance* p = insts[k];
     Problem& P = B.probs[k];
     P.jimg = p->d_img;
-    P.jimg4 = (flags & PIM_PATH_BIG_FP8) ? nullptr : p->d_img4;
+    P.jimg4 = (flags & PIM_PATH_FP8) ? nullptr : p->d_img4;
     P.jf = p->d_jf;
     P.j8 = p->d_J8;
     P.h = p->d_h;

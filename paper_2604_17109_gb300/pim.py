@@ -22,7 +22,7 @@ PIM_J_INT8, PIM_J_FP32, PIM_J_FP64 = 0, 1, 2
 PIM_NOISE_GAUSS, PIM_NOISE_UNIFORM = 0, 1
 PIM_ACT_TANH, PIM_ACT_LUT = 0, 1
 PIM_CONTINUE, PIM_PATH_FP32REF, PIM_PATH_MID, PIM_PATH_BIG, PIM_RESULTS_TO_HOST = 1, 2, 4, 8, 16
-PIM_PATH_BIG_FP8 = 32
+PIM_PATH_FP8 = 32
 PIM_NOALLOC_MAX_N, PIM_NOALLOC_MAX_STEPS, PIM_NOALLOC_MAX_REPLICAS = 256, 2048, 4096
 
 # name -> (restype, argtypes); every symbol declared in include/pim.h

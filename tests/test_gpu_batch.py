@@ -275,7 +275,7 @@ def test_mid_batch_mixes_diagonal_and_general_units():
 
 def test_batch_route_reports_kernel_and_large_n_variant():
     """pim_batch_route: fused for n <= 256; the E2M1 coupling-resident large-N variant for
-    integer couplings in {0, +-1, +-2, +-3, +-4, +-6} (FP8 with PIM_PATH_BIG_FP8, and for a
+    integer couplings in {0, +-1, +-2, +-3, +-4, +-6} (FP8 with PIM_PATH_FP8, and for a
     coupling magnitude E2M1 cannot hold); BF16 for real couplings."""
     from workloads import Instance, maxcut_gauss
     P = pim()
@@ -289,7 +289,7 @@ def test_batch_route_reports_kernel_and_large_n_variant():
         for hd in handles:
             P.pim_set_schedule(hd, beta, eta_power(beta), 0.5)
         for flags, want in ((P.PIM_PATH_BIG, ["fused", "e2m1_resident", "fp8", "bf16"]),
-                            (P.PIM_PATH_BIG | P.PIM_PATH_BIG_FP8, ["fused", "fp8", "fp8", "bf16"])):
+                            (P.PIM_PATH_BIG | P.PIM_PATH_FP8, ["fused", "fp8", "fp8", "bf16"])):
             b = P.pim_batch_create(handles, [128] * 4, flags=flags)
             try:
                 got = [P.pim_batch_route(b, k) for k in range(4)]

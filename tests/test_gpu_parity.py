@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 # library's choice, plain FP32 path (PIM_PATH_FP32REF), persistent mid-N kernel for every
 # integer n <= 1024 (PIM_PATH_MID), large-N kernel for every n > 256 (PIM_PATH_BIG: the
 # coupling-resident E2M1 variant where the couplings allow it), large-N kernel with FP8
-# couplings streamed every sweep (PIM_PATH_BIG | PIM_PATH_BIG_FP8)
+# couplings streamed every sweep (PIM_PATH_BIG | PIM_PATH_FP8)
 PATHS = [0, 2, 4, 8, 8 | 32]
 
 CASES = [
