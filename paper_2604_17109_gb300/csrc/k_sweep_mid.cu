@@ -62,23 +62,38 @@ __device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint3
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: integer D in the low mantissa bits
 constexpr uint32_t kMagicBits = 0x4B400000u;
 
+// Bits of (a + 1.5 * 2^23) and (b + 1.5 * 2^23) for two exactly integral fields in one
+// packed FP32 add (round to nearest: identical to two scalar adds, exact for |D| < 2^22).
+__device__ __forceinline__ void magic_add2(uint32_t a, uint32_t b, uint32_t& va, uint32_t& vb) {
+  uint64_t pr, rr;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(pr) : "r"(a), "r"(b));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(pr), "l"(0x4B4000004B400000ull));
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(va), "=r"(vb) : "l"(rr));
+}
+
 // Sixteen spins of one replica, general-bias table without bias (h = 0, plain image):
 // vb = bits(D + 1.5 * 2^23) = 0x4B400000 + I, the 16-bit threshold of (s, I) at shared
 // address tab_c + 4 vb + 2 s (tab_c = table + 4 (imax - 0x4B400000), mod 2^32), and
 // key >= M  <=>  d >= 16 M for the 16-bit draw d (key = d >> 4); the sign bits of d - 16 M
 // (new spin -1) are shifted in by two chains.  sum_all / sum_up collect vb over all spins /
 // the +1 spins for the energy.  Returns the new spins as bits 0..15.
+template <bool DECIDE>
 __device__ __forceinline__ uint32_t bias_chunk16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
                                                  uint32_t cw16, uint32_t tab_c, uint32_t& sum_all,
-                                                 uint32_t& sum_up, bool decide) {
+                                                 uint32_t& sum_up) {
   uint32_t neg_hi = 0, neg_lo = 0, sa = 0, su = 0;
+  uint32_t vpair = 0;
 #pragma unroll
   for (int e = 15; e >= 0; --e) {
-    const uint32_t vb = __float_as_uint(__fadd_rn(__uint_as_float(v[e]), kMagic));
+    uint32_t vb;
+    if (e & 1)
+      magic_add2(v[e - 1], v[e], vpair, vb);
+    else
+      vb = vpair;
     const uint32_t s = (cw16 >> e) & 1u;
     sa += vb;
     su += s * vb;
-    if (decide) {
+    if constexpr (DECIDE) {
       uint32_t m;
       asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(tab_c + 4u * vb + 2u * s));
       const uint32_t w = rw[e >> 1];
@@ -99,15 +114,21 @@ __device__ __forceinline__ uint32_t bias_chunk16(const uint32_t (&v)[16], const 
 // 16-bit threshold of (s, I) is the table entry of D at shared address 2 vb + tab_d
 // (vb = bits(D + 1.5 * 2^23), tab_d = table + 2 (2 dk) - 2 * 0x4B400000, mod 2^32), and
 // |D| = s I + dk sums to the energy.  Returns the new spins as bits 0..15.
+template <bool DECIDE>
 __device__ __forceinline__ uint32_t diag_chunk16(const uint32_t (&v)[16], const uint32_t (&rw)[8],
-                                                 uint32_t tab_d, float& esum, bool decide) {
+                                                 uint32_t tab_d, float& esum) {
   uint32_t neg_hi = 0, neg_lo = 0;
   float e_a = 0.0f, e_b = 0.0f;
+  uint32_t vpair = 0;
 #pragma unroll
   for (int e = 15; e >= 0; --e) {
     const float fd = __uint_as_float(v[e]);
-    if (decide) {
-      const uint32_t vb = __float_as_uint(__fadd_rn(fd, kMagic));
+    if constexpr (DECIDE) {
+      uint32_t vb;
+      if (e & 1)
+        magic_add2(v[e - 1], v[e], vpair, vb);
+      else
+        vb = vpair;
       uint32_t m;
       asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(vb * 2u + tab_d));
       const uint32_t w = rw[e >> 1];
@@ -125,6 +146,58 @@ __device__ __forceinline__ uint32_t diag_chunk16(const uint32_t (&v)[16], const 
   }
   esum += e_a + e_b;
   return ~((neg_hi << 8) | neg_lo) & 0xFFFFu;
+}
+
+// A thread's 32 columns of one chunk (two 16-column halves): the TMEM load of each half runs
+// while its two Philox blocks are drawn (DECIDE: every sweep but the final energy pass),
+// then diag_chunk16 / bias_chunk16.  Returns the new spins of the 32 columns as bits.
+template <bool DECIDE>
+__device__ __forceinline__ uint32_t diag_chunk32(uint32_t ta, uint32_t blk0, uint32_t rg, uint32_t t,
+                                                 uint32_t q, const uint32_t* rk, uint32_t tab_d,
+                                                 float& esum) {
+  uint32_t word = 0;
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2) {
+    uint32_t v[16];
+    tmem_ld16(ta + 16 * h2, v);
+    PhiloxOut o0{}, o1{};
+    if constexpr (DECIDE) {
+      o0 = philox4x32_10_rk(blk0 + 2 * h2, rg, t, q, rk);
+      o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, rg, t, q, rk);
+    }
+    tmem_wait_ld(v);
+    const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+    word |= diag_chunk16<DECIDE>(v, rw8, tab_d, esum) << (16 * h2);
+  }
+  return word;
+}
+
+// As diag_chunk32 for the general table without bias (h = 0, plain image); cw32 holds the
+// 32 current spins, eacc collects sum_i s_i I_i.
+template <bool DECIDE>
+__device__ __forceinline__ uint32_t bias_chunk32(uint32_t ta, uint32_t blk0, uint32_t rg, uint32_t t,
+                                                 uint32_t q, const uint32_t* rk, uint32_t cw32,
+                                                 uint32_t tab_c, int& eacc) {
+  uint32_t word = 0;
+#pragma unroll
+  for (int h2 = 0; h2 < 2; ++h2) {
+    uint32_t v[16];
+    tmem_ld16(ta + 16 * h2, v);
+    PhiloxOut o0{}, o1{};
+    if constexpr (DECIDE) {
+      o0 = philox4x32_10_rk(blk0 + 2 * h2, rg, t, q, rk);
+      o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, rg, t, q, rk);
+    }
+    tmem_wait_ld(v);
+    const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
+    const uint32_t cw16 = (cw32 >> (16 * h2)) & 0xFFFFu;
+    uint32_t sa = 0, su = 0;
+    const uint32_t nb = bias_chunk16<DECIDE>(v, rw8, cw16, tab_c, sa, su);
+    eacc += static_cast<int>(2u * (su - static_cast<uint32_t>(__popc(cw16)) * kMagicBits) -
+                             (sa - 16u * kMagicBits));
+    word |= nb << (16 * h2);
+  }
+  return word;
 }
 
 // DIAG = true: every unit has a diagonal-encoded image (P.dk > 0) and decides from its
@@ -345,28 +418,15 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           const uint32_t blk0 = static_cast<uint32_t>((c * kNT + grp * kCols) >> 3);
           if (dfast) {
             // Diagonal-encoded fields, 16 columns at a time (diag_chunk16).
+            static_assert(kCols == 32 && kWordsPT == 1, "one 32-bit spin word per thread and chunk");
             if (warp_active) {
               float esum = 0.0f;
-#pragma unroll
-              for (int h2 = 0; h2 < kCols / 16; ++h2) {
-                uint32_t v[16];
-                tmem_ld16(ta + 16 * h2, v);
-                PhiloxOut o0{}, o1{};
-                if (!last) {
-                  o0 = philox4x32_10_rk(blk0 + 2 * h2, static_cast<uint32_t>(rg),
-                                        static_cast<uint32_t>(t), q, L.round_keys);
-                  o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, static_cast<uint32_t>(rg),
-                                        static_cast<uint32_t>(t), q, L.round_keys);
-                }
-                tmem_wait_ld(v);
-                const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-                const int w = h2 >> 1;
-                const uint32_t nb = diag_chunk16(v, rw8, tab_d, esum, !last);
-                if (h2 & 1)
-                  nxt[c][w] = (nxt[c][w] | (nb << 16)) & valid_mask(c, w);
-                else
-                  nxt[c][w] = nb;
-              }
+              const uint32_t word =
+                  last ? diag_chunk32<false>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
+                                             L.round_keys, tab_d, esum)
+                       : diag_chunk32<true>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
+                                            L.round_keys, tab_d, esum);
+              nxt[c][0] = word & valid_mask(c, 0);
               eacc += static_cast<int>(esum);
             }
             tc_fence_before();
@@ -378,30 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
             // 16 columns at a time: the TMEM load runs while their two Philox blocks are
             // drawn, then the decisions (bias_chunk16); the buffer is released at the end.
             if (warp_active) {
-#pragma unroll
-              for (int h2 = 0; h2 < kCols / 16; ++h2) {
-                uint32_t v[16];
-                tmem_ld16(ta + 16 * h2, v);
-                PhiloxOut o0{}, o1{};
-                if (!last) {
-                  o0 = philox4x32_10_rk(blk0 + 2 * h2, static_cast<uint32_t>(rg),
-                                        static_cast<uint32_t>(t), q, L.round_keys);
-                  o1 = philox4x32_10_rk(blk0 + 2 * h2 + 1, static_cast<uint32_t>(rg),
-                                        static_cast<uint32_t>(t), q, L.round_keys);
-                }
-                tmem_wait_ld(v);
-                const uint32_t rw8[8] = {o0.x0, o0.x1, o0.x2, o0.x3, o1.x0, o1.x1, o1.x2, o1.x3};
-                const int w = h2 >> 1;
-                const uint32_t cw16 = (cur[c][w] >> (16 * (h2 & 1))) & 0xFFFFu;
-                uint32_t sa = 0, su = 0;
-                const uint32_t nb = bias_chunk16(v, rw8, cw16, tab_c, sa, su, !last);
-                eacc += static_cast<int>(2u * (su - static_cast<uint32_t>(__popc(cw16)) * kMagicBits) -
-                                         (sa - 16u * kMagicBits));
-                if (h2 & 1)
-                  nxt[c][w] = (nxt[c][w] | (nb << 16)) & valid_mask(c, w);
-                else
-                  nxt[c][w] = nb;
-              }
+              const uint32_t word =
+                  last ? bias_chunk32<false>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
+                                             L.round_keys, cur[c][0], tab_c, eacc)
+                       : bias_chunk32<true>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
+                                            L.round_keys, cur[c][0], tab_c, eacc);
+              nxt[c][0] = word & valid_mask(c, 0);
             }
             tc_fence_before();
             __syncwarp();

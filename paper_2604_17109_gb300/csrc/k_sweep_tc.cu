@@ -12,8 +12,8 @@
 //            float32 rule tau_t(I) + xi s + eta_t z(key) >= 0 (Eq. 4)
 //   write    s(t+1) back into the shared-memory A operand, then the next sweep's MMA.
 // The GEMM is transposed with respect to the paper's J s: TMEM lane = replica, column =
-// spin, so that one thread owns one replica row and the energy of that replica is a
-// thread-local sum (plus one partner thread that holds the other half of the columns).
+// spin, so that one thread owns one replica row of one column group and the energy of that
+// replica is a thread-local sum plus the partial sums of the other column groups' threads.
 #include <climits>
 
 #include "kernels.h"
@@ -23,13 +23,15 @@
 namespace pim {
 namespace {
 
-constexpr int kThreads = 256;   // 8 warps: 4 TMEM lane quadrants x 2 column halves
-constexpr int kTileM = 128;     // replicas per CTA (MMA M)
+constexpr int kGroups = 2;               // column groups of a replica row (2 or 3)
+constexpr int kThreads = 128 * kGroups;  // 4 TMEM lane quadrants x kGroups column groups
+constexpr int kTileM = 128;              // replicas per CTA (MMA M)
 
 // The integer value I of an exactly integral float f (|f| < 2^22) appears in the low
 // mantissa bits of f + 1.5 * 2^23.
 constexpr float kMagic = 12582912.0f;
 constexpr uint32_t kMagicBits = 0x4B400000u;
+constexpr uint64_t kMagicPair = 0x4B4000004B400000ull;  // two FP32 1.5 * 2^23
 
 // Two decision modes.
 //  kModeDiag: h = 0 and |I| <= 255.  The couplings are staged with 256 on the diagonal, so
@@ -40,7 +42,20 @@ constexpr int kModeDiag = 0;
 constexpr int kModeBias = 1;
 constexpr int kDiagOffset = 256;
 constexpr int kDiagEntries = 1024;  // D = -512 .. 511
-constexpr int kMaxPrefetch = 1;     // 16-byte table pieces per thread: 256 x 16 B covers 4 KB
+constexpr int kMaxPrefetch = 1;     // 16-byte table pieces per thread: >= 256 x 16 B covers 4 KB
+
+// First 16-column chunk of column group g (g = kGroups: the end), so that every group holds
+// about n / kGroups spins.
+__device__ __forceinline__ int group_begin(int g, int n, int nch) {
+  return g == 0 ? 0 : g == kGroups ? nch : (g * n + 8 * kGroups) / (16 * kGroups);
+}
+
+// Most chunks one group holds, n <= NPAD (checked exhaustively for 2 and 3 groups).
+template <int NPAD>
+__host__ __device__ constexpr int max_group_chunks() {
+  return (NPAD / 16 + kGroups - 1) / kGroups;
+}
+static_assert(kGroups == 2 || kGroups == 3, "column split checked for 2 and 3 groups only");
 
 // One chunk of W = 16 or 8 consecutive spins of one replica in kModeDiag: load the fields
 // D from tensor memory, draw the noise block(s), decide, and add |D| to the energy sum.
@@ -74,10 +89,20 @@ __device__ __forceinline__ uint32_t diag_chunk(uint32_t taddr, uint32_t c, uint3
   // dependent sequences short.
   uint32_t neg_hi = 0, neg_lo = 0;
   float e_a = 0.0f, e_b = 0.0f;
+  // bits of D + 1.5 * 2^23 for two spins per instruction (packed FP32 add, round to nearest:
+  // exact for these integers, identical to two scalar adds)
+  uint32_t ibv[W];
+#pragma unroll
+  for (int e = 0; e < W; e += 2) {
+    uint64_t pr, rr;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(pr) : "r"(v[e]), "r"(v[e + 1]));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rr) : "l"(pr), "l"(kMagicPair));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(ibv[e]), "=r"(ibv[e + 1]) : "l"(rr));
+  }
 #pragma unroll
   for (int e = W - 1; e >= 0; --e) {
     const float f = __uint_as_float(v[e]);
-    const uint32_t ib = __float_as_uint(__fadd_rn(f, kMagic));
+    const uint32_t ib = ibv[e];
     uint32_t m;
     asm volatile("ld.shared.u16 %0, [%1];" : "=r"(m) : "r"(ib * 2u + diag_bias));
     const uint32_t w = rw[e >> 1];
@@ -102,8 +127,8 @@ __device__ __forceinline__ uint32_t diag_chunk(uint32_t taddr, uint32_t c, uint3
 // counter, hence by a CTA already running) published.
 template <int NPAD, int MODE, bool QUEUE>
 __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
-  constexpr int kMaxSlots = NPAD / 32;  // 16-column chunks per column half
-  constexpr int kWordsPerThread = kMaxSlots / 2;
+  constexpr int kMaxSlots = max_group_chunks<NPAD>();  // 16-column chunks per column group
+  constexpr int kWordsPerThread = (kMaxSlots + 1) / 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -112,13 +137,13 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
   uint8_t* sA = sJ + NPAD * NPAD;
   uint32_t* sT = reinterpret_cast<uint32_t*>(sA + kTileM * NPAD);
   float* sPart = reinterpret_cast<float*>(sT + 2 * SW);
-  int* sH = reinterpret_cast<int*>(sPart + 2 * 2 * kTileM);
+  int* sH = reinterpret_cast<int*>(sPart + 2 * kGroups * kTileM);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sH + (MODE == kModeBias ? NPAD : 0));
   uint32_t* sTmem = reinterpret_cast<uint32_t*>(bars + 2);
   int* sAbort = reinterpret_cast<int*>(sTmem + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, grp = warp >> 2;
   const int row = quad * 32 + lane;
 
   const uint32_t bar_mma = smem_u32(&bars[0]);
@@ -168,11 +193,10 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
     const int rg = wk.rbase + row;
     const bool row_valid = rg < R;
     const bool warp_active = (wk.rbase + quad * 32) < R;
-    // Column halves split at the 16-column boundary nearest n/2.
+    // Column groups: contiguous ranges of 16-column chunks, about n / kGroups spins each.
     const int nch = (n + 15) >> 4;
-    const int split = (n + 16) >> 5;
-    const int c0 = half == 0 ? 0 : split;
-    const int myc = half == 0 ? split : nch - split;
+    const int c0 = group_begin(grp, n, nch);
+    const int myc = group_begin(grp + 1, n, nch) - c0;
     const int ksteps = (n + 31) >> 5;
     const int mma_n = (n + 15) & ~15;
     const int t_begin =
@@ -222,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
                  bar_j);
     }
 
-    // ---- per-thread replica state: 16-bit spin chunks of this thread's column half ----
+    // ---- per-thread replica state: 16-bit spin chunks of this thread's column group ---
     // (L2 loads: a later chunk's state was written by another CTA of this launch)
     uint32_t cur[kWordsPerThread], best[kWordsPerThread];
     const uint16_t* cur_in = reinterpret_cast<const uint16_t*>(P.cur_bits);
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
           }
         }
       }
-      sPart[(t & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+      sPart[((t & 1) * kGroups + grp) * kTileM + row] = eacc;
       {
         uint4* pre_dst = reinterpret_cast<uint4*>(sT + ((t + 1) & 1) * SW);
 #pragma unroll
@@ -390,7 +414,9 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
         tc_fence_after();
         issue_fields();  // fields of s(t+1)
       }
-      const float etot = eacc + sPart[(t & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+      float etot = 0.0f;
+#pragma unroll
+      for (int g = 0; g < kGroups; ++g) etot += sPart[((t & 1) * kGroups + g) * kTileM + row];
       const int E = MODE == kModeDiag
                         ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
                         : -(static_cast<int>(etot) / 2);
@@ -436,11 +462,13 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
         }
       }
     }
-    sPart[(t_end & 1) * 2 * kTileM + half * kTileM + row] = eacc;
+    sPart[((t_end & 1) * kGroups + grp) * kTileM + row] = eacc;
     tc_fence_before();
     __syncthreads();
     aborted = *sAbort != 0;
-    const float etot = eacc + sPart[(t_end & 1) * 2 * kTileM + (half ^ 1) * kTileM + row];
+    float etot = 0.0f;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) etot += sPart[((t_end & 1) * kGroups + g) * kTileM + row];
     const int E = MODE == kModeDiag
                       ? -((static_cast<int>(etot) - kDiagOffset * n) / 2)
                       : -(static_cast<int>(etot) / 2);
@@ -461,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_tc_kernel(const Launch L) {
           cur_out[o] = static_cast<uint16_t>(cur[k >> 1] >> ((k & 1) * 16));
           best_out[o] = static_cast<uint16_t>(best[k >> 1] >> ((k & 1) * 16));
         }
-      if (half == 0) {
+      if (grp == 0) {
         P.best_E[rg] = static_cast<double>(best_E);
         P.best_t[rg] = best_t;
         P.first_hit[rg] = first_hit;
@@ -516,7 +544,7 @@ cudaError_t launch_variant(const Launch& L, int blocks, cudaStream_t st) {
 
 int sweep_tc_smem_bytes(int npad, int stride_words_max) {
   return 1024 /* alignment slack */ + npad * npad + kTileM * npad + 2 * stride_words_max * 4 +
-         2 * 2 * kTileM * 4 + 64;
+         2 * kGroups * kTileM * 4 + 64;
 }
 
 cudaError_t launch_sweep_tc(const Launch& L, int npad_max, int blocks, cudaStream_t st,
