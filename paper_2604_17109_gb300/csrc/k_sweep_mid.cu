@@ -419,7 +419,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           if (dfast) {
             // Diagonal-encoded fields, 16 columns at a time (diag_chunk16).
             static_assert(kCols == 32 && kWordsPT == 1, "one 32-bit spin word per thread and chunk");
-            if (warp_active) {
+            // Columns at or past n (the padding of the last chunk) have zero fields and stay
+            // -1: a thread whose 32 columns all lie there skips them (nxt stays 0).
+            if (warp_active && c * kNT + grp * kCols < n) {
               float esum = 0.0f;
               const uint32_t word =
                   last ? diag_chunk32<false>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           if (fast) {
             // 16 columns at a time: the TMEM load runs while their two Philox blocks are
             // drawn, then the decisions (bias_chunk16); the buffer is released at the end.
-            if (warp_active) {
+            if (warp_active && c * kNT + grp * kCols < n) {
               const uint32_t word =
                   last ? bias_chunk32<false>(ta, blk0, static_cast<uint32_t>(rg), static_cast<uint32_t>(t), q,
                                              L.round_keys, cur[c][0], tab_c, eacc)
