@@ -96,7 +96,7 @@ FP4_BF16_NOMINAL = 13.5 / 2.25  # dense E2M1 / BF16 tensor rates (nominal, per G
 #   maxcut8192  sweep_big_kernel<128,BF16>, 50-sweep capture 7.137 GB = the 134 MB image
 #               streamed from HBM every pass (it exceeds L2)
 DRAM_TRAFFIC = {
-    "sk200": (17.862e6 + 0.027e6, 0.0),
+    "sk200": (17.717e6 + 0.036e6, 0.0),
     "sk4096": (8.857e6 - 51 * 32768.0, 32768.0),
     "maxcut8192": (0.0, 7.137e9 / 51),
 }
