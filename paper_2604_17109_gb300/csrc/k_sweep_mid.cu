@@ -6,17 +6,19 @@
 // synchronisation.
 //
 // Per unit, per sweep t (Box 1, PIMI loop; Eq. 2 then Eq. 4):
-//   spins    the panel's spins s(t) stay in shared memory as the A operand of the field GEMM
-//            (128 replicas x npad FP8 +-1, K-major, 128-byte swizzle);
-//   fields   the couplings stream from L2 through a 4-stage cp.async.bulk ring in chunks of
-//            128 output spins; chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one
-//            of four TMEM buffers (tcgen05.mma kind::f8f6f4), so the MMAs of chunk c+1 run
+//   spins    the panel's spins s(t) stay in tensor memory as the A operand of the field
+//            GEMM (128 replicas = TMEM lanes, npad FP8 +-1 along the columns, four per
+//            32-bit column), written by the epilogue threads that own the rows;
+//   fields   the couplings stream from L2 through a 6-stage cp.async.bulk ring in chunks of
+//            128 output spins (the whole shared memory but the step table goes to the ring);
+//            chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one of two TMEM
+//            buffers (tcgen05.mma kind::f8f6f4, A from TMEM), so the MMAs of chunk c+1 run
 //            while the epilogue decides chunk c;
 //   decision 16 epilogue warps (4 TMEM lane quadrants x 4 groups of 32 columns): each
 //            thread owns one replica and 32 spins of every chunk, keeps their old / new
 //            bits in registers, draws the Philox blocks and looks the threshold up in the
 //            step's table at I = D + h; after the last chunk it writes the new spins into
-//            the A image (all MMAs of the sweep have completed by then);
+//            the tensor-memory A image (all MMAs of the sweep have completed by then);
 //   energy   E(s(t)) = -1/2 sum_i s_i (I_i + h_i), exact in int32, reduced over the two
 //            column groups in shared memory; best state (written to the output array when
 //            it improves) and first hit per replica.
@@ -32,8 +34,8 @@ namespace {
 constexpr int kNT = 128;                    // output spins per chunk (MMA N)
 constexpr int kMaxNpad = 1024;
 constexpr int kMaxChunks = kMaxNpad / kNT;
-constexpr int kStages = 4;                  // coupling ring depth
-constexpr int kBufs = 4;                    // TMEM accumulators of kNT columns
+constexpr int kStages = 6;                  // coupling ring depth
+constexpr int kBufs = 2;                    // TMEM accumulators of kNT columns
 constexpr int kTabWords = 4096;             // threshold table of one step in shared memory
 constexpr int kEpiWarps = 16;
 constexpr int kGroups = kEpiWarps / 4;      // column groups per chunk
@@ -41,7 +43,8 @@ constexpr int kCols = kNT / kGroups;        // columns of a chunk per epilogue t
 constexpr int kWordsPT = kCols / 32;        // 32-bit spin words per thread and chunk
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;  // + producer warp + MMA warp
-constexpr int kABytes = 128 * kMaxNpad;     // spin image: 128 rows x npad FP8
+constexpr int kTmemA = kBufs * kNT;         // first TMEM column of the spin image (npad / 4 columns)
+constexpr int kTmemCols = kTmemA + kMaxNpad / 4;
 constexpr int kStageBytes = kNT * 128;      // one K-block of 128 coupling rows
 constexpr int kBarCount = 2 * kStages + 2 * kBufs + 2;
 
@@ -51,12 +54,26 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, uint64
   return mbar_try_wait(bar, parity) || mbar_wait_sleep(bar, parity, limit_ns);
 }
 
-// 32 spins (bits) -> their 32 FP8 +-1 bytes in one row of the A image (neg: the bytes of -1
-// in the unit's format).
-__device__ __forceinline__ void put_spins32(uint8_t* sA, int row, int col, uint32_t bits,
-                                            uint32_t neg) {
-  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col, 128)) = fp8x16_from_bits(bits & 0xFFFFu, neg);
-  *reinterpret_cast<uint4*>(sA + sw128_offset(row, col + 16, 128)) = fp8x16_from_bits(bits >> 16, neg);
+// 32 spins -> their FP8 bytes in the thread's TMEM lane: K index col .. col + 31 = columns
+// col / 4 .. col / 4 + 7 of the spin image (four K values per 32-bit column, lowest byte
+// first).  Warp-collective.
+__device__ __forceinline__ void put_spins32_tm(uint32_t tlane, int col, uint32_t bits, uint32_t neg) {
+  const uint4 lo = fp8x16_from_bits(bits & 0xFFFFu, neg), hi = fp8x16_from_bits(bits >> 16, neg);
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                   tlane + static_cast<uint32_t>(kTmemA + col / 4)),
+               "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w)
+               : "memory");
+}
+
+// D (+)= A B with A (128 x 32 FP8, K-major) in tensor memory at a_tmem.
+__device__ __forceinline__ void mma_f8_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
 }
 
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: integer D in the low mantissa bits
@@ -208,8 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint8_t* sA = smem;
-  uint8_t* sRing = sA + kABytes;
+  uint8_t* sRing = smem;
   uint32_t* sTab = reinterpret_cast<uint32_t*>(sRing + kStages * kStageBytes);
   int* sRed = reinterpret_cast<int*>(sTab + kTabWords);  // [kGroups][128 rows]
   int* sH = sRed + kGroups * 128;                         // [kMaxNpad]
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
   const uint32_t drain = aready + 8;
 
   if (warp == 1) {
-    tmem_alloc(smem_u32(sTmem), kBufs * kNT);
+    tmem_alloc(smem_u32(sTmem), kTmemCols);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -252,6 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
+  const uint32_t tlane = tmem + (static_cast<uint32_t>(quad * 32) << 16);  // this warp's TMEM lanes
 
   // Role counters, continued across units so every mbarrier phase is tracked exactly.
   uint32_t loads = 0, mmas = 0, cpass = 0, apass = 0;
@@ -319,12 +336,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
               break;
             }
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA) + kb * (128 * 128);
             const uint32_t b0 = smem_u32(sRing + s * kStageBytes);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
-              mma_e4m3(tmem + b * kNT, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc_u,
-                       (kb > 0 || ks > 0) ? 1u : 0u);
+              mma_f8_ta(tmem + b * kNT, tmem + kTmemA + kb * 32 + ks * 8, sw128_desc(b0 + ks * 32),
+                        idesc_u, (kb > 0 || ks > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * s);
             ++mmas;
           }
@@ -375,8 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       for (int c = 0; c < kMaxChunks; ++c)
 #pragma unroll
         for (int w = 0; w < kWordsPT; ++w)
-          if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, cur[c][w], neg8);
-      fence_proxy_async_smem();
+          if (c < nchunks) {
+            put_spins32_tm(tlane, c * kNT + grp * kCols + 32 * w, cur[c][w], neg8);
+          }
+      tmem_wait_st();
+      tc_fence_before();
       bool stop = bar_sync_or(1, kEpiThreads, false);
       if (etid == 0) mbar_arrive(aready);
 
@@ -509,8 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
           for (int c = 0; c < kMaxChunks; ++c)
 #pragma unroll
             for (int w = 0; w < kWordsPT; ++w)
-              if (c < nchunks) put_spins32(sA, row, c * kNT + grp * kCols + 32 * w, nxt[c][w], neg8);
-          fence_proxy_async_smem();
+              if (c < nchunks) {
+                put_spins32_tm(tlane, c * kNT + grp * kCols + 32 * w, nxt[c][w], neg8);
+              }
+          tmem_wait_st();
+          tc_fence_before();
         }
         sRed[grp * 128 + row] = eacc;
         stop = bar_sync_or(1, kEpiThreads, waitfail || *sAbort != 0);
@@ -574,13 +596,13 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, kBufs * kNT);
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
 
 int sweep_mid_smem_bytes() {
-  return 1024 + kABytes + kStages * kStageBytes + kTabWords * 4 + kGroups * 128 * 4 + kMaxNpad * 4 +
+  return 1024 + kStages * kStageBytes + kTabWords * 4 + kGroups * 128 * 4 + kMaxNpad * 4 +
          kBarCount * 8 + 32;
 }
 
