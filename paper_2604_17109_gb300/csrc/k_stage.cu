@@ -12,10 +12,16 @@ namespace pim {
 // value J_ij; zero outside n x n.  One thread per image byte.
 // ---------------------------------------------------------------------------------------
 __global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int npad, int diag,
-                                       int e5m2, uint8_t* __restrict__ img) {
-  const uint32_t off = blockIdx.x * blockDim.x + threadIdx.x;
-  if (off >= static_cast<uint32_t>(npad) * npad) return;
+                                       int e5m2, int chunk_major, uint8_t* __restrict__ img) {
+  const uint32_t dst = blockIdx.x * blockDim.x + threadIdx.x;
+  if (dst >= static_cast<uint32_t>(npad) * npad) return;
   const uint32_t block_bytes = static_cast<uint32_t>(npad) * 128u;
+  uint32_t off = dst;  // position in the K-block-major layout
+  if (chunk_major) {
+    // 16 KB block q = (row block c) * kblocks + kb holds K-block kb of rows 128 c .. 128 c + 127
+    const uint32_t kblocks = static_cast<uint32_t>(npad) >> 7, q = dst >> 14;
+    off = (q % kblocks) * block_bytes + (q / kblocks) * 16384u + (dst & 16383u);
+  }
   const int kb = off / block_bytes;
   const uint32_t rem = off % block_bytes;
   const int i = (rem >> 10) * 8 + ((rem & 1023) >> 7);
@@ -29,13 +35,15 @@ __global__ void stage_fp8_image_kernel(const int8_t* __restrict__ J, int n, int 
                                                        e5m2 ? __NV_E5M2 : __NV_E4M3);
     v = static_cast<uint8_t>(e);
   }
-  img[off] = v;
+  img[dst] = v;
 }
 
 cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
-                                   cudaStream_t st, bool e5m2) {
+                                   cudaStream_t st, bool e5m2, bool chunk_major) {
+  if (chunk_major && npad % 128 != 0) return cudaErrorInvalidValue;
   const uint32_t total = static_cast<uint32_t>(npad) * npad;
-  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, diag, e5m2 ? 1 : 0, d_img);
+  stage_fp8_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, diag, e5m2 ? 1 : 0,
+                                                              chunk_major ? 1 : 0, d_img);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 //   spins    the panel's spins s(t) stay in tensor memory as the A operand of the field
 //            GEMM (128 replicas = TMEM lanes, npad FP8 +-1 along the columns, four per
 //            32-bit column), written by the epilogue threads that own the rows;
-//   fields   the couplings stream from L2 through a 6-stage cp.async.bulk ring in chunks of
-//            128 output spins (the whole shared memory but the step table goes to the ring);
+//   fields   the couplings stream from L2 through a 6-stage cp.async.bulk ring (two
+//            K-blocks of 128 coupling rows per stage, one copy when the image is chunk-major)
+//            in chunks of 128 output spins (the shared memory but the step table is the ring);
 //            chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one of two TMEM
 //            buffers (tcgen05.mma kind::f8f6f4, A from TMEM), so the MMAs of chunk c+1 run
 //            while the epilogue decides chunk c;
@@ -45,7 +46,9 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;  // + producer warp + MMA warp
 constexpr int kTmemA = kBufs * kNT;         // first TMEM column of the spin image (npad / 4 columns)
 constexpr int kTmemCols = kTmemA + kMaxNpad / 4;
-constexpr int kStageBytes = kNT * 128;      // one K-block of 128 coupling rows
+constexpr int kBlockBytes = kNT * 128;      // one K-block of 128 coupling rows
+constexpr int kKPS = 2;                     // K-blocks per ring stage
+constexpr int kStageBytes = kKPS * kBlockBytes;
 constexpr int kBarCount = 2 * kStages + 2 * kBufs + 2;
 
 // Bounded wait with the common case (phase already complete) inline; the out-of-line wait
@@ -293,17 +296,26 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
       for (int t = t_begin; t <= t_end && ok; ++t) {
         if (L.inject == 1 && first_unit && t == t_begin) continue;  // injected fault
         for (int c = 0; c < nchunks && ok; ++c)
-          for (int kb = 0; kb < kblocks; ++kb) {
+          for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+            const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
             const uint32_t s = loads % kStages, use = loads / kStages;
             if ((use > 0 && !wait_phase(empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) ||
                 *sAbort != 0) {
               ok = false;
               break;
             }
-            mbar_expect_tx(full0 + 8 * s, kStageBytes);
-            bulk_g2s(smem_u32(sRing + s * kStageBytes),
-                     P.jimg + static_cast<size_t>(kb) * npad * 128 + static_cast<size_t>(c) * kNT * 128,
-                     kStageBytes, full0 + 8 * s);
+            mbar_expect_tx(full0 + 8 * s, nk * kBlockBytes);
+            if (P.e5m2) {
+              // chunk-major image: the stage's K-blocks of chunk c are contiguous, one copy
+              bulk_g2s(smem_u32(sRing + s * kStageBytes),
+                       P.jimg + (static_cast<size_t>(c) * kblocks + kb0) * kBlockBytes, nk * kBlockBytes,
+                       full0 + 8 * s);
+            } else {
+              for (int j = 0; j < nk; ++j)
+                bulk_g2s(smem_u32(sRing + s * kStageBytes + j * kBlockBytes),
+                         P.jimg + static_cast<size_t>(kb0 + j) * npad * 128 + static_cast<size_t>(c) * kNT * 128,
+                         kBlockBytes, full0 + 8 * s);
+            }
             ++loads;
           }
       }
@@ -329,18 +341,22 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
             break;
           }
           tc_fence_after();
-          for (int kb = 0; kb < kblocks; ++kb) {
+          for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+            const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
             const uint32_t s = mmas % kStages, use = mmas / kStages;
             if (!wait_phase(full0 + 8 * s, use & 1, L.wait_ns)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t b0 = smem_u32(sRing + s * kStageBytes);
+            for (int j = 0; j < nk; ++j) {
+              const int kb = kb0 + j;
+              const uint32_t b0 = smem_u32(sRing + s * kStageBytes + j * kBlockBytes);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_f8_ta(tmem + b * kNT, tmem + kTmemA + kb * 32 + ks * 8, sw128_desc(b0 + ks * 32),
-                        idesc_u, (kb > 0 || ks > 0) ? 1u : 0u);
+              for (int ks = 0; ks < 4; ++ks)
+                mma_f8_ta(tmem + b * kNT, tmem + kTmemA + kb * 32 + ks * 8, sw128_desc(b0 + ks * 32),
+                          idesc_u, (kb > 0 || ks > 0) ? 1u : 0u);
+            }
             mma_commit(empty0 + 8 * s);
             ++mmas;
           }

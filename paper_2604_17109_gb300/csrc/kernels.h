@@ -21,9 +21,12 @@ __host__ __device__ inline uint32_t sw128_offset(int row, int k, int rows) {
 
 // Staging (once per instance).
 // diag != 0 puts that value on the diagonal of the image (inside n x n); e5m2 selects the
-// E5M2 element format (default E4M3).
+// E5M2 element format (default E4M3).  The image is a sequence of 16 KB blocks of 128 rows x
+// one 128-byte K-block: K-block-major ([kb][npad / 128 row blocks]) by default, chunk-major
+// ([npad / 128 row blocks][kb]: the K-blocks of 128 output rows contiguous) when
+// chunk_major is set (npad a multiple of 128).
 cudaError_t launch_stage_fp8_image(const int8_t* d_J, int n, int npad, int diag, uint8_t* d_img,
-                                   cudaStream_t st, bool e5m2 = false);
+                                   cudaStream_t st, bool e5m2 = false, bool chunk_major = false);
 cudaError_t launch_stage_f32(const int8_t* d_J, int n, float* d_jf, cudaStream_t st);
 // E2M1 image of the coupling-resident large-N variant, npad x npad / 2 bytes (npad a
 // multiple of 256; couplings in {0, +-1, +-2, +-3, +-4, +-6}).

@@ -994,7 +994,7 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
     return bail(e, "stage J image");
   if (p->dk5) {
     p->d_img5 = reinterpret_cast<uint8_t*>(p->d_slab + o_img5);
-    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->dk5, p->d_img5, ctx->staging, true)) !=
+    if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->dk5, p->d_img5, ctx->staging, true, true)) !=
         cudaSuccess)
       return bail(e, "stage E5M2 J image");
   }
