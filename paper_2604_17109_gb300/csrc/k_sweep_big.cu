@@ -317,7 +317,11 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     // (the image is tile-major), streamed coupling rows in one copy per K-block.
     auto produce = [&](const uint8_t* img) -> bool {
       const uint8_t* a_src = img + static_cast<size_t>(rt) * tile_bytes;
-      const uint8_t* b_src = P.jimg + static_cast<size_t>(cb) * NT * 128;
+      // Coupling images of n > 256 are chunk-major: 16 KB blocks of 128 rows x one K-block,
+      // ordered [row block][K-block], so the stage's K-blocks of a 128-row column block are
+      // one copy; a 64-row column block is half of each 16 KB block (one copy per K-block).
+      const uint8_t* b_src = P.jimg + static_cast<size_t>(NT == 128 ? cb : cb >> 1) * kblocks * 16384 +
+                             (NT == 128 ? 0 : (cb & 1) * 8192);
       for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
         const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
         const uint32_t s = loads % kStages, use = loads / kStages;
@@ -325,10 +329,16 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         mbar_expect_tx(bar_full0 + 8 * s, nk * (kABytes + kBBytes));
         bulk_g2s(smem_u32(sA + s * kKPS * kABytes), a_src + static_cast<size_t>(kb0) * kABytes,
                  nk * kABytes, bar_full0 + 8 * s);
-        if constexpr (kBBytes > 0)
-          for (int j = 0; j < nk; ++j)
-            bulk_g2s(smem_u32(sB + (s * kKPS + j) * kBBytes),
-                     b_src + static_cast<size_t>(kb0 + j) * npad * 128, kBBytes, bar_full0 + 8 * s);
+        if constexpr (kBBytes > 0) {
+          if constexpr (NT == 128) {
+            bulk_g2s(smem_u32(sB + s * kKPS * kBBytes), b_src + static_cast<size_t>(kb0) * 16384,
+                     nk * kBBytes, bar_full0 + 8 * s);
+          } else {
+            for (int j = 0; j < nk; ++j)
+              bulk_g2s(smem_u32(sB + (s * kKPS + j) * kBBytes), b_src + static_cast<size_t>(kb0 + j) * 16384,
+                       kBBytes, bar_full0 + 8 * s);
+          }
+        }
         ++loads;
       }
       return true;

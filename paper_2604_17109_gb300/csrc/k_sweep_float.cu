@@ -443,19 +443,27 @@ cudaError_t launch_serve_float(const Launch& L, const ServeQueue& Q, int npad, i
 
 // J (BF16 bits, row-major n x n) -> BF16 operand image (rows npad, K = npad values, 2 bytes
 // each, K-major with the 128-byte swizzle); zero outside n x n.  One thread per element.
+// chunk_major: the 16 KB blocks (128 rows x one K-block) ordered [row block][K-block].
 __global__ void stage_bf16_image_kernel(const uint16_t* __restrict__ J, int n, int npad,
-                                        uint8_t* __restrict__ img) {
+                                        int chunk_major, uint8_t* __restrict__ img) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= static_cast<uint32_t>(npad) * npad) return;
   const int i = e / npad, j = e % npad;
   const uint16_t v = (i < n && j < n) ? J[static_cast<size_t>(i) * n + j] : 0;
-  *reinterpret_cast<uint16_t*>(img + sw128_offset(i, 2 * j, npad)) = v;
+  uint32_t off = sw128_offset(i, 2 * j, npad);  // K-block-major position
+  if (chunk_major) {
+    const uint32_t kblocks = static_cast<uint32_t>(npad) * 2u / 128u, block_bytes = npad * 128u;
+    const uint32_t kb = off / block_bytes, rem = off % block_bytes;
+    off = ((rem >> 14) * kblocks + kb) * 16384u + (rem & 16383u);
+  }
+  *reinterpret_cast<uint16_t*>(img + off) = v;
 }
 
 cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, bool chunk_major) {
+  if (chunk_major && npad % 128 != 0) return cudaErrorInvalidValue;
   const uint32_t total = static_cast<uint32_t>(npad) * npad;
-  stage_bf16_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, d_img);
+  stage_bf16_image_kernel<<<(total + 255) / 256, 256, 0, st>>>(d_J, n, npad, chunk_major ? 1 : 0, d_img);
   return cudaGetLastError();
 }
 

@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_mid_kernel(const __grid_con
               break;
             }
             mbar_expect_tx(full0 + 8 * s, nk * kBlockBytes);
-            if (P.e5m2) {
-              // chunk-major image: the stage's K-blocks of chunk c are contiguous, one copy
+            if (npad > 256) {
+              // images of n > 256 (npad >= 512) are chunk-major: the stage's K-blocks of chunk
+              // c are contiguous, one copy
               bulk_g2s(smem_u32(sRing + s * kStageBytes),
                        P.jimg + (static_cast<size_t>(c) * kblocks + kb0) * kBlockBytes, nk * kBlockBytes,
                        full0 + 8 * s);

@@ -63,8 +63,10 @@ int sweep_tc_smem_bytes(int npad, int stride_words_max);
 // Real-valued couplings (BF16 operands, FP32 decision), n <= 256.
 cudaError_t launch_sweep_float(const Launch& L, int npad, int blocks, cudaStream_t st);
 int sweep_float_smem_bytes(int npad);
+// BF16 image: the same block structure as the FP8 image (16 KB blocks of 128 rows x one
+// 128-byte K-block of 64 values), K-block-major or chunk-major.
 cudaError_t launch_stage_bf16_image(const uint16_t* d_J, int n, int npad, uint8_t* d_img,
-                                    cudaStream_t st);
+                                    cudaStream_t st, bool chunk_major = false);
 // Persistent serving variant of the real-valued kernel: `blocks` CTAs take requests from Q
 // until it stays empty for Q.idle_ns or Q.stop is set (L: sweeps, round keys, waits).
 cudaError_t launch_serve_float(const Launch& L, const ServeQueue& Q, int npad, int blocks,

@@ -849,7 +849,7 @@ int create_real(pim_instance** out, int n, int j_type, const void* J, const void
       return bail(e, "upload h");
   }
   if ((e = staging_after_upload(ctx, p->device)) != cudaSuccess) return bail(e, "staging order");
-  if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging)) != cudaSuccess)
+  if ((e = launch_stage_bf16_image(d_bf, n, p->npad, p->d_img, ctx->staging, n > kMaxNTensor)) != cudaSuccess)
     return bail(e, "stage BF16 J image");
   if ((e = take_event(p->device, &p->ready)) != cudaSuccess)
     return bail(e, "cudaEventCreate");
@@ -989,7 +989,8 @@ PIM_API int pim_create(pim_instance** out, int n, int j_type, const void* J, con
   }
   if ((e = staging_after_upload(ctx, p->device)) != cudaSuccess) return bail(e, "staging order");
   p->diag = n <= kMaxNTensor && !p->has_h && (p->imax | 63) <= kMaxImaxDiag;
-  if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging)) !=
+  if ((e = launch_stage_fp8_image(p->d_J8, n, p->npad, p->diag ? 256 : 0, p->d_img, ctx->staging, false,
+                                   n > kMaxNTensor)) !=
       cudaSuccess)
     return bail(e, "stage J image");
   if (p->dk5) {
