@@ -50,6 +50,11 @@ constexpr int kSmemBudget = 227 * 1024;
 // its size (up to 16 KB measured), so a stage moves two K-blocks of the tile's spins in one
 // copy (the spin image is tile-major for that) instead of one copy per K-block.
 constexpr int KPS = 2;
+// Odd sweeps walk the K-blocks from the last to the first, so a sweep starts on the coupling
+// blocks the previous one read last, which are still in L2 (BF16 Max-Cut N = 8192, whose
+// 134 MB image just exceeds L2: DRAM reads 136 -> 75 MB per sweep, 43.9 -> 41.7 us).  The
+// order depends on the absolute sweep index, so split runs and resumes sum in the same order.
+constexpr bool kRev = true;
 constexpr int kMaxStagesFp4 = 4;  // ring depth cap of the coupling-resident variant
 
 // Shared-memory plan of one kernel variant: NT output spins per CTA, operand variant OP.
@@ -320,14 +325,16 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     // is refilled once the MMAs that read it have completed (its empty barrier).
     // A stage holds kKPS consecutive K-blocks: the tile's spins of all of them in one copy
     // (the image is tile-major), streamed coupling rows in one copy per K-block.
-    auto produce = [&](const uint8_t* img) -> bool {
+    auto produce = [&](const uint8_t* img, bool rev) -> bool {
       const uint8_t* a_src = img + static_cast<size_t>(rt) * tile_bytes;
       // Coupling images of n > 256 are chunk-major: 16 KB blocks of 128 rows x one K-block,
       // ordered [row block][K-block], so the stage's K-blocks of a 128-row column block are
       // one copy; a 64-row column block is half of each 16 KB block (one copy per K-block).
       const uint8_t* b_src = P.jimg + static_cast<size_t>(NT == 128 ? cb : cb >> 1) * kblocks * 16384 +
                              (NT == 128 ? 0 : (cb & 1) * 8192);
-      for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+      const int nst = (kblocks + kKPS - 1) / kKPS;
+      for (int si = 0; si < nst; ++si) {
+        const int kb0 = (rev ? nst - 1 - si : si) * kKPS;
         const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
         const uint32_t s = loads % kStages, use = loads / kStages;
         if (use > 0 && !mbar_wait_fast(bar_empty0 + 8 * s, (use - 1) & 1, L.wait_ns)) return false;
@@ -351,12 +358,14 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
     // MMA issuer (thread 32): D = S_tile x J_block^T, K block by K block as stages land; it
     // never waits for an MMA to finish, only for data.  Each MMA consumes 32 bytes of K
     // (32 FP8, 16 BF16 or 64 E2M1 values).
-    auto multiply = [&]() -> bool {
+    auto multiply = [&](bool rev) -> bool {
       if (!jres_ready) {
         if (!mbar_wait_fast(bar_jres, 0, L.wait_ns)) return false;
         jres_ready = true;
       }
-      for (int kb0 = 0; kb0 < kblocks; kb0 += kKPS) {
+      const int nst = (kblocks + kKPS - 1) / kKPS;
+      for (int si = 0; si < nst; ++si) {
+        const int kb0 = (rev ? nst - 1 - si : si) * kKPS;
         const int nk = kblocks - kb0 < kKPS ? kblocks - kb0 : kKPS;
         const uint32_t s = mmas % kStages, use = mmas / kStages;
         if (!mbar_wait_fast(bar_full0 + 8 * s, use & 1, L.wait_ns)) return false;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
                                   : smem_u32(sB + (s * kKPS + j) * kBBytes);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t acc = (kb0 + j > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t acc = (si > 0 || j > 0 || ks > 0) ? 1u : 0u;
             if constexpr (REAL)
               mma_bf16(tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc, acc);
             else if constexpr (FP4)
@@ -416,12 +425,12 @@ __global__ void __launch_bounds__(kThreads, 1) sweep_big_kernel(const __grid_con
         fence_proxy_async_global();
         // Injected fault: nothing is loaded in the first sweep, so the MMA thread's first
         // wait cannot complete.
-        if (!(L.inject == 1 && t == t_begin) && !produce(L.s_img[cur_img])) {
+        if (!(L.inject == 1 && t == t_begin) && !produce(L.s_img[cur_img], kRev && (t & 1))) {
           atomicOr(L.err, kDevErrTimeout);
           grid_abort(L.bar);
         }
       } else if (tid == 32) {
-        if (!multiply()) {
+        if (!multiply(kRev && (t & 1))) {
           atomicOr(L.err, kDevErrTimeout);
           grid_abort(L.bar);
         }
