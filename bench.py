@@ -97,7 +97,7 @@ FP4_BF16_NOMINAL = 13.5 / 2.25  # dense E2M1 / BF16 tensor rates (nominal, per G
 #               streamed from HBM every pass (it exceeds L2)
 DRAM_TRAFFIC = {
     "sk200": (17.717e6 + 0.036e6, 0.0),
-    "sk4096": (9.025e6 - 51 * 32768.0, 32768.0),
+    "sk4096": (8.978e6 - 51 * 32768.0, 32768.0),
     "maxcut8192": (0.0, (3.839e9 + 0.217e9) / 51),
 }
 
