@@ -11,7 +11,7 @@
 //            32-bit column), written by the epilogue threads that own the rows;
 //   fields   the couplings stream from L2 through a 3-stage cp.async.bulk ring (four
 //            K-blocks of 128 coupling rows per stage, one copy when the image is chunk-major)
-//            in chunks of 128 output spins (the shared memory but the step table is the ring);
+//            in chunks of 128 output spins (all shared memory but the step table is ring);
 //            chunk c accumulates D[r, i] = sum_j S[r, j] J[i, j] into one of two TMEM
 //            buffers (tcgen05.mma kind::f8f6f4, A from TMEM), so the MMAs of chunk c+1 run
 //            while the epilogue decides chunk c;
@@ -20,7 +20,7 @@
 //            bits in registers, draws the Philox blocks and looks the threshold up in the
 //            step's table at I = D + h; after the last chunk it writes the new spins into
 //            the tensor-memory A image (all MMAs of the sweep have completed by then);
-//   energy   E(s(t)) = -1/2 sum_i s_i (I_i + h_i), exact in int32, reduced over the two
+//   energy   E(s(t)) = -1/2 sum_i s_i (I_i + h_i), exact in int32, reduced over the four
 //            column groups in shared memory; best state (written to the output array when
 //            it improves) and first hit per replica.
 #include <climits>
